@@ -1,0 +1,198 @@
+/*
+ * sem.h -- C ABI of the GB300 (sm_103a) spectral-element pressure-Poisson
+ * library (libsem_gb300.so).
+ *
+ * The operations follow the paper "Experience and Analysis of Scalable
+ * High-Fidelity Computational Fluid Dynamics on Modular Supercomputing
+ * Architectures" (Karp et al., arXiv 2405.05640), section 3.1 ("Neko"): the
+ * domain is split into E hexahedral elements carrying an order-N Lagrange
+ * basis on the Gauss-Lobatto-Legendre (GLL) points; every operator except
+ * the gather-scatter acts element by element (matrix-free); the gather-
+ * scatter sums the copies of nodes shared between elements; a preconditioned
+ * Krylov method solves Ax = b each time step.  Section 4.2 notes that the
+ * solver is memory bound and that the gather-scatter is the communication
+ * kernel.  Formulas are the textbook SEM ones the paper cites (Deville,
+ * Fischer & Mund 2002).
+ *
+ * Conventions (all entry points):
+ *  - Every device pointer is owned by the caller.  The library allocates no
+ *    device memory: sem_mesh_create places its arrays in a caller-supplied
+ *    device workspace, sem_pcg_solve uses a caller-supplied scratch buffer.
+ *    Host pointers are read during the call only.
+ *  - Fields are element-local ("E-layout"): u[e][k][j][i], i fastest,
+ *    E * (N+1)^3 contiguous values, element e = ex + nx*(ey + ny*ez).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    are stream-ordered and asynchronous unless stated otherwise.
+ *  - Return value: SEM_OK or a negative SEM_ERR_* code; no call aborts the
+ *    process.  sem_last_error() gives a message for the calling thread.
+ *  - Thread safety: calls on distinct meshes may run concurrently from
+ *    different host threads.
+ */
+#ifndef SEM_GB300_H
+#define SEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_OK 0
+#define SEM_ERR_INVALID_ARG (-1)
+#define SEM_ERR_CUDA (-2)
+#define SEM_ERR_MESH (-3)          /* det J <= 0 somewhere */
+#define SEM_ERR_WORKSPACE (-4)     /* workspace / scratch too small or misaligned */
+#define SEM_ERR_NAN (-5)           /* NaN or Inf in the right-hand side */
+#define SEM_ERR_NOT_CONVERGED (-6) /* max_iter reached; x and stats still filled */
+#define SEM_ERR_TIMEOUT (-7)       /* a bounded device wait gave up */
+#define SEM_ERR_UNSUPPORTED (-8)   /* order N or option not built */
+
+#define SEM_MAX_ORDER 11           /* 1 <= N <= SEM_MAX_ORDER */
+
+/* Data types of field arguments. */
+#define SEM_F64 0
+#define SEM_F32 1
+
+/* Extra precision copies of the geometric factors that sem_mesh_create
+ * builds (bitmask; FP64 factors are always built). */
+#define SEM_GEOM_F32 1             /* FP32 factors for the FP32 operator */
+
+typedef struct sem_mesh sem_mesh;  /* opaque; freed by sem_mesh_destroy */
+
+/* A box of nel[0] x nel[1] x nel[2] hexahedra.  Topology: local point
+ * (e; i,j,k) of element (ex,ey,ez) is the global node
+ * (ex*N+i, ey*N+j, ez*N+k), wrapped on periodic axes.  Geometry: the
+ * trilinear map of the 8 vertices of each element (any hexahedra with a
+ * positive Jacobian; the box only fixes which nodes are shared). */
+typedef struct {
+    int N;                 /* polynomial order, 1..SEM_MAX_ORDER */
+    int nel[3];            /* elements per axis, each >= 1 */
+    int periodic[3];       /* nonzero = periodic axis */
+    int dirichlet_faces;   /* bit 2a: low face of axis a, bit 2a+1: high face;
+                              ignored on periodic axes */
+    const double *vertices;/* HOST array [E][8][3], vertex v = vx+2vy+4vz */
+    int geom_flags;        /* SEM_GEOM_* bitmask */
+} sem_mesh_desc;
+
+typedef struct {
+    int N;
+    int64_t E;             /* number of elements */
+    int64_t nloc;          /* E * (N+1)^3 element-local points */
+    int64_t nglob;         /* unique global nodes (including Dirichlet nodes) */
+    int64_t n_paper;       /* E * N^3, the paper's DOF count (Table 1) */
+    int64_t n_shared_groups;  /* gather-scatter groups (shared or masked nodes) */
+    int64_t n_shared_points;  /* local points in those groups */
+    size_t workspace_bytes;   /* bytes of the mesh workspace in use */
+} sem_mesh_info;
+
+/* Library version string and message for the calling thread's last error. */
+const char *sem_version(void);
+const char *sem_last_error(void);
+const char *sem_status_string(int status);
+
+/* Bytes of device workspace sem_mesh_create needs for `desc` (0 on invalid
+ * arguments).  Builds the host-side connectivity to count shared nodes. */
+size_t sem_mesh_workspace_bytes(const sem_mesh_desc *desc);
+
+/* Build a mesh: copy the vertices to the device, compute the geometric
+ * factors G (six per point: rr, ss, tt, rs, rt, st, each
+ * rho_i rho_j rho_k detJ sum_m dr_a/dx_m dr_b/dx_m), the diagonal mass B,
+ * the multiplicity, the assembled Jacobi diagonal and the gather-scatter
+ * groups, all inside `d_workspace` (device, 256-byte aligned, `bytes` >=
+ * sem_mesh_workspace_bytes).  Waits for `stream` before returning (it checks
+ * det J).  Returns SEM_ERR_MESH if det J <= 0 at any GLL point,
+ * SEM_ERR_WORKSPACE if the workspace is too small or misaligned. */
+int sem_mesh_create(const sem_mesh_desc *desc, void *d_workspace, size_t bytes,
+                    void *stream, sem_mesh **out);
+int sem_mesh_destroy(sem_mesh *mesh);
+int sem_mesh_get_info(const sem_mesh *mesh, sem_mesh_info *info);
+
+/* Physical coordinates of the GLL points: xyz[a][e][p] (device, 3*nloc). */
+int sem_mesh_coords(const sem_mesh *mesh, double *xyz, void *stream);
+
+/* Copies of mesh arrays (device destinations, nloc values each):
+ * which = 0: mass B; 1: multiplicity; 2: inverse assembled Jacobi diagonal
+ * (0 on Dirichlet nodes); 3..8: geometric factor rr, ss, tt, rs, rt, st
+ * (E-layout, nloc values each). */
+int sem_mesh_field(const sem_mesh *mesh, int which, double *dst, void *stream);
+
+/* Local (unassembled) stiffness w = A_L u, element by element:
+ *   u_r = D u, u_s, u_t along the three directions; v = G (u_r,u_s,u_t);
+ *   w = D^T v_r + D^T v_s + D^T v_t.
+ * u, w: device, nloc values of `dtype` (SEM_F64, or SEM_F32 when the mesh
+ * was built with SEM_GEOM_F32; FP32 accumulation).  u and w must not
+ * overlap. */
+int sem_ax(const sem_mesh *mesh, const void *u, void *w, int dtype, void *stream);
+
+/* Local Helmholtz operator w = h1 A_L u + h2 B u (FP64). */
+int sem_helmholtz(const sem_mesh *mesh, double h1, double h2, const double *u, double *w,
+                  void *stream);
+
+/* Gather-scatter (direct stiffness summation) in place: every copy of a
+ * shared global node receives the sum of all its copies, accumulated in
+ * ascending local index; with apply_mask != 0 the nodes on Dirichlet faces
+ * are then set to 0.  u: device, nloc values of `dtype`. */
+int sem_dssum(const sem_mesh *mesh, void *u, int dtype, int apply_mask, void *stream);
+
+/* Scatter a global-node vector to E-layout: u_loc[l] = u_glob[gid(l)],
+ * gid = I + Gx (J + Gy K) of the box numbering (G_a = nel_a N, plus 1 on a
+ * non-periodic axis).  Device pointers, FP64. */
+int sem_scatter(const sem_mesh *mesh, const double *u_glob, double *u_loc, void *stream);
+
+/* Unique-node inner product <a, b> = sum_l a_l b_l / mult_l of continuous
+ * E-layout fields, FP64, written to *d_result (device).  Deterministic. */
+int sem_glsc3(const sem_mesh *mesh, const double *a, const double *b, double *d_result,
+              void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* Jacobi-preconditioned conjugate gradients on the assembled system
+ * M Q Q^T (h1 A_L + h2 B) x = b (M: Dirichlet mask).  b must be continuous
+ * and zero on Dirichlet nodes.  Stops when ||r|| <= tol ||b|| (tol_is_
+ * relative) or ||r|| <= tol, with ||.|| the unique-node norm.
+ * precision = SEM_PCG_F64: all FP64.
+ * precision = SEM_PCG_MIXED: FP64 iterative refinement around inner FP32
+ *   PCG solves (FP32 operator and vectors, FP32 accumulation), each to
+ *   inner_tol relative; the outer residual b - A x, the outer dot products
+ *   and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh. */
+#define SEM_PCG_F64 0
+#define SEM_PCG_MIXED 1
+typedef struct {
+    double tol;            /* stopping tolerance */
+    int tol_is_relative;   /* 1: relative to ||b||, 0: absolute */
+    int max_iter;          /* total inner iterations allowed */
+    int precision;         /* SEM_PCG_F64 or SEM_PCG_MIXED */
+    double inner_tol;      /* SEM_PCG_MIXED: inner relative tolerance (e.g. 1e-4) */
+    double h1, h2;         /* operator h1 A + h2 B; Poisson: h1 = 1, h2 = 0 */
+    int check_every;       /* iterations between host convergence checks (0 = 16) */
+    int use_initial_guess; /* 1: x holds x0 on entry; 0: start from x = 0 */
+} sem_pcg_opts;
+
+typedef struct {
+    int iters;             /* total (inner) CG iterations */
+    int outer_iters;       /* refinement steps (SEM_PCG_MIXED), else 0 */
+    int status;            /* same as the return value */
+    double rel_res;        /* final ||r|| / ||b|| (FP64 true residual for MIXED) */
+    double abs_res;        /* final ||r|| */
+    double bnorm;          /* ||b|| */
+    double wall_ms;        /* host wall time of the call */
+} sem_pcg_stats;
+
+/* Scratch bytes sem_pcg_solve needs (device). */
+size_t sem_pcg_scratch_bytes(const sem_mesh *mesh, const sem_pcg_opts *opts);
+
+/* Solve; b, x device FP64 E-layout (x: initial guess if use_initial_guess,
+ * solution on return, continuous).  Waits for `stream` (it reads the
+ * convergence flag every check_every iterations) and fills *stats (host).
+ * Returns SEM_OK, SEM_ERR_NOT_CONVERGED (x and stats still valid),
+ * SEM_ERR_NAN, SEM_ERR_WORKSPACE, SEM_ERR_TIMEOUT or SEM_ERR_CUDA. */
+int sem_pcg_solve(const sem_mesh *mesh, const double *b, double *x, const sem_pcg_opts *opts,
+                  sem_pcg_stats *stats, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* Read and clear the mesh's device error word after waiting for `stream`:
+ * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */
+int sem_mesh_check_device_error(const sem_mesh *mesh, int *code, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_GB300_H */

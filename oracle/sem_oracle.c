@@ -135,6 +135,10 @@ int or_geometry(int N, long E, const double *verts, const double *xi,
     int status = OR_OK;
     for (long e = 0; e < E; ++e) {
         const double *V = verts + e * 24;
+        /* J is invariant under translation, so it is taken from the
+         * coordinates relative to vertex 0 (same derivative, smaller
+         * rounding in the D contraction far from the origin). */
+        double V0[3] = {V[0], V[1], V[2]};
         /* trilinear map evaluated at the GLL points */
         for (int k = 0; k < n1; ++k)
             for (int j = 0; j < n1; ++j)
@@ -147,7 +151,7 @@ int or_geometry(int N, long E, const double *verts, const double *xi,
                     for (int a = 0; a < 3; ++a) {
                         double x = 0.0;
                         for (int v = 0; v < 8; ++v)
-                            x += V[v * 3 + a] * fr[v & 1] * fs[(v >> 1) & 1] * ft[(v >> 2) & 1];
+                            x += (V[v * 3 + a] - V0[a]) * fr[v & 1] * fs[(v >> 1) & 1] * ft[(v >> 2) & 1];
                         X[a * npt + p] = x;
                     }
                 }
@@ -192,7 +196,13 @@ int or_geometry(int N, long E, const double *verts, const double *xi,
                         }
                     if (B) B[e * npt + p] = wq;
                     if (xyz)
-                        for (int a = 0; a < 3; ++a) xyz[(a * E + e) * npt + p] = X[a * npt + p];
+                        for (int a = 0; a < 3; ++a) {
+                            double r = xi[i], s = xi[j], t = xi[k], x = 0.0;
+                            for (int v = 0; v < 8; ++v)
+                                x += V[v * 3 + a] * 0.125 * ((v & 1) ? 1.0 + r : 1.0 - r) *
+                                     (((v >> 1) & 1) ? 1.0 + s : 1.0 - s) * (((v >> 2) & 1) ? 1.0 + t : 1.0 - t);
+                            xyz[(a * E + e) * npt + p] = x;
+                        }
                 }
     }
     free(X);

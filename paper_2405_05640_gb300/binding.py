@@ -1,0 +1,248 @@
+"""ctypes binding of libsem_gb300.so (include/sem.h): argument marshalling only.
+
+Device memory comes from PyTorch tensors (their data pointers are passed
+through), streams from torch.cuda.current_stream().  Every computation runs in
+the library's CUDA kernels; there is no CPU or PyTorch fallback -- if the
+library is missing, lib() raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "_lib", "libsem_gb300.so")
+
+SEM_OK = 0
+SEM_ERR_INVALID_ARG = -1
+SEM_ERR_CUDA = -2
+SEM_ERR_MESH = -3
+SEM_ERR_WORKSPACE = -4
+SEM_ERR_NAN = -5
+SEM_ERR_NOT_CONVERGED = -6
+SEM_ERR_TIMEOUT = -7
+SEM_ERR_UNSUPPORTED = -8
+SEM_F64, SEM_F32 = 0, 1
+SEM_GEOM_F32 = 1
+SEM_PCG_F64, SEM_PCG_MIXED = 0, 1
+
+FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("nel", ctypes.c_int * 3), ("periodic", ctypes.c_int * 3),
+                ("dirichlet_faces", ctypes.c_int), ("vertices", ctypes.POINTER(ctypes.c_double)),
+                ("geom_flags", ctypes.c_int)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("E", ctypes.c_int64), ("nloc", ctypes.c_int64),
+                ("nglob", ctypes.c_int64), ("n_paper", ctypes.c_int64),
+                ("n_shared_groups", ctypes.c_int64), ("n_shared_points", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class PcgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("tol_is_relative", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
+                ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int)]
+
+
+class PcgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("wall_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "sem_version": ([], ctypes.c_char_p),
+    "sem_last_error": ([], ctypes.c_char_p),
+    "sem_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "sem_mesh_workspace_bytes": ([ctypes.POINTER(MeshDesc)], ctypes.c_size_t),
+    "sem_mesh_create": ([ctypes.POINTER(MeshDesc), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "sem_mesh_destroy": ([_VP], ctypes.c_int),
+    "sem_mesh_get_info": ([_VP, ctypes.POINTER(MeshInfo)], ctypes.c_int),
+    "sem_mesh_coords": ([_VP, _VP, _VP], ctypes.c_int),
+    "sem_mesh_field": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "sem_ax": ([_VP, _VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
+    "sem_helmholtz": ([_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP], ctypes.c_int),
+    "sem_dssum": ([_VP, _VP, ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
+    "sem_scatter": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_glsc3": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_pcg_scratch_bytes": ([_VP, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
+    "sem_pcg_solve": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t,
+                       _VP], ctypes.c_int),
+    "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def exported_names() -> list[str]:
+    return list(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (raises if it has not been built: no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO):
+                raise RuntimeError(f"{SO} not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(SO)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().sem_last_error().decode()
+        super().__init__(f"{where}: status {status} ({lib().sem_status_string(status).decode()}): {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> int:
+    if status != SEM_OK:
+        raise SemError(status, where)
+    return status
+
+
+def _stream():
+    import torch
+    return _VP(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return _VP(t.data_ptr())
+
+
+class Mesh:
+    """A box mesh living in a caller-owned (PyTorch) device workspace."""
+
+    def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False):
+        import numpy as np
+        import torch
+        self._verts = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 8, 3)
+        d = MeshDesc()
+        d.N = int(N)
+        d.nel[:] = [int(a) for a in nel]
+        d.periodic[:] = [int(bool(a)) for a in periodic]
+        d.dirichlet_faces = int(faces)
+        d.vertices = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.geom_flags = SEM_GEOM_F32 if geom_f32 else 0
+        self.desc = d
+        nbytes = lib().sem_mesh_workspace_bytes(ctypes.byref(d))
+        if nbytes == 0:
+            raise SemError(SEM_ERR_INVALID_ARG, "sem_mesh_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        h = _VP()
+        check(lib().sem_mesh_create(ctypes.byref(d), _VP(self._ws_ptr), nbytes, _stream(), ctypes.byref(h)),
+              "sem_mesh_create")
+        self.handle = h
+        info = MeshInfo()
+        check(lib().sem_mesh_get_info(h, ctypes.byref(info)), "sem_mesh_get_info")
+        self.info = info
+        self.N, self.E, self.nloc, self.nglob = info.N, info.E, info.nloc, info.nglob
+        self.npt = (self.N + 1) ** 3
+        self._red = torch.empty(1024 * 8 + 256, dtype=torch.uint8, device="cuda")
+        self._res = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sem_mesh_destroy(h)
+            self.handle = None
+
+    # ---- mesh data
+    def coords(self):
+        import torch
+        xyz = torch.empty((3, self.E, self.npt), dtype=torch.float64, device="cuda")
+        check(lib().sem_mesh_coords(self.handle, _ptr(xyz), _stream()), "sem_mesh_coords")
+        return xyz
+
+    def field(self, which: int):
+        import torch
+        out = torch.empty(self.nloc, dtype=torch.float64, device="cuda")
+        check(lib().sem_mesh_field(self.handle, int(which), _ptr(out), _stream()), "sem_mesh_field")
+        return out
+
+    # ---- operators
+    def ax(self, u, w=None):
+        import torch
+        if w is None:
+            w = torch.empty_like(u)
+        dt = SEM_F64 if u.dtype == torch.float64 else SEM_F32
+        check(lib().sem_ax(self.handle, _ptr(u), _ptr(w), dt, _stream()), "sem_ax")
+        return w
+
+    def helmholtz(self, h1, h2, u, w=None):
+        import torch
+        if w is None:
+            w = torch.empty_like(u)
+        check(lib().sem_helmholtz(self.handle, float(h1), float(h2), _ptr(u), _ptr(w), _stream()), "sem_helmholtz")
+        return w
+
+    def dssum(self, u, mask: bool = True):
+        import torch
+        dt = SEM_F64 if u.dtype == torch.float64 else SEM_F32
+        check(lib().sem_dssum(self.handle, _ptr(u), dt, int(bool(mask)), _stream()), "sem_dssum")
+        return u
+
+    def scatter(self, u_glob):
+        import torch
+        out = torch.empty(self.nloc, dtype=torch.float64, device="cuda")
+        check(lib().sem_scatter(self.handle, _ptr(u_glob), _ptr(out), _stream()), "sem_scatter")
+        return out
+
+    def glsc3(self, a, b) -> float:
+        base = (self._red.data_ptr() + 255) // 256 * 256
+        check(lib().sem_glsc3(self.handle, _ptr(a), _ptr(b), _ptr(self._res), _VP(base), 1024 * 8 + 64,
+                              _stream()), "sem_glsc3")
+        return float(self._res.item())
+
+    def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
+                 check_every=16, use_initial_guess=False, relative=True) -> PcgOpts:
+        o = PcgOpts()
+        o.tol, o.tol_is_relative, o.max_iter, o.precision = float(tol), int(relative), int(max_iter), int(precision)
+        o.inner_tol, o.h1, o.h2 = float(inner_tol), float(h1), float(h2)
+        o.check_every, o.use_initial_guess = int(check_every), int(bool(use_initial_guess))
+        return o
+
+    def pcg_scratch(self, opts: PcgOpts):
+        import torch
+        n = lib().sem_pcg_scratch_bytes(self.handle, ctypes.byref(opts))
+        return torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+
+    def pcg(self, b, x=None, scratch=None, raise_on_error=True, **kw):
+        """Solve with sem_pcg_solve; returns (x, stats dict)."""
+        import torch
+        opts = self.pcg_opts(use_initial_guess=x is not None, **kw)
+        if x is None:
+            x = torch.zeros_like(b)
+        if scratch is None:
+            scratch = self.pcg_scratch(opts)
+        base = (scratch.data_ptr() + 255) // 256 * 256
+        nbytes = scratch.numel() - (base - scratch.data_ptr())
+        st = PcgStats()
+        status = lib().sem_pcg_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(st),
+                                     _VP(base), nbytes, _stream())
+        if raise_on_error and status not in (SEM_OK,):
+            raise SemError(status, "sem_pcg_solve")
+        return x, st.as_dict()
+
+    def check_device_error(self) -> int:
+        c = ctypes.c_int()
+        check(lib().sem_mesh_check_device_error(self.handle, ctypes.byref(c), _stream()), "check_device_error")
+        return c.value

@@ -1,0 +1,315 @@
+// sem_ax.cu -- matrix-free local stiffness / Helmholtz operator.
+//
+// Paper section 3.1: every operator except the gather-scatter is applied
+// element by element ("matrix-free"), with identical cost per element; the
+// basis is the order-N Lagrange basis on the GLL points.  Per element e:
+//   u_r = D u (along r), u_s, u_t likewise;
+//   (v_r, v_s, v_t) = G (u_r, u_s, u_t), G the symmetric 3x3 geometric factors;
+//   w = D^T v_r + D^T v_s + D^T v_t  [+ Helmholtz: w = h1 w + h2 B u].
+//
+// GB300 design: a persistent grid (a few CTAs per SM), each CTA owning one
+// element at a time.  The element's u slab and its six geometric-factor slabs
+// (contiguous in the [E][6][npt] layout) are brought into shared memory by
+// 1-D bulk copies on the TMA engine, completing on an mbarrier; a ring of
+// stages lets the copies of the next element overlap the contraction of the
+// current one.  Threads are laid out (i, j) over the (N+1)^2 columns and loop
+// over k, holding their u column and the t-direction results in registers.
+// Every mbarrier wait is bounded in time; on time-out the kernel records
+// kDevTimeoutTma in the mesh error word and all CTAs leave the loop.
+
+#include "sem_common.cuh"
+
+namespace sem {
+
+template <typename T>
+struct AxSmem {
+    // byte offsets inside dynamic shared memory
+    int stage_bytes, u_off, g_off, b_off;
+    int vr_off, vs_off, d_off, bar_off, total;
+};
+
+template <int N, typename T, bool HELM>
+__host__ __device__ constexpr int ax_stage_bytes() {
+    constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
+    return ((NPT * (7 + (HELM ? 1 : 0)) * (int)sizeof(T)) + 15) / 16 * 16;
+}
+
+template <int N, typename T, bool HELM>
+__host__ __device__ constexpr int ax_smem_bytes(int nst) {
+    constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
+    return nst * ax_stage_bytes<N, T, HELM>() + 2 * NPT * (int)sizeof(T) +
+           ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4;
+}
+
+template <int N>
+__host__ __device__ constexpr int ax_threads() {
+    return ((N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
+struct AxArgs {
+    int64_t E;
+    int nst;      // pipeline stages (1..3)
+    int use_tma;  // 1: bulk-copy staging; 0: plain cooperative loads
+    double h1, h2;
+};
+
+template <typename T, typename DM>
+__device__ __forceinline__ const void *dm_ptr(const DM &d) {
+    return d.d;
+}
+
+template <int N, typename T, bool HELM, typename DM>
+__global__ void __launch_bounds__(ax_threads<N>())
+    ax_kernel(const T *__restrict__ u, T *__restrict__ w, const T *__restrict__ G,
+              const double *__restrict__ Bm, const DM Dm, const AxArgs args, int *__restrict__ err) {
+    constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
+    constexpr int SB = ax_stage_bytes<N, T, HELM>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nst = args.nst;
+    T *svr = reinterpret_cast<T *>(smem + nst * SB);
+    T *svs = svr + NPT;
+    T *sD = svs + NPT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + nst * SB + 2 * NPT * sizeof(T) +
+                                                 ((N1 * N1 * sizeof(T) + 15) / 16 * 16));
+    const int tid = threadIdx.x;
+    const bool active = tid < N1 * N1;
+    const int i = tid % N1, j = tid / N1;
+
+    for (int q = tid; q < N1 * N1; q += blockDim.x) sD[q] = (T)Dm.d[q];
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    T rDi[N1], rDj[N1], rDti[N1], rDtj[N1];
+#pragma unroll
+    for (int l = 0; l < N1; ++l) {
+        rDi[l] = active ? sD[i * N1 + l] : T(0);
+        rDj[l] = active ? sD[j * N1 + l] : T(0);
+        rDti[l] = active ? sD[l * N1 + i] : T(0);
+        rDtj[l] = active ? sD[l * N1 + j] : T(0);
+    }
+
+    const int64_t E = args.E;
+    const int64_t stride = gridDim.x;
+    const uint32_t ubytes = NPT * sizeof(T), gbytes = 6 * NPT * sizeof(T);
+    const uint32_t bbytes = HELM ? NPT * sizeof(double) : 0;
+
+    auto stage_ptr = [&](int s) { return smem + s * SB; };
+    auto issue = [&](int64_t e, int s) {
+        unsigned char *st = stage_ptr(s);
+        mbar_arrive_expect_tx(&bar[s], ubytes + gbytes + bbytes);
+        bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
+        bulk_g2s(st + ubytes, G + e * 6 * NPT, gbytes, &bar[s]);
+        if (HELM) bulk_g2s(st + ubytes + gbytes, Bm + e * NPT, bbytes, &bar[s]);
+    };
+
+    if (args.use_tma && tid == 0) {
+        for (int s = 0; s < nst; ++s) {
+            const int64_t e = blockIdx.x + s * stride;
+            if (e < E) issue(e, s);
+        }
+    }
+
+    int it = 0;
+    bool ok = true;
+    for (int64_t e = blockIdx.x; e < E; e += stride, ++it) {
+        const int s = it % nst;
+        const uint32_t parity = (it / nst) & 1;
+        unsigned char *st = stage_ptr(s);
+        if (args.use_tma) {
+            bool mine = mbar_wait_bounded(&bar[s], parity, err, kDevTimeoutTma);
+            ok = __syncthreads_and(mine);
+            if (!ok) break;
+        } else {
+            T *dst = reinterpret_cast<T *>(st);
+            const T *us = u + e * NPT;
+            const T *gs = G + e * 6 * NPT;
+            for (int q = tid; q < NPT; q += blockDim.x) dst[q] = us[q];
+            for (int q = tid; q < 6 * NPT; q += blockDim.x) dst[NPT + q] = gs[q];
+            if (HELM) {
+                double *db = reinterpret_cast<double *>(st + ubytes + gbytes);
+                for (int q = tid; q < NPT; q += blockDim.x) db[q] = Bm[e * NPT + q];
+            }
+            __syncthreads();
+        }
+        const T *su = reinterpret_cast<const T *>(st);
+        const T *sg = su + NPT;
+        const double *sb = reinterpret_cast<const double *>(st + ubytes + gbytes);
+
+        T ru[N1], rvt[N1];
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) ru[k] = su[i + N1 * (j + N1 * k)];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    ur = fma(rDi[l], su[l + N1 * (j + N1 * k)], ur);
+                    us = fma(rDj[l], su[i + N1 * (l + N1 * k)], us);
+                    ut = fma(sD[k * N1 + l], ru[l], ut);
+                }
+                const int p = i + N1 * (j + N1 * k);
+                const T g0 = sg[p], g1 = sg[NPT + p], g2 = sg[2 * NPT + p];
+                const T g3 = sg[3 * NPT + p], g4 = sg[4 * NPT + p], g5 = sg[5 * NPT + p];
+                svr[p] = g0 * ur + g3 * us + g4 * ut;
+                svs[p] = g3 * ur + g1 * us + g5 * ut;
+                rvt[k] = g4 * ur + g5 * us + g2 * ut;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            T *we = w + e * NPT;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                T acc = T(0);
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    acc = fma(rDti[l], svr[l + N1 * (j + N1 * k)], acc);
+                    acc = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], acc);
+                    acc = fma(sD[l * N1 + k], rvt[l], acc);
+                }
+                const int p = i + N1 * (j + N1 * k);
+                if (HELM) acc = (T)(args.h1 * (double)acc + args.h2 * sb[p] * (double)ru[k]);
+                we[p] = acc;
+            }
+        }
+        __syncthreads();  // stage s and svr/svs free again
+        if (args.use_tma && tid == 0) {
+            const int64_t en = e + nst * stride;
+            if (en < E) {
+                fence_proxy_async_smem();
+                issue(en, s);
+            }
+        }
+    }
+    if (!ok && args.use_tma && tid == 0) {
+        // a wait gave up: drain the copies this CTA still has in flight (bounded)
+        for (int s = 0; s < nst; ++s) {
+            const int itn = it + ((s - it % nst) + nst) % nst;
+            const int64_t en = blockIdx.x + (int64_t)itn * stride;
+            if (en < E) mbar_wait_bounded(&bar[s], (itn / nst) & 1, err, kDevTimeoutTma);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launch
+
+template <int N, typename T, bool HELM, typename DM>
+static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
+                       const DM &Dm, cudaStream_t st) {
+    constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
+    constexpr int threads = ax_threads<N>();
+    auto kern = ax_kernel<N, T, HELM, DM>;
+    int dev_max = 0;
+    SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    int nst = 2;
+    while (nst > 1 && ax_smem_bytes<N, T, HELM>(nst) > dev_max) --nst;
+    const int smem = ax_smem_bytes<N, T, HELM>(nst);
+    if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
+    SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)m->num_sms * per_sm;
+    if (grid > m->E) grid = m->E;
+    AxArgs a;
+    a.E = m->E;
+    a.nst = nst;
+    a.h1 = h1;
+    a.h2 = h2;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(G) |
+                           reinterpret_cast<uintptr_t>(m->B)) % 16) == 0;
+    a.use_tma = ((NPT * sizeof(T)) % 16 == 0) && ((NPT * sizeof(double)) % 16 == 0) && aligned;
+    kern<<<(int)grid, threads, smem, st>>>(u, w, G, m->B, Dm, a, m->d_err);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+template <typename T, bool HELM, typename DM>
+static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
+                       const DM &Dm, cudaStream_t st) {
+    switch (m->N) {
+#define SEM_AX_CASE(n) \
+    case n: return launch_ax_n<n, T, HELM, DM>(m, u, w, G, h1, h2, Dm, st);
+        SEM_AX_CASE(1) SEM_AX_CASE(2) SEM_AX_CASE(3) SEM_AX_CASE(4) SEM_AX_CASE(5)
+        SEM_AX_CASE(6) SEM_AX_CASE(7) SEM_AX_CASE(8) SEM_AX_CASE(9) SEM_AX_CASE(10) SEM_AX_CASE(11)
+#undef SEM_AX_CASE
+        default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
+    }
+}
+
+int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2, cudaStream_t st) {
+    if (h2 != 0.0) return dispatch_ax<double, true>(m, u, w, m->G, h1, h2, m->D, st);
+    if (h1 != 1.0) return dispatch_ax<double, true>(m, u, w, m->G, h1, 0.0, m->D, st);
+    return dispatch_ax<double, false>(m, u, w, m->G, 1.0, 0.0, m->D, st);
+}
+
+int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
+    if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
+    return dispatch_ax<float, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, st);
+}
+
+// ---------------------------------------------------------------- Jacobi diagonal
+
+// diag(A_L) at (i,j,k): sum_l D_li^2 G_rr(ljk) + sum_l D_lj^2 G_ss(ilk)
+//   + sum_l D_lk^2 G_tt(ijl) + 2 D_ii D_jj G_rs + 2 D_ii D_kk G_rt + 2 D_jj D_kk G_st.
+__global__ void jacobi_diag_kernel(const double *__restrict__ G, int64_t E, int N, DMat Dm,
+                                   double *__restrict__ diag) {
+    const int n1 = N + 1;
+    const int64_t npt = (int64_t)n1 * n1 * n1;
+    const int64_t nloc = E * npt;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nloc;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = l / npt;
+        const int p = (int)(l - e * npt);
+        const int i = p % n1, j = (p / n1) % n1, k = p / (n1 * n1);
+        const double *Ge = G + e * 6 * npt;
+        double s = 0.0;
+        for (int q = 0; q < n1; ++q) {
+            const double a = Dm.d[q * n1 + i], b = Dm.d[q * n1 + j], c = Dm.d[q * n1 + k];
+            s += a * a * Ge[q + n1 * (j + n1 * k)];
+            s += b * b * Ge[npt + i + n1 * (q + n1 * k)];
+            s += c * c * Ge[2 * npt + i + n1 * (j + n1 * q)];
+        }
+        const double di = Dm.d[i * n1 + i], dj = Dm.d[j * n1 + j], dk = Dm.d[k * n1 + k];
+        s += 2.0 * di * dj * Ge[3 * npt + p] + 2.0 * di * dk * Ge[4 * npt + p] +
+             2.0 * dj * dk * Ge[5 * npt + p];
+        diag[l] = s;
+    }
+}
+
+int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st) {
+    int64_t g = (m->nloc + 255) / 256;
+    if (g > (int64_t)m->num_sms * 64) g = (int64_t)m->num_sms * 64;
+    jacobi_diag_kernel<<<(int)g, 256, 0, st>>>(m->G, m->E, m->N, m->D, diag);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+int sem_ax(const sem_mesh *m, const void *u, void *w, int dtype, void *stream) {
+    if (!m || !u || !w) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (u == w) return fail(SEM_ERR_INVALID_ARG, "u and w must not overlap");
+    if (dtype == SEM_F64)
+        return ax_launch_f64(m, static_cast<const double *>(u), static_cast<double *>(w), 1.0, 0.0,
+                             as_stream(stream));
+    if (dtype == SEM_F32)
+        return ax_launch_f32(m, static_cast<const float *>(u), static_cast<float *>(w), as_stream(stream));
+    return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
+}
+
+int sem_helmholtz(const sem_mesh *m, double h1, double h2, const double *u, double *w, void *stream) {
+    if (!m || !u || !w) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (u == w) return fail(SEM_ERR_INVALID_ARG, "u and w must not overlap");
+    return ax_launch_f64(m, u, w, h1, h2, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// sem_common.cuh -- internal declarations shared by the library's CUDA
+// translation units: the mesh object, error plumbing, and the inline-PTX
+// helpers for the bulk-copy (TMA) + mbarrier pipeline.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/sem.h"
+
+namespace sem {
+
+constexpr int kMaxN = SEM_MAX_ORDER;
+constexpr int kMaxN1 = kMaxN + 1;
+constexpr int kAlign = 256;
+
+// Derivative matrix passed by value to kernels (copied to shared memory).
+struct DMat {
+    double d[kMaxN1 * kMaxN1];  // row-major D[i][j] = l_j'(xi_i)
+};
+struct DMatF {
+    float d[kMaxN1 * kMaxN1];
+};
+
+// Error word values written by kernels into mesh->d_err.
+enum DevErr : int { kDevOk = 0, kDevTimeoutTma = 1, kDevTimeoutFlag = 2 };
+
+}  // namespace sem
+
+struct sem_mesh {
+    int N, n1, npt;
+    int64_t E, nloc, nglob;
+    int nel[3], periodic[3], faces;
+    int geom_flags;
+    // host copies of the 1-D GLL data
+    double xi[sem::kMaxN1], rho[sem::kMaxN1];
+    sem::DMat D;
+    sem::DMatF Df;
+    // device arrays (inside the caller's workspace)
+    double *verts;       // [E][8][3]
+    double *G;           // [E][6][npt]
+    float *G32;          // [E][6][npt] or nullptr
+    double *B;           // [E][npt]
+    double *mult;        // [nloc]
+    double *minv;        // [nloc] 1/mult
+    double *dinv;        // [nloc] inverse assembled Jacobi diagonal (0 on Dirichlet)
+    float *dinv32;       // [nloc] same in FP32 (when G32 built)
+    float *minv32;       // [nloc]
+    int *gs_off;         // [ngroups + 1]
+    int *gs_idx;         // [nentries]
+    int *d_err;          // device error word
+    int64_t ngroups, nmasked, nentries;
+    size_t ws_bytes;
+    int device;
+    int num_sms;
+};
+
+namespace sem {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *where);
+
+#define SEM_CUDA_CHECK(call)                                  \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return sem::cuda_fail(_e, #call); \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- shared PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted in bytes on
+// `bar`.  dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` of global time.
+// On give-up writes `code` into *err (first writer wins) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  int code, uint64_t limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host helpers
+int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
+                  cudaStream_t st);
+int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st);
+int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st);
+int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);
+
+// gather-scatter modes
+constexpr int kGsSum = 0;       // sum copies
+constexpr int kGsSumMask = 1;   // sum copies, then zero Dirichlet nodes
+constexpr int kGsMaskOnly = 2;  // zero Dirichlet nodes only
+
+}  // namespace sem
