@@ -1,0 +1,358 @@
+"""Benchmark of the SEM pressure-Poisson hot path on GB300.
+
+One step = one Jacobi-PCG solve to relative residual 1e-8 of the channel
+workload: 32 x 32 x 32 hexahedra, N = 7 (16.8 M element-local points,
+n = E N^3 = 11.2 M), tanh wall-normal stretching (beta = 2), periodic in x and
+z, Dirichlet walls in y, right-hand side i.i.d. U[-1, 1] on the global nodes,
+zero-mean.  The mesh, its geometric factors and the right-hand side are
+resident in HBM before the timed region; every step solves from x0 = 0.
+
+value  = n * CG iterations / step time   (operator applications, GDOF/s)
+e2e    = the same through sem_pcg_solve_host: b copied host->device and x
+         device->host inside the timed region.
+roofline = the operator kernel: 64 algorithmic bytes per local point (u 8,
+         G 48, w 8) per launch / its mean duration from CUDA events recorded
+         on the launching stream inside the timed solves.
+
+`--impl reference` times the FP64 CPU oracle on this machine's host cores on
+a bounded sample of the same workload (a few CG iterations per step).
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun every rank solves its own replica (weak scaling, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ax GDOF/s (% HBM roofline); PCG time-to-1e-8 residual, plain FP64 vs chosen"
+UNIT = "GDOF/s"
+WORKLOAD = "channel 32x32x32 hex, N=7, tanh beta=2 in y, periodic x/z, Dirichlet y, random mean-zero RHS"
+TOL = 1e-8
+AX_BYTES_PER_POINT = {"f64": 64}
+
+# DRAM traffic per launch of the operator kernel from one ncu capture (bytes),
+# keyed by the SHA-256 of the kernel source it was taken on; null once the
+# source changes.
+NCU_TRAFFIC = {"ax_f64": {"bytes_per_launch": 1029.0e6, "src_sha": "e66fd15511053f11",
+                          "from": "profiles/ax_f64_n7_nel20_ncu_full.md (20^3 case scaled x4.096)"}}
+
+
+def _src_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--nel", type=int, default=32)
+    p.add_argument("--order", type=int, default=7)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations in the CPU sample")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device="cpu") -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+
+def cpu_oracle_sample(case, iters, verts=None):
+    """Time `iters` oracle CG iterations on the full workload (FP64, 1 thread).
+    Returns (GDOF/s, seconds, description)."""
+    import numpy as np
+
+    import oracle
+    V = case.vertices() if verts is None else verts
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    t0 = time.perf_counter()
+    _, it, _, _ = om.pcg(b, tol=1e-30, max_iter=iters)
+    dt = time.perf_counter() - t0
+    gdofs = case.n_paper * it / dt / 1e9
+    return gdofs, dt, f"{it} FP64 oracle CG iterations on the full {case.E}-element workload ({dt:.1f} s)", om, b
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2405_05640_gb300 import binding, inputs
+    from paper_2405_05640_gb300 import build as _build
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist_init("nccl")
+    _build.build()
+    case = inputs.channel(args.nel, args.order)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    bg = torch.from_numpy(case.rhs_global()).cuda()
+    b = gm.scatter(bg)
+    x = torch.zeros_like(b)
+    opts_kw = dict(tol=TOL, max_iter=50000, check_every=32)
+    scratch = gm.pcg_scratch(gm.pcg_opts(**opts_kw))
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        gm.pcg(b, scratch=scratch, **opts_kw)
+    torch.cuda.synchronize()
+    barrier()
+    iters, ax_ms, ax_n, launches, gs_ms = 0, 0.0, 0, 0, 0.0
+    stats = None
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, stats = gm.pcg(b, scratch=scratch, profile=True, **opts_kw)
+            iters += stats["iters"]
+            ax_ms += stats["ax_ms"]
+            gs_ms += stats["gs_ms"]
+            ax_n += stats["ax_launches"]
+            launches += stats["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    barrier()
+    t_max = max_over_ranks(elapsed_ms / 1e3, device="cuda")
+    tot_iters = sum_over_ranks(float(iters), device="cuda")
+    value = case.n_paper * tot_iters / t_max / 1e9
+    ms_per_step = t_max * 1e3 / args.steps
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.empty(case.nloc, dtype=torch.float64, pin_memory=True)
+        hb.copy_(b.cpu())
+        hx = torch.empty(case.nloc, dtype=torch.float64, pin_memory=True)
+        hscr = gm.pcg_host_scratch(gm.pcg_opts(**opts_kw))
+        gm.pcg_host(hb, hx, scratch=hscr, **opts_kw)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(args.steps):
+            _, s2 = gm.pcg_host(hb, hx, scratch=hscr, **opts_kw)
+            e_iters += s2["iters"]
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, device="cuda")
+        e_iters = sum_over_ranks(float(e_iters), device="cuda")
+        e2e = {"value": case.n_paper * e_iters / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
+               "ms_per_step": te * 1e3 / args.steps}
+
+    peaks = measured_peaks()
+    ax_avg_ms = ax_ms / max(ax_n, 1)
+    algo_bytes = AX_BYTES_PER_POINT["f64"] * case.nloc
+    achieved = algo_bytes / (ax_avg_ms * 1e-3) / 1e9
+    sha = _src_sha(os.path.join(ROOT, "paper_2405_05640_gb300", "csrc", "sem_ax.cu"))
+    tr = NCU_TRAFFIC.get("ax_f64")
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha else None
+    roofline = {"kernel": "ax_kernel<7,double> (FP64 operator)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": traffic, "peak_source": peaks["source"] + " hbm_gbs",
+                "algorithmic_bytes_per_launch": algo_bytes, "mean_launch_ms": round(ax_avg_ms, 4),
+                "note": "FP64 ALU-bound on GB300 (1.26 TFLOP/s FP64 measured): see fp64_alu"}
+    # the FP64 pipe bound for the same kernel: 57 FMA per local point
+    flops = 2 * 57 * case.nloc
+    roofline["fp64_alu"] = {"achieved_tflops": round(flops / (ax_avg_ms * 1e-3) / 1e12, 3), "peak_tflops": 1.257,
+                            "peak_source": "measured FMA-chain probe on GB300"}
+    rec = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "E": case.E, "N": case.N, "n_paper": case.n_paper,
+                   "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL, "precision": "plain FP64 Jacobi-PCG",
+                   "l2": "inputs larger than L2 (G alone 805 MB)", "parallelism": f"replicas x{world}"},
+        "pcg": {"iters_per_solve": iters / args.steps, "time_to_1e-8_ms": round(ms_per_step, 3),
+                "rel_res": stats["rel_res"] if stats else None, "status": stats["status"] if stats else None,
+                "gs_ms_per_launch": round(gs_ms / max(ax_n, 1), 4)},
+        "ax_kernel_gdofs": round(case.n_paper / (ax_avg_ms * 1e-3) / 1e9, 3),
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, dt, desc, _, _ = cpu_oracle_sample(case, args.cpu_iters, V)
+        rec["cpu_baseline"] = {"value": round(g, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(rec), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2405_05640_gb300 import inputs
+    case = inputs.channel(args.nel, args.order)
+    import oracle
+    V = case.vertices()
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    per_step = 1  # CG iterations per timed step (bounded sample of one solve)
+    for _ in range(args.warmup):
+        om.pcg(b, tol=1e-30, max_iter=per_step)
+    t0 = time.perf_counter()
+    it_total = 0
+    for _ in range(args.steps):
+        _, it, _, _ = om.pcg(b, tol=1e-30, max_iter=per_step)
+        it_total += it
+    dt = time.perf_counter() - t0
+    value = case.n_paper * it_total / dt / 1e9
+    desc = f"{per_step} FP64 oracle CG iteration(s) per step on the full {case.E}-element workload, 1 thread"
+    rec = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "E": case.E, "N": case.N,
+                                           "n_paper": case.n_paper, "tol": TOL, "precision": "FP64 oracle"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -165,6 +165,8 @@ typedef struct {
     double h1, h2;         /* operator h1 A + h2 B; Poisson: h1 = 1, h2 = 0 */
     int check_every;       /* iterations between host convergence checks (0 = 16) */
     int use_initial_guess; /* 1: x holds x0 on entry; 0: start from x = 0 */
+    int profile;           /* 1: time the operator kernels with CUDA events
+                              recorded on `stream` (fills ax_ms / gs_ms) */
 } sem_pcg_opts;
 
 typedef struct {
@@ -175,6 +177,10 @@ typedef struct {
     double abs_res;        /* final ||r|| */
     double bnorm;          /* ||b|| */
     double wall_ms;        /* host wall time of the call */
+    double ax_ms;          /* profile: summed device time of operator kernels */
+    double gs_ms;          /* profile: summed device time of gather-scatter kernels */
+    int ax_launches;       /* operator kernel launches */
+    int kernel_launches;   /* all kernel launches of the call */
 } sem_pcg_stats;
 
 /* Scratch bytes sem_pcg_solve needs (device). */
@@ -187,6 +193,14 @@ size_t sem_pcg_scratch_bytes(const sem_mesh *mesh, const sem_pcg_opts *opts);
  * SEM_ERR_NAN, SEM_ERR_WORKSPACE, SEM_ERR_TIMEOUT or SEM_ERR_CUDA. */
 int sem_pcg_solve(const sem_mesh *mesh, const double *b, double *x, const sem_pcg_opts *opts,
                   sem_pcg_stats *stats, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* The same solve with HOST buffers: copies b (host, nloc doubles; pinned
+ * memory makes the copy asynchronous) to the device, solves, and copies the
+ * solution back to x (host; its contents on entry are the initial guess when
+ * use_initial_guess).  d_scratch must hold sem_pcg_host_scratch_bytes. */
+size_t sem_pcg_host_scratch_bytes(const sem_mesh *mesh, const sem_pcg_opts *opts);
+int sem_pcg_solve_host(const sem_mesh *mesh, const double *h_b, double *h_x, const sem_pcg_opts *opts,
+                       sem_pcg_stats *stats, void *d_scratch, size_t scratch_bytes, void *stream);
 
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */

@@ -46,13 +46,15 @@ class MeshInfo(ctypes.Structure):
 class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_is_relative", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
-                ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int)]
+                ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class PcgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("wall_ms", ctypes.c_double)]
+                ("wall_ms", ctypes.c_double), ("ax_ms", ctypes.c_double), ("gs_ms", ctypes.c_double),
+                ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +79,9 @@ _SIGS = {
     "sem_pcg_scratch_bytes": ([_VP, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
     "sem_pcg_solve": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t,
                        _VP], ctypes.c_int),
+    "sem_pcg_host_scratch_bytes": ([_VP, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
+    "sem_pcg_solve_host": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP,
+                            ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
 }
 
@@ -213,8 +218,9 @@ class Mesh:
         return float(self._res.item())
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
-                 check_every=16, use_initial_guess=False, relative=True) -> PcgOpts:
+                 check_every=16, use_initial_guess=False, relative=True, profile=False) -> PcgOpts:
         o = PcgOpts()
+        o.profile = int(bool(profile))
         o.tol, o.tol_is_relative, o.max_iter, o.precision = float(tol), int(relative), int(max_iter), int(precision)
         o.inner_tol, o.h1, o.h2 = float(inner_tol), float(h1), float(h2)
         o.check_every, o.use_initial_guess = int(check_every), int(bool(use_initial_guess))
@@ -241,6 +247,26 @@ class Mesh:
         if raise_on_error and status not in (SEM_OK,):
             raise SemError(status, "sem_pcg_solve")
         return x, st.as_dict()
+
+    def pcg_host_scratch(self, opts: PcgOpts):
+        import torch
+        n = lib().sem_pcg_host_scratch_bytes(self.handle, ctypes.byref(opts))
+        return torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+
+    def pcg_host(self, b_host, x_host, scratch=None, raise_on_error=True, use_initial_guess=False, **kw):
+        """sem_pcg_solve_host: b_host / x_host are CPU float64 tensors (pinned
+        for asynchronous copies); the solution is written into x_host."""
+        opts = self.pcg_opts(use_initial_guess=use_initial_guess, **kw)
+        if scratch is None:
+            scratch = self.pcg_host_scratch(opts)
+        base = (scratch.data_ptr() + 255) // 256 * 256
+        nbytes = scratch.numel() - (base - scratch.data_ptr())
+        st = PcgStats()
+        status = lib().sem_pcg_solve_host(self.handle, _ptr(b_host), _ptr(x_host), ctypes.byref(opts),
+                                          ctypes.byref(st), _VP(base), nbytes, _stream())
+        if raise_on_error and status != SEM_OK:
+            raise SemError(status, "sem_pcg_solve_host")
+        return x_host, st.as_dict()
 
     def check_device_error(self) -> int:
         c = ctypes.c_int()

@@ -21,6 +21,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 #include "sem_common.cuh"
 
@@ -211,12 +212,118 @@ static PcgWork carve(const sem_mesh *m, void *scratch) {
     return W;
 }
 
-// Assembled operator y = M Q Q^T (h1 A_L + h2 B) x (FP64).
-static int apply_assembled(const sem_mesh *m, const double *x, double *y, double h1, double h2,
-                           cudaStream_t st) {
+// Event pairs recorded on the launching stream around selected kernels;
+// harvested after each host synchronisation.
+struct EvTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    double total_ms = 0.0;
+    int init(bool enable, int pairs) {
+        on = enable;
+        if (!on) return SEM_OK;
+        ev.resize(2 * pairs);
+        for (auto &e : ev) SEM_CUDA_CHECK(cudaEventCreate(&e));
+        return SEM_OK;
+    }
+    void start(cudaStream_t st) {
+        if (on && used < (int)ev.size() / 2) cudaEventRecord(ev[2 * used], st);
+    }
+    void stop(cudaStream_t st) {
+        if (on && used < (int)ev.size() / 2) cudaEventRecord(ev[2 * used + 1], st), ++used;
+    }
+    void harvest() {
+        for (int q = 0; q < used; ++q) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]) == cudaSuccess) total_ms += ms;
+        }
+        used = 0;
+    }
+    ~EvTimer() {
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+struct SolveCtx {
+    EvTimer tax, tgs;
+    int launches = 0, ax_launches = 0;
+};
+
+static int apply_assembled_timed(const sem_mesh *m, const double *x, double *y, double h1, double h2,
+                                 cudaStream_t st, SolveCtx &c) {
+    c.tax.start(st);
     int s = ax_launch_f64(m, x, y, h1, h2, st);
+    c.tax.stop(st);
     if (s != SEM_OK) return s;
-    return gs_launch(m, y, SEM_F64, kGsSumMask, st);
+    c.tgs.start(st);
+    s = gs_launch(m, y, SEM_F64, kGsSumMask, st);
+    c.tgs.stop(st);
+    c.launches += 2;
+    c.ax_launches += 1;
+    return s;
+}
+
+static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
+                   void *scratch, cudaStream_t st) {
+    PcgWork W = carve(m, scratch);
+    const int64_t n = m->nloc;
+    const int check = o->check_every > 0 ? o->check_every : 16;
+    SolveCtx c;
+    int s0 = c.tax.init(o->profile != 0, check + 1);
+    if (s0 == SEM_OK) s0 = c.tgs.init(o->profile != 0, check + 1);
+    if (s0 != SEM_OK) return s0;
+    SEM_CUDA_CHECK(cudaMemsetAsync(W.scal, 0, sizeof(PcgScal), st));
+    const double *ax0 = nullptr;
+    if (o->use_initial_guess) {
+        int s = apply_assembled_timed(m, x, W.w, o->h1, o->h2, st, c);
+        if (s != SEM_OK) return s;
+        ax0 = W.w;
+    } else {
+        SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    }
+    pcg_init_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, ax0, m->dinv, m->minv, n, W, o->tol,
+                                                    o->tol_is_relative, o->max_iter);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    c.launches += 1;
+    PcgScal h{};
+    int launched = 0;
+    while (true) {
+        SEM_CUDA_CHECK(cudaMemcpyAsync(&h, W.scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        c.tax.harvest();
+        c.tgs.harvest();
+        if (h.done || launched >= o->max_iter) break;
+        for (int q = 0; q < check && launched < o->max_iter; ++q, ++launched) {
+            int s = apply_assembled_timed(m, W.p, W.w, o->h1, o->h2, st, c);
+            if (s != SEM_OK) return s;
+            pcg_pw_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->minv, n, W);
+            pcg_update_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, m->dinv, m->minv, n, W);
+            pcg_p_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->dinv, n, W);
+            SEM_CUDA_CHECK(cudaGetLastError());
+            c.launches += 3;
+        }
+    }
+    int derr = 0;
+    SEM_CUDA_CHECK(cudaMemcpyAsync(&derr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+    stats->iters = h.iter;
+    stats->outer_iters = 0;
+    stats->bnorm = std::sqrt(h.bb);
+    stats->abs_res = std::sqrt(h.rr);
+    stats->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : stats->abs_res;
+    stats->ax_ms = c.tax.total_ms;
+    stats->gs_ms = c.tgs.total_ms;
+    stats->ax_launches = c.ax_launches;
+    stats->kernel_launches = c.launches;
+    int status = h.done ? h.status : SEM_ERR_NOT_CONVERGED;
+    if (derr != 0) status = SEM_ERR_TIMEOUT;
+    return status;
+}
+
+static int check_opts(const sem_pcg_opts *o) {
+    if (o->precision != SEM_PCG_F64) return fail(SEM_ERR_UNSUPPORTED, "precision mode not built");
+    if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
+    return SEM_OK;
 }
 
 }  // namespace sem
@@ -231,59 +338,54 @@ size_t sem_pcg_scratch_bytes(const sem_mesh *m, const sem_pcg_opts *o) {
     return pcg_scratch(m);
 }
 
+size_t sem_pcg_host_scratch_bytes(const sem_mesh *m, const sem_pcg_opts *o) {
+    if (!m) return 0;
+    return sem_pcg_scratch_bytes(m, o) + 2 * align_up(sizeof(double) * m->nloc);
+}
+
 int sem_pcg_solve(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
                   void *scratch, size_t scratch_bytes, void *stream) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!m || !b || !x || !o || !stats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
-    if (o->precision != SEM_PCG_F64) return fail(SEM_ERR_UNSUPPORTED, "precision mode not built");
-    if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
-    if (scratch_bytes < pcg_scratch(m) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
+    *stats = sem_pcg_stats{};
+    int s = check_opts(o);
+    if (s != SEM_OK) return s;
+    if (scratch_bytes < sem_pcg_scratch_bytes(m, o) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
         return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_scratch_bytes or not 256-byte aligned");
-    cudaStream_t st = as_stream(stream);
-    PcgWork W = carve(m, scratch);
-    const int64_t n = m->nloc;
-    const int check = o->check_every > 0 ? o->check_every : 16;
-    SEM_CUDA_CHECK(cudaMemsetAsync(W.scal, 0, sizeof(PcgScal), st));
-    const double *ax0 = nullptr;
-    if (o->use_initial_guess) {
-        int s = apply_assembled(m, x, W.w, o->h1, o->h2, st);
-        if (s != SEM_OK) return s;
-        ax0 = W.w;
-    } else {
-        SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    }
-    pcg_init_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, ax0, m->dinv, m->minv, n, W, o->tol,
-                                                    o->tol_is_relative, o->max_iter);
-    SEM_CUDA_CHECK(cudaGetLastError());
-    PcgScal h{};
-    int launched = 0;
-    while (true) {
-        SEM_CUDA_CHECK(cudaMemcpyAsync(&h, W.scal, sizeof(h), cudaMemcpyDeviceToHost, st));
-        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
-        if (h.done || launched >= o->max_iter) break;
-        for (int c = 0; c < check && launched < o->max_iter; ++c, ++launched) {
-            int s = apply_assembled(m, W.p, W.w, o->h1, o->h2, st);
-            if (s != SEM_OK) return s;
-            pcg_pw_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->minv, n, W);
-            pcg_update_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, m->dinv, m->minv, n, W);
-            pcg_p_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->dinv, n, W);
-            SEM_CUDA_CHECK(cudaGetLastError());
-        }
-    }
-    int derr = 0;
-    SEM_CUDA_CHECK(cudaMemcpyAsync(&derr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SEM_CUDA_CHECK(cudaStreamSynchronize(st));
-    stats->iters = h.iter;
-    stats->outer_iters = 0;
-    stats->bnorm = std::sqrt(h.bb);
-    stats->abs_res = std::sqrt(h.rr);
-    stats->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : stats->abs_res;
-    int status = h.done ? h.status : SEM_ERR_NOT_CONVERGED;
-    if (derr != 0) status = SEM_ERR_TIMEOUT;
-    stats->status = status;
+    s = pcg_f64(m, b, x, o, stats, scratch, as_stream(stream));
+    stats->status = s;
     stats->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (status != SEM_OK) set_error(sem_status_string(status));
-    return status;
+    if (s != SEM_OK && s != SEM_ERR_CUDA) set_error(sem_status_string(s));
+    return s;
+}
+
+int sem_pcg_solve_host(const sem_mesh *m, const double *hb, double *hx, const sem_pcg_opts *o,
+                       sem_pcg_stats *stats, void *scratch, size_t scratch_bytes, void *stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!m || !hb || !hx || !o || !stats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    *stats = sem_pcg_stats{};
+    int s = check_opts(o);
+    if (s != SEM_OK) return s;
+    if (scratch_bytes < sem_pcg_host_scratch_bytes(m, o) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
+        return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_host_scratch_bytes or not 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    const size_t vb = align_up(sizeof(double) * m->nloc);
+    char *p = static_cast<char *>(scratch);
+    double *db = reinterpret_cast<double *>(p);
+    double *dx = reinterpret_cast<double *>(p + vb);
+    void *inner = p + 2 * vb;
+    SEM_CUDA_CHECK(cudaMemcpyAsync(db, hb, sizeof(double) * m->nloc, cudaMemcpyHostToDevice, st));
+    if (o->use_initial_guess)
+        SEM_CUDA_CHECK(cudaMemcpyAsync(dx, hx, sizeof(double) * m->nloc, cudaMemcpyHostToDevice, st));
+    s = pcg_f64(m, db, dx, o, stats, inner, st);
+    if (s == SEM_OK || s == SEM_ERR_NOT_CONVERGED) {
+        SEM_CUDA_CHECK(cudaMemcpyAsync(hx, dx, sizeof(double) * m->nloc, cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+    }
+    stats->status = s;
+    stats->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (s != SEM_OK && s != SEM_ERR_CUDA) set_error(sem_status_string(s));
+    return s;
 }
 
 }  // extern "C"
