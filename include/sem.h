@@ -145,6 +145,29 @@ int sem_scatter(const sem_mesh *mesh, const double *u_glob, double *u_loc, void 
 int sem_glsc3(const sem_mesh *mesh, const double *a, const double *b, double *d_result,
               void *d_scratch, size_t scratch_bytes, void *stream);
 
+/* sem_glsc3 without a scratch argument, for callers that cannot allocate
+ * device memory: host codes whose device memory is owned by their own pool
+ * or framework allocator (a library must not allocate behind it), fixed-
+ * budget embedded or plugin contexts, and time-step loops that cannot take
+ * the implicit device synchronisation or the failure point of cudaMalloc /
+ * cudaFree.  The paper has no counterpart; this is a library convenience.
+ *  - Scratch: a file-scope device array of 8448 bytes (1024 block partials
+ *    and a counter), held by every device that loads the library until the
+ *    process exits.  The reduction always runs 1024 blocks, so any mesh the
+ *    library accepts fits; the call still checks the need against the array
+ *    and rejects it with SEM_ERR_WORKSPACE, and rejects nloc >= 2^31 with
+ *    SEM_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and give wrong results; serialise
+ *    them.  The counter is cleared on every call.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called.
+ * Result and arguments as sem_glsc3. */
+int sem_glsc3_noalloc(const sem_mesh *mesh, const double *a, const double *b, double *d_result,
+                      void *stream);
+
 /* Jacobi-preconditioned conjugate gradients on the assembled system
  * M Q Q^T (h1 A_L + h2 B) x = b (M: Dirichlet mask).  b must be continuous
  * and zero on Dirichlet nodes.  Stops when ||r|| <= tol ||b|| (tol_is_

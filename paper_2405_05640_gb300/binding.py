@@ -76,6 +76,7 @@ _SIGS = {
     "sem_dssum": ([_VP, _VP, ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
     "sem_scatter": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_glsc3": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_glsc3_noalloc": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_pcg_scratch_bytes": ([_VP, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
     "sem_pcg_solve": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t,
                        _VP], ctypes.c_int),
@@ -215,6 +216,12 @@ class Mesh:
         base = (self._red.data_ptr() + 255) // 256 * 256
         check(lib().sem_glsc3(self.handle, _ptr(a), _ptr(b), _ptr(self._res), _VP(base), 1024 * 8 + 64,
                               _stream()), "sem_glsc3")
+        return float(self._res.item())
+
+    def glsc3_noalloc(self, a, b) -> float:
+        """sem_glsc3_noalloc: the same product with the library's static scratch."""
+        check(lib().sem_glsc3_noalloc(self.handle, _ptr(a), _ptr(b), _ptr(self._res), _stream()),
+              "sem_glsc3_noalloc")
         return float(self._res.item())
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,

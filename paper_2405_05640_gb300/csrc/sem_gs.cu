@@ -14,6 +14,8 @@
 // its copies in ascending local index (deterministic; every copy receives
 // bit-identical values) and writes the sum back.
 
+#include <mutex>
+
 #include "sem_common.cuh"
 
 namespace sem {
@@ -120,6 +122,36 @@ __global__ void __launch_bounds__(kRedThreads)
     }
 }
 
+// ---- allocation-free inner product ------------------------------------
+// Scratch of sem_glsc3_noalloc: the 1024 block partials and the arrival
+// counter of glsc3_kernel, in a file-scope device array.  Every device that
+// loads the library holds these bytes until the process exits.
+constexpr size_t kNoAllocScratchBytes = 8448;  // 1024 doubles + counter, rounded to 256
+static_assert(sizeof(double) * kRedBlocks + sizeof(unsigned) <= kNoAllocScratchBytes,
+              "static scratch too small for the reduction");
+static __device__ __align__(256) unsigned char g_glsc3_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static void *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+static std::mutex g_noalloc_mutex;
+
+// The array's name is only a host-side stand-in; its device address must be
+// looked up once per device with that device current.
+static int noalloc_scratch_for_current_device(void **out) {
+    int dev = 0;
+    SEM_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SEM_ERR_UNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_glsc3_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_glsc3_noalloc_scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SEM_OK;
+}
+
 }  // namespace sem
 
 using namespace sem;
@@ -153,6 +185,31 @@ int sem_glsc3(const sem_mesh *m, const double *a, const double *b, double *d_res
     double *partial = static_cast<double *>(d_scratch);
     unsigned *counter = reinterpret_cast<unsigned *>(partial + kRedBlocks);
     cudaStream_t st = as_stream(stream);
+    SEM_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    glsc3_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, m->minv, m->nloc, partial, counter, d_result);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+// Same reduction as sem_glsc3, with its scratch in g_glsc3_noalloc_scratch
+// instead of a caller buffer; no cudaMalloc, cudaFree or allocating library
+// call.  The first call on a device looks up the array's device address.
+int sem_glsc3_noalloc(const sem_mesh *m, const double *a, const double *b, double *d_result, void *stream) {
+    if (!m || !a || !b || !d_result) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = sizeof(double) * kRedBlocks + sizeof(unsigned);
+    if (need > kNoAllocScratchBytes)
+        return fail(SEM_ERR_WORKSPACE, "sem_glsc3_noalloc: reduction needs " + std::to_string(need) +
+                                           " bytes, static scratch holds " + std::to_string(kNoAllocScratchBytes));
+    if (m->nloc >= (int64_t(1) << 31))
+        return fail(SEM_ERR_INVALID_ARG, "sem_glsc3_noalloc: more than 2^31-1 points");
+    void *scratch = nullptr;
+    int s = noalloc_scratch_for_current_device(&scratch);
+    if (s != SEM_OK) return s;
+    double *partial = static_cast<double *>(scratch);
+    unsigned *counter = reinterpret_cast<unsigned *>(partial + kRedBlocks);
+    cudaStream_t st = as_stream(stream);
+    // the counter must start at 0 (a previous call leaves it at 0, but a
+    // call cut short would not): clear it every time
     SEM_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
     glsc3_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, m->minv, m->nloc, partial, counter, d_result);
     SEM_CUDA_CHECK(cudaGetLastError());
