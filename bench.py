@@ -1,18 +1,21 @@
 """Benchmark of the SEM pressure-Poisson hot path on GB300.
 
-One step = one Jacobi-PCG solve to relative residual 1e-8 of the channel
+One step = one solve to relative residual 1e-8 (FP64 residual) of the channel
 workload: 32 x 32 x 32 hexahedra, N = 7 (16.8 M element-local points,
 n = E N^3 = 11.2 M), tanh wall-normal stretching (beta = 2), periodic in x and
 z, Dirichlet walls in y, right-hand side i.i.d. U[-1, 1] on the global nodes,
 zero-mean.  The mesh, its geometric factors and the right-hand side are
-resident in HBM before the timed region; every step solves from x0 = 0.
+resident in HBM before the timed region; every step solves from x0 = 0 with
+the chosen solver: FP64 iterative refinement around FP32 Jacobi-PCG.  The
+plain FP64 Jacobi-PCG solve is timed beside it on the same GPU.
 
 value  = n * CG iterations / step time   (operator applications, GDOF/s)
 e2e    = the same through sem_pcg_solve_host: b copied host->device and x
          device->host inside the timed region.
-roofline = the operator kernel: 64 algorithmic bytes per local point (u 8,
-         G 48, w 8) per launch / its mean duration from CUDA events recorded
-         on the launching stream inside the timed solves.
+roofline = the fused FP32 operator kernel (the step's dominant kernel): 44
+         algorithmic bytes per local point per launch / its mean duration
+         from CUDA events recorded on the launching stream inside the timed
+         solves.
 
 `--impl reference` times the FP64 CPU oracle on this machine's host cores on
 a bounded sample of the same workload (a few CG iterations per step).
@@ -45,8 +48,8 @@ AX_BYTES_PER_POINT = {"f64": 64}
 # DRAM traffic per launch of the operator kernel from one ncu capture (bytes),
 # keyed by the SHA-256 of the kernel source it was taken on; null once the
 # source changes.
-NCU_TRAFFIC = {"ax_f64": {"bytes_per_launch": 1029.0e6, "src_sha": "e66fd15511053f11",
-                          "from": "profiles/ax_f64_n7_nel20_ncu_full.md (20^3 case scaled x4.096)"}}
+NCU_TRAFFIC = {"ax_f32_cg": {"bytes_per_launch": 664.0e6, "src_sha": "6a9970ea35dbd9a2",
+                             "from": "profiles/ax_f32cg_n7_nel20_ncu_full.md (20^3 case scaled x4.096)"}}
 
 
 def _src_sha(path):
@@ -65,6 +68,9 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations in the CPU sample")
+    p.add_argument("--plain-steps", type=int, default=2, help="plain FP64 solves timed for comparison")
+    p.add_argument("--op", choices=["ax-f64", "ax-f32", "dssum-f64", "dssum-f32"], default=None,
+                   help="time one entry point alone instead of the solve")
     return p.parse_args(argv)
 
 
@@ -203,9 +209,31 @@ def cpu_oracle_sample(case, iters, verts=None):
 
 # ------------------------------------------------------------------ our arm
 
+# Algorithmic bytes per local point of the operator kernels:
+#   fused FP32 CG operator: reads r, dinv, p (4 B each) and G (6 x 4 B),
+#     writes p and w (4 B each) = 44 B;
+#   FP64 operator: reads u (8 B) and G (6 x 8 B), writes w (8 B) = 64 B.
+OP_BYTES = {"f32_cg": 44, "f64": 64, "f64_cg": 64 + 16 + 8}
+CHOSEN = dict(precision=1, inner_tol=1e-2)   # FP64 refinement around FP32 Jacobi-PCG
+PLAIN = dict(precision=0)
+
+
+def _solve_series(gm, b, scratch, steps, opts, profile=True):
+    iters, ax_ms, ax_n, launches, outer_ms, outer_n = 0, 0.0, 0, 0, 0.0, 0
+    stats = None
+    for _ in range(steps):
+        _, stats = gm.pcg(b, scratch=scratch, profile=profile, **opts)
+        iters += stats["iters"]
+        ax_ms += stats["ax_ms"]
+        ax_n += stats["ax_launches"]
+        launches += stats["kernel_launches"]
+        outer_ms += stats["outer_ax_ms"]
+        outer_n += stats["outer_ax_launches"]
+    return dict(iters=iters, ax_ms=ax_ms, ax_n=ax_n, launches=launches, outer_ms=outer_ms, outer_n=outer_n,
+                last=stats)
+
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_2405_05640_gb300 import binding, inputs
@@ -217,91 +245,111 @@ def run_ours(args):
     _build.build()
     case = inputs.channel(args.nel, args.order)
     V = case.vertices()
-    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
     bg = torch.from_numpy(case.rhs_global()).cuda()
     b = gm.scatter(bg)
-    x = torch.zeros_like(b)
-    opts_kw = dict(tol=TOL, max_iter=50000, check_every=32)
-    scratch = gm.pcg_scratch(gm.pcg_opts(**opts_kw))
+    base = dict(tol=TOL, max_iter=50000, check_every=32)
+    chosen = dict(base, **CHOSEN)
+    plain = dict(base, **PLAIN)
+    scratch = gm.pcg_scratch(gm.pcg_opts(**chosen))
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        gm.pcg(b, scratch=scratch, **opts_kw)
+        gm.pcg(b, scratch=scratch, **chosen)
     torch.cuda.synchronize()
     barrier()
-    iters, ax_ms, ax_n, launches, gs_ms = 0, 0.0, 0, 0, 0.0
-    stats = None
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
-            _, stats = gm.pcg(b, scratch=scratch, profile=True, **opts_kw)
-            iters += stats["iters"]
-            ax_ms += stats["ax_ms"]
-            gs_ms += stats["gs_ms"]
-            ax_n += stats["ax_launches"]
-            launches += stats["kernel_launches"]
+        ser = _solve_series(gm, b, scratch, args.steps, chosen)
         e1.record(stream)
         torch.cuda.synchronize()
     elapsed_ms = e0.elapsed_time(e1)
     barrier()
     t_max = max_over_ranks(elapsed_ms / 1e3, device="cuda")
-    tot_iters = sum_over_ranks(float(iters), device="cuda")
+    tot_iters = sum_over_ranks(float(ser["iters"]), device="cuda")
     value = case.n_paper * tot_iters / t_max / 1e9
     ms_per_step = t_max * 1e3 / args.steps
 
-    # end to end through the host-buffer entry point
+    # the plain FP64 solve on the same GPU, same mesh and right-hand side
+    gm.pcg(b, scratch=scratch, **plain)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    pser = _solve_series(gm, b, scratch, args.plain_steps, plain)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1) / args.plain_steps
+
+    # end to end through the host-buffer entry point (chosen solver)
     e2e = None
     if not args.no_e2e:
         hb = torch.empty(case.nloc, dtype=torch.float64, pin_memory=True)
         hb.copy_(b.cpu())
         hx = torch.empty(case.nloc, dtype=torch.float64, pin_memory=True)
-        hscr = gm.pcg_host_scratch(gm.pcg_opts(**opts_kw))
-        gm.pcg_host(hb, hx, scratch=hscr, **opts_kw)
+        hscr = gm.pcg_host_scratch(gm.pcg_opts(**chosen))
+        gm.pcg_host(hb, hx, scratch=hscr, **chosen)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(args.steps):
-            _, s2 = gm.pcg_host(hb, hx, scratch=hscr, **opts_kw)
+            _, s2 = gm.pcg_host(hb, hx, scratch=hscr, **chosen)
             e_iters += s2["iters"]
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, device="cuda")
         e_iters = sum_over_ranks(float(e_iters), device="cuda")
-        e2e = {"value": case.n_paper * e_iters / te / 1e9, "unit": UNIT,
+        e2e = {"value": round(case.n_paper * e_iters / te / 1e9, 4), "unit": UNIT,
                "h2d_bytes_per_step": int(hb.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8),
-               "ms_per_step": te * 1e3 / args.steps}
+               "ms_per_step": round(te * 1e3 / args.steps, 3)}
 
     peaks = measured_peaks()
-    ax_avg_ms = ax_ms / max(ax_n, 1)
-    algo_bytes = AX_BYTES_PER_POINT["f64"] * case.nloc
+    ax_avg_ms = ser["ax_ms"] / max(ser["ax_n"], 1)
+    algo_bytes = OP_BYTES["f32_cg"] * case.nloc
     achieved = algo_bytes / (ax_avg_ms * 1e-3) / 1e9
     sha = _src_sha(os.path.join(ROOT, "paper_2405_05640_gb300", "csrc", "sem_ax.cu"))
-    tr = NCU_TRAFFIC.get("ax_f64")
+    tr = NCU_TRAFFIC.get("ax_f32_cg")
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha else None
-    roofline = {"kernel": "ax_kernel<7,double> (FP64 operator)", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": traffic, "peak_source": peaks["source"] + " hbm_gbs",
-                "algorithmic_bytes_per_launch": algo_bytes, "mean_launch_ms": round(ax_avg_ms, 4),
-                "note": "FP64 ALU-bound on GB300 (1.26 TFLOP/s FP64 measured): see fp64_alu"}
-    # the FP64 pipe bound for the same kernel: 57 FMA per local point
-    flops = 2 * 57 * case.nloc
-    roofline["fp64_alu"] = {"achieved_tflops": round(flops / (ax_avg_ms * 1e-3) / 1e12, 3), "peak_tflops": 1.257,
-                            "peak_source": "measured FMA-chain probe on GB300"}
+    roofline = {"kernel": "ax_kernel<7,float,CG> (fused FP32 operator: p update, A p, <p,Ap>)",
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": peaks["source"] + " hbm_gbs",
+                "algorithmic_bytes_per_launch": algo_bytes, "mean_launch_ms": round(ax_avg_ms, 4)}
+    # the FP64 operator of the plain solve: FP64-pipe bound on GB300
+    f64_ms = pser["ax_ms"] / max(pser["ax_n"], 1)
+    f64_bytes = OP_BYTES["f64_cg"] * case.nloc
+    flops = 2 * (57 + 3) * case.nloc
+    roofline_f64 = {"kernel": "ax_kernel<7,double,CG> (fused FP64 operator)", "bound": "fp64 alu",
+                    "mean_launch_ms": round(f64_ms, 4),
+                    "achieved_gbs": round(f64_bytes / (f64_ms * 1e-3) / 1e9, 1),
+                    "hbm_frac": round(f64_bytes / (f64_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                    "achieved_tflops": round(flops / (f64_ms * 1e-3) / 1e12, 3), "peak_tflops": 1.257,
+                    "peak_source": "measured FMA-chain probe on GB300 (FP64)",
+                    "gdofs": round(case.n_paper / (f64_ms * 1e-3) / 1e9, 3)}
+    st = ser["last"]
     rec = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
         "config": {"workload": WORKLOAD, "E": case.E, "N": case.N, "n_paper": case.n_paper,
-                   "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL, "precision": "plain FP64 Jacobi-PCG",
-                   "l2": "inputs larger than L2 (G alone 805 MB)", "parallelism": f"replicas x{world}"},
-        "pcg": {"iters_per_solve": iters / args.steps, "time_to_1e-8_ms": round(ms_per_step, 3),
-                "rel_res": stats["rel_res"] if stats else None, "status": stats["status"] if stats else None,
-                "gs_ms_per_launch": round(gs_ms / max(ax_n, 1), 4)},
+                   "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL,
+                   "precision": "FP64 iterative refinement around FP32 Jacobi-PCG (inner tol 1e-2)",
+                   "l2": "inputs larger than L2 (FP32 G 403 MB, FP64 G 805 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "pcg": {"chosen_time_to_1e-8_ms": round(ms_per_step, 3),
+                "plain_fp64_time_to_1e-8_ms": round(plain_ms, 3),
+                "speedup_vs_plain_fp64": round(plain_ms / ms_per_step, 3),
+                "chosen_inner_iters": ser["iters"] / args.steps,
+                "chosen_outer_iters": st["outer_iters"] if st else None,
+                "plain_iters": pser["iters"] / args.plain_steps,
+                "chosen_rel_res_fp64": st["rel_res"] if st else None,
+                "status": st["status"] if st else None,
+                "outer_fp64_operator_ms": round(ser["outer_ms"] / max(ser["outer_n"], 1), 4)},
         "ax_kernel_gdofs": round(case.n_paper / (ax_avg_ms * 1e-3) / 1e9, 3),
         "roofline": roofline,
-        "gpu_launches": launches,
+        "roofline_fp64_operator": roofline_f64,
+        "gpu_launches": ser["launches"],
         "e2e": e2e,
         "clocks": clk.summary(),
     }
@@ -346,9 +394,48 @@ def run_reference(args):
     print(json.dumps(rec), flush=True)
 
 
+def run_op(args):
+    """Time one entry point alone: K launches of sem_ax / sem_dssum on the
+    channel mesh, CUDA events on the launching stream (inputs > L2)."""
+    import torch
+
+    from paper_2405_05640_gb300 import binding, inputs
+    from paper_2405_05640_gb300 import build as _build
+    _build.build()
+    case = inputs.channel(args.nel, args.order)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+    kind, dt = args.op.split("-")
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    u = torch.randn(case.nloc, dtype=tdt, device="cuda")
+    w = torch.empty_like(u)
+    if kind == "ax":
+        fn, nbytes = (lambda: gm.ax(u, w)), (64 if dt == "f64" else 32) * case.nloc
+    else:
+        fn = lambda: gm.dssum(w, mask=True)
+        nbytes = 2 * gm.info.n_shared_points * (8 if dt == "f64" else 4)
+    for _ in range(args.warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peak = measured_peaks()["hbm_gbs"]
+    print(json.dumps({"op": args.op, "nel": args.nel, "N": case.N, "ms_per_launch": round(ms, 4),
+                      "gdofs": round(case.n_paper / (ms * 1e-3) / 1e9, 3), "algorithmic_bytes": nbytes,
+                      "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                      "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.op:
+        run_op(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

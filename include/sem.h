@@ -202,8 +202,10 @@ typedef struct {
     double wall_ms;        /* host wall time of the call */
     double ax_ms;          /* profile: summed device time of operator kernels */
     double gs_ms;          /* profile: summed device time of gather-scatter kernels */
-    int ax_launches;       /* operator kernel launches */
+    int ax_launches;       /* operator kernel launches (MIXED: inner FP32 ones) */
     int kernel_launches;   /* all kernel launches of the call */
+    double outer_ax_ms;    /* MIXED + profile: device time of the FP64 outer operators */
+    int outer_ax_launches; /* MIXED: FP64 outer operator launches */
 } sem_pcg_stats;
 
 /* Scratch bytes sem_pcg_solve needs (device). */

@@ -54,7 +54,8 @@ class PcgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("ax_ms", ctypes.c_double), ("gs_ms", ctypes.c_double),
-                ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("outer_ax_ms", ctypes.c_double), ("outer_ax_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -21,24 +21,19 @@
 
 namespace sem {
 
-template <typename T>
-struct AxSmem {
-    // byte offsets inside dynamic shared memory
-    int stage_bytes, u_off, g_off, b_off;
-    int vr_off, vs_off, d_off, bar_off, total;
-};
-
-template <int N, typename T, bool HELM>
+// Slabs per stage: the input field (u; or r, dinv, p in the fused CG mode),
+// the six geometric factors, and B (Helmholtz, FP64).
+template <int N, typename T, bool HELM, bool CG>
 __host__ __device__ constexpr int ax_stage_bytes() {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
-    return ((NPT * (7 + (HELM ? 1 : 0)) * (int)sizeof(T)) + 15) / 16 * 16;
+    return ((NPT * ((CG ? 3 : 1) + 6) * (int)sizeof(T) + (HELM ? NPT * 8 : 0)) + 15) / 16 * 16;
 }
 
-template <int N, typename T, bool HELM>
+template <int N, typename T, bool HELM, bool CG>
 __host__ __device__ constexpr int ax_smem_bytes(int nst) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    return nst * ax_stage_bytes<N, T, HELM>() + 2 * NPT * (int)sizeof(T) +
-           ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4;
+    return nst * ax_stage_bytes<N, T, HELM, CG>() + 2 * NPT * (int)sizeof(T) +
+           ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4 + 64;
 }
 
 template <int N>
@@ -53,24 +48,27 @@ struct AxArgs {
     double h1, h2;
 };
 
-template <typename T, typename DM>
-__device__ __forceinline__ const void *dm_ptr(const DM &d) {
-    return d.d;
-}
-
-template <int N, typename T, bool HELM, typename DM>
+// One element per CTA at a time (persistent grid).  Modes:
+//   plain / HELM: w = A_L u  (or h1 A_L u + h2 B u);
+//   CG: p <- dinv r + beta p (written back), w = A_L p (or Helmholtz), and
+//       sum_l p_l w_l reduced over the grid into alpha = rho / pw.
+template <int N, typename T, bool HELM, bool CG, typename DM>
 __global__ void __launch_bounds__(ax_threads<N>())
     ax_kernel(const T *__restrict__ u, T *__restrict__ w, const T *__restrict__ G,
-              const double *__restrict__ Bm, const DM Dm, const AxArgs args, int *__restrict__ err) {
+              const double *__restrict__ Bm, const DM Dm, const AxArgs args, const CgFuse<T> cg,
+              int *__restrict__ err) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    constexpr int SB = ax_stage_bytes<N, T, HELM>();
+    constexpr int SB = ax_stage_bytes<N, T, HELM, CG>();
+    constexpr int NIN = CG ? 3 : 1;  // input slabs
     extern __shared__ __align__(128) unsigned char smem[];
+    if (CG && cg.scal->done) return;  // uniform: the solve has converged
     const int nst = args.nst;
     T *svr = reinterpret_cast<T *>(smem + nst * SB);
     T *svs = svr + NPT;
     T *sD = svs + NPT;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + nst * SB + 2 * NPT * sizeof(T) +
                                                  ((N1 * N1 * sizeof(T) + 15) / 16 * 16));
+    double *sred = reinterpret_cast<double *>(bar + 4);  // 8 doubles: per-warp partials
     const int tid = threadIdx.x;
     const bool active = tid < N1 * N1;
     const int i = tid % N1, j = tid / N1;
@@ -90,6 +88,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
         rDti[l] = active ? sD[l * N1 + i] : T(0);
         rDtj[l] = active ? sD[l * N1 + j] : T(0);
     }
+    const T beta = CG ? (T)cg.scal->beta : T(0);
 
     const int64_t E = args.E;
     const int64_t stride = gridDim.x;
@@ -99,10 +98,16 @@ __global__ void __launch_bounds__(ax_threads<N>())
     auto stage_ptr = [&](int s) { return smem + s * SB; };
     auto issue = [&](int64_t e, int s) {
         unsigned char *st = stage_ptr(s);
-        mbar_arrive_expect_tx(&bar[s], ubytes + gbytes + bbytes);
-        bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
-        bulk_g2s(st + ubytes, G + e * 6 * NPT, gbytes, &bar[s]);
-        if (HELM) bulk_g2s(st + ubytes + gbytes, Bm + e * NPT, bbytes, &bar[s]);
+        mbar_arrive_expect_tx(&bar[s], NIN * ubytes + gbytes + bbytes);
+        if (CG) {
+            bulk_g2s(st, cg.r + e * NPT, ubytes, &bar[s]);
+            bulk_g2s(st + ubytes, cg.dinv + e * NPT, ubytes, &bar[s]);
+            bulk_g2s(st + 2 * ubytes, cg.p + e * NPT, ubytes, &bar[s]);
+        } else {
+            bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
+        }
+        bulk_g2s(st + NIN * ubytes, G + e * 6 * NPT, gbytes, &bar[s]);
+        if (HELM) bulk_g2s(st + NIN * ubytes + gbytes, Bm + e * NPT, bbytes, &bar[s]);
     };
 
     if (args.use_tma && tid == 0) {
@@ -112,6 +117,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
         }
     }
 
+    T pw_acc = T(0);
     int it = 0;
     bool ok = true;
     for (int64_t e = blockIdx.x; e < E; e += stride, ++it) {
@@ -124,19 +130,42 @@ __global__ void __launch_bounds__(ax_threads<N>())
             if (!ok) break;
         } else {
             T *dst = reinterpret_cast<T *>(st);
-            const T *us = u + e * NPT;
+            if (CG) {
+                for (int q = tid; q < NPT; q += blockDim.x) {
+                    dst[q] = cg.r[e * NPT + q];
+                    dst[NPT + q] = cg.dinv[e * NPT + q];
+                    dst[2 * NPT + q] = cg.p[e * NPT + q];
+                }
+            } else {
+                for (int q = tid; q < NPT; q += blockDim.x) dst[q] = u[e * NPT + q];
+            }
             const T *gs = G + e * 6 * NPT;
-            for (int q = tid; q < NPT; q += blockDim.x) dst[q] = us[q];
-            for (int q = tid; q < 6 * NPT; q += blockDim.x) dst[NPT + q] = gs[q];
+            for (int q = tid; q < 6 * NPT; q += blockDim.x) dst[NIN * NPT + q] = gs[q];
             if (HELM) {
-                double *db = reinterpret_cast<double *>(st + ubytes + gbytes);
+                double *db = reinterpret_cast<double *>(st + NIN * ubytes + gbytes);
                 for (int q = tid; q < NPT; q += blockDim.x) db[q] = Bm[e * NPT + q];
             }
             __syncthreads();
         }
-        const T *su = reinterpret_cast<const T *>(st);
-        const T *sg = su + NPT;
-        const double *sb = reinterpret_cast<const double *>(st + ubytes + gbytes);
+        // the operand: u, or the updated search direction p (CG)
+        T *su = reinterpret_cast<T *>(st) + (CG ? 2 * NPT : 0);
+        const T *sg = reinterpret_cast<const T *>(st) + NIN * NPT;
+        const double *sb = reinterpret_cast<const double *>(st + NIN * ubytes + gbytes);
+        if (CG) {
+            const T *sr = reinterpret_cast<const T *>(st);
+            const T *sdi = sr + NPT;
+            T *pe = cg.p + e * NPT;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    const int q = i + N1 * (j + N1 * k);
+                    const T pn = fma(beta, su[q], sdi[q] * sr[q]);
+                    su[q] = pn;
+                    pe[q] = pn;
+                }
+            }
+            __syncthreads();
+        }
 
         T ru[N1], rvt[N1];
         if (active) {
@@ -174,6 +203,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
                 const int p = i + N1 * (j + N1 * k);
                 if (HELM) acc = (T)(args.h1 * (double)acc + args.h2 * sb[p] * (double)ru[k]);
                 we[p] = acc;
+                if (CG) pw_acc = fma(ru[k], acc, pw_acc);
             }
         }
         __syncthreads();  // stage s and svr/svs free again
@@ -193,47 +223,76 @@ __global__ void __launch_bounds__(ax_threads<N>())
             if (en < E) mbar_wait_bounded(&bar[s], (itn / nst) & 1, err, kDevTimeoutTma);
         }
     }
+    if (CG) {
+        // grid reduction of p.w: per-CTA partial, last CTA sums them in order
+        double v = (double)pw_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) sred[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sred[q];
+            cg.partial[blockIdx.x] = t;
+            __threadfence();
+            const bool last = atomicAdd(&cg.scal->cnt[3], 1u) == gridDim.x - 1;
+            if (last) {
+                __threadfence();
+                const volatile double *vp = cg.partial;
+                double pw = 0.0;
+                for (int q = 0; q < (int)gridDim.x; ++q) pw += vp[q];
+                cg.scal->pw = pw;
+                cg.scal->alpha = cg.scal->rho / pw;
+                cg.scal->cnt[3] = 0u;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- launch
 
-template <int N, typename T, bool HELM, typename DM>
+template <int N, typename T, bool HELM, bool CG, typename DM>
 static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
-                       const DM &Dm, cudaStream_t st) {
+                       const DM &Dm, const CgFuse<T> &cg, cudaStream_t st) {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
     constexpr int threads = ax_threads<N>();
-    auto kern = ax_kernel<N, T, HELM, DM>;
+    auto kern = ax_kernel<N, T, HELM, CG, DM>;
     int dev_max = 0;
     SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
     int nst = 2;
-    while (nst > 1 && ax_smem_bytes<N, T, HELM>(nst) > dev_max) --nst;
-    const int smem = ax_smem_bytes<N, T, HELM>(nst);
+    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG>(nst) > dev_max) --nst;
+    const int smem = ax_smem_bytes<N, T, HELM, CG>(nst);
     if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
     SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)m->num_sms * per_sm;
+    if (grid > kAxMaxGrid) grid = kAxMaxGrid;
     if (grid > m->E) grid = m->E;
     AxArgs a;
     a.E = m->E;
     a.nst = nst;
     a.h1 = h1;
     a.h2 = h2;
-    const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(G) |
-                           reinterpret_cast<uintptr_t>(m->B)) % 16) == 0;
-    a.use_tma = ((NPT * sizeof(T)) % 16 == 0) && ((NPT * sizeof(double)) % 16 == 0) && aligned;
-    kern<<<(int)grid, threads, smem, st>>>(u, w, G, m->B, Dm, a, m->d_err);
+    uintptr_t al = reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(m->B);
+    if (CG)
+        al |= reinterpret_cast<uintptr_t>(cg.r) | reinterpret_cast<uintptr_t>(cg.dinv) |
+              reinterpret_cast<uintptr_t>(cg.p);
+    else
+        al |= reinterpret_cast<uintptr_t>(u);
+    a.use_tma = ((NPT * sizeof(T)) % 16 == 0) && ((NPT * sizeof(double)) % 16 == 0) && (al % 16 == 0);
+    kern<<<(int)grid, threads, smem, st>>>(u, w, G, m->B, Dm, a, cg, m->d_err);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
 
-template <typename T, bool HELM, typename DM>
+template <typename T, bool HELM, bool CG, typename DM>
 static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
-                       const DM &Dm, cudaStream_t st) {
+                       const DM &Dm, const CgFuse<T> &cg, cudaStream_t st) {
     switch (m->N) {
 #define SEM_AX_CASE(n) \
-    case n: return launch_ax_n<n, T, HELM, DM>(m, u, w, G, h1, h2, Dm, st);
+    case n: return launch_ax_n<n, T, HELM, CG, DM>(m, u, w, G, h1, h2, Dm, cg, st);
         SEM_AX_CASE(1) SEM_AX_CASE(2) SEM_AX_CASE(3) SEM_AX_CASE(4) SEM_AX_CASE(5)
         SEM_AX_CASE(6) SEM_AX_CASE(7) SEM_AX_CASE(8) SEM_AX_CASE(9) SEM_AX_CASE(10) SEM_AX_CASE(11)
 #undef SEM_AX_CASE
@@ -242,14 +301,26 @@ static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h
 }
 
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2, cudaStream_t st) {
-    if (h2 != 0.0) return dispatch_ax<double, true>(m, u, w, m->G, h1, h2, m->D, st);
-    if (h1 != 1.0) return dispatch_ax<double, true>(m, u, w, m->G, h1, 0.0, m->D, st);
-    return dispatch_ax<double, false>(m, u, w, m->G, 1.0, 0.0, m->D, st);
+    const CgFuse<double> none{};
+    if (h2 != 0.0 || h1 != 1.0) return dispatch_ax<double, true, false>(m, u, w, m->G, h1, h2, m->D, none, st);
+    return dispatch_ax<double, false, false>(m, u, w, m->G, 1.0, 0.0, m->D, none, st);
 }
 
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
-    return dispatch_ax<float, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, st);
+    const CgFuse<float> none{};
+    return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st);
+}
+
+int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
+                     cudaStream_t st) {
+    if (h2 != 0.0 || h1 != 1.0) return dispatch_ax<double, true, true>(m, nullptr, w, m->G, h1, h2, m->D, cg, st);
+    return dispatch_ax<double, false, true>(m, nullptr, w, m->G, 1.0, 0.0, m->D, cg, st);
+}
+
+int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st) {
+    if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
+    return dispatch_ax<float, false, true>(m, nullptr, w, m->G32, 1.0, 0.0, m->Df, cg, st);
 }
 
 // ---------------------------------------------------------------- Jacobi diagonal

@@ -23,6 +23,25 @@ struct DMatF {
     float d[kMaxN1 * kMaxN1];
 };
 
+// Device-resident scalars of one CG solve (read by the fused kernels).
+struct PcgScal {
+    double bb, rr, rho, pw, alpha, beta, tol2, rr0;
+    double scale;  // mixed precision: 1/||r|| of the outer residual (inner init)
+    int iter, done, status, max_iter;
+    unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
+};
+
+// Arguments of the fused CG operator: p <- dinv r + beta p, w = A_L p,
+// alpha = rho / sum_l p_l w_l (grid reduction over per-CTA partials).
+template <typename T>
+struct CgFuse {
+    const T *r;
+    const T *dinv;
+    T *p;
+    PcgScal *scal;
+    double *partial;  // >= gridDim.x doubles
+};
+
 // Error word values written by kernels into mesh->d_err.
 enum DevErr : int { kDevOk = 0, kDevTimeoutTma = 1, kDevTimeoutFlag = 2 };
 
@@ -147,6 +166,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
                   cudaStream_t st);
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st);
+// Fused CG operator (see CgFuse); w receives the local (unassembled) A_L p.
+int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
+                     cudaStream_t st);
+int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st);
+constexpr int kAxMaxGrid = 152 * 32;  // upper bound of the operator grid (partials of the fused kernel)
 int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st);
 int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);
 

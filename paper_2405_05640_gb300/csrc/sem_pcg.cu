@@ -10,10 +10,10 @@
 //         stop if ||r|| <= tol ||b||; z = P r; rho' = <r,z>; p = z + (rho'/rho) p
 // with <a,b> = sum_l a_l b_l / mult_l the unique-node product.
 //
-// GB300 design: per iteration four stream-ordered kernels -- the persistent
-// TMA operator kernel, the gather-scatter, a fused p.w reduction, and one
-// fused update kernel (x, r, z, both dot products, beta, convergence flag);
-// the p update is fused into the next iteration's reduction kernel.  All
+// GB300 design: per iteration three stream-ordered kernels -- the persistent
+// TMA operator kernel fused with the search-direction update p = z + beta p
+// and the <p, A p> reduction (alpha); the gather-scatter; and one fused
+// update kernel (x, r, z, both dot products, beta, convergence flag).  All
 // scalars stay on the device; the host reads a convergence flag every
 // `check_every` iterations, and kernels launched after convergence return at
 // once.  Reductions are two-level (block partials, summed in block order by
@@ -30,14 +30,10 @@ namespace sem {
 constexpr int kPThreads = 256;
 constexpr int kPBlocks = 1184;  // 152 SMs x 8 blocks: fixed so the reduction order is fixed
 
-struct PcgScal {
-    double bb, rr, rho, pw, alpha, beta, tol2, rr0;
-    int iter, done, status, max_iter;
-    unsigned cnt[4];
-};
-
+// Vectors of one CG iteration space in precision T.
+template <typename T>
 struct PcgWork {
-    double *r, *p, *w;
+    T *r, *p, *w;
     double *partial;  // [4][kPBlocks]
     PcgScal *scal;
 };
@@ -95,22 +91,50 @@ __device__ bool grid_reduce(double (&v)[NV], double *partial, unsigned *counter,
     return true;
 }
 
-// r = b - Ax0 (or b), z = dinv r, p = z; bb, rr, rho.
+__device__ __forceinline__ void set_start_flags(PcgScal *s, double bb, double rr) {
+    if (!isfinite(bb) || !isfinite(rr)) {
+        s->done = 1;
+        s->status = SEM_ERR_NAN;
+    } else if (rr <= s->tol2) {
+        s->done = 1;
+        s->status = SEM_OK;
+    } else {
+        s->done = 0;
+        s->status = SEM_ERR_NOT_CONVERGED;
+    }
+}
+
+// Start of a CG solve in precision T: r = scale * (b - Ax0) (ax0 may be
+// null), z = dinv r, p = z; bb = <b,b>, rr = <r,r>, rho = <r,z>.
+// In the mixed solver b is the FP64 outer residual and `scale` = 1/||b||
+// comes from the outer scalars (scale_src), so the inner system is O(1).
+template <typename T, typename TB>
 __global__ void __launch_bounds__(kPThreads)
-    pcg_init_kernel(const double *__restrict__ b, const double *__restrict__ ax0, const double *__restrict__ dinv,
-                    const double *__restrict__ minv, int64_t n, PcgWork W, double tol, int rel, int max_iter) {
+    pcg_init_kernel(const TB *__restrict__ b, const T *__restrict__ ax0, const T *__restrict__ dinv,
+                    const T *__restrict__ minv, int64_t n, PcgWork<T> W, const PcgScal *__restrict__ scale_src,
+                    double tol, int rel, int max_iter) {
+    const double sc = scale_src ? scale_src->scale : 1.0;
     double v[3] = {0.0, 0.0, 0.0};
+    T f[3] = {T(0), T(0), T(0)};  // per-thread partials in T (FP32: no FP64 pipe per element)
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
-        const double bl = b[l];
-        const double r = ax0 ? bl - ax0[l] : bl;
-        const double z = dinv[l] * r;
+        const T bl = scale_src ? (T)((double)b[l] * sc) : (T)b[l];
+        const T r = ax0 ? bl - ax0[l] : bl;
+        const T z = dinv[l] * r;
         W.r[l] = r;
         W.p[l] = z;
-        const double mi = minv[l];
-        v[0] = fma(bl * bl, mi, v[0]);
-        v[1] = fma(r * r, mi, v[1]);
-        v[2] = fma(r * z, mi, v[2]);
+        const T mi = minv[l];
+        if (sizeof(T) == 8) {
+            v[0] = fma((double)(bl * bl), (double)mi, v[0]);
+            v[1] = fma((double)(r * r), (double)mi, v[1]);
+            v[2] = fma((double)(r * z), (double)mi, v[2]);
+        } else {
+            f[0] = fmaf(bl * bl, mi, f[0]);
+            f[1] = fmaf(r * r, mi, f[1]);
+            f[2] = fmaf(r * z, mi, f[2]);
+        }
     }
+    if (sizeof(T) == 4)
+        for (int q = 0; q < 3; ++q) v[q] = (double)f[q];
     double t[3];
     if (grid_reduce<3>(v, W.partial, &W.scal->cnt[0], t)) {
         PcgScal *s = W.scal;
@@ -122,49 +146,37 @@ __global__ void __launch_bounds__(kPThreads)
         s->iter = 0;
         s->max_iter = max_iter;
         s->beta = 0.0;
-        if (!isfinite(t[0]) || !isfinite(t[1])) {
-            s->done = 1;
-            s->status = SEM_ERR_NAN;
-        } else if (t[1] <= s->tol2) {
-            s->done = 1;
-            s->status = SEM_OK;
-        } else {
-            s->done = 0;
-            s->status = SEM_ERR_NOT_CONVERGED;
-        }
-    }
-}
-
-// pw = <p, w>, alpha = rho / pw.
-__global__ void __launch_bounds__(kPThreads)
-    pcg_pw_kernel(const double *__restrict__ minv, int64_t n, PcgWork W) {
-    if (W.scal->done) return;
-    double v[1] = {0.0};
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
-        v[0] = fma(W.p[l] * W.w[l], minv[l], v[0]);
-    double t[1];
-    if (grid_reduce<1>(v, W.partial + kPBlocks, &W.scal->cnt[1], t)) {
-        W.scal->pw = t[0];
-        W.scal->alpha = W.scal->rho / t[0];
+        set_start_flags(s, t[0], t[1]);
     }
 }
 
 // x += alpha p; r -= alpha w; z = dinv r; rr = <r,r>; rz = <r,z>;
 // last block: beta = rz/rho, rho = rz, iteration count and convergence flag.
+template <typename T>
 __global__ void __launch_bounds__(kPThreads)
-    pcg_update_kernel(double *__restrict__ x, const double *__restrict__ dinv, const double *__restrict__ minv,
-                      int64_t n, PcgWork W) {
+    pcg_update_kernel(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
+                      PcgWork<T> W) {
     if (W.scal->done) return;
-    const double alpha = W.scal->alpha;
+    const T alpha = (T)W.scal->alpha;
     double v[2] = {0.0, 0.0};
+    T f0 = T(0), f1 = T(0);
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
-        const double p = W.p[l];
+        const T p = W.p[l];
         x[l] = fma(alpha, p, x[l]);
-        const double r = fma(-alpha, W.w[l], W.r[l]);
+        const T r = fma(-alpha, W.w[l], W.r[l]);
         W.r[l] = r;
-        const double mi = minv[l];
-        v[0] = fma(r * r, mi, v[0]);
-        v[1] = fma(r * (dinv[l] * r), mi, v[1]);
+        const T mi = minv[l];
+        if (sizeof(T) == 8) {
+            v[0] = fma((double)(r * r), (double)mi, v[0]);
+            v[1] = fma((double)(r * (dinv[l] * r)), (double)mi, v[1]);
+        } else {
+            f0 = fma(r * r, mi, f0);
+            f1 = fma(r * (dinv[l] * r), mi, f1);
+        }
+    }
+    if (sizeof(T) == 4) {
+        v[0] = (double)f0;
+        v[1] = (double)f1;
     }
     double t[2];
     if (grid_reduce<2>(v, W.partial + 2 * kPBlocks, &W.scal->cnt[2], t)) {
@@ -186,30 +198,98 @@ __global__ void __launch_bounds__(kPThreads)
     }
 }
 
-// p = dinv r + beta p.
+// ---- FP64 outer loop of the mixed solver ----
+
+// r = b - w (w = A x, or null for x = 0); rr = <r,r>, bb = <b,b>; the
+// convergence flag of the outer loop; scale = 1/||r|| for the inner start.
 __global__ void __launch_bounds__(kPThreads)
-    pcg_p_kernel(const double *__restrict__ dinv, int64_t n, PcgWork W) {
-    if (W.scal->done) return;
-    const double beta = W.scal->beta;
+    ir_residual_kernel(const double *__restrict__ b, const double *__restrict__ w, double *__restrict__ r,
+                       const double *__restrict__ minv, int64_t n, double *partial, PcgScal *s, double tol,
+                       int rel) {
+    double v[2] = {0.0, 0.0};
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const double bl = b[l];
+        const double rl = w ? bl - w[l] : bl;
+        r[l] = rl;
+        const double mi = minv[l];
+        v[0] = fma(bl * bl, mi, v[0]);
+        v[1] = fma(rl * rl, mi, v[1]);
+    }
+    double t[2];
+    if (grid_reduce<2>(v, partial, &s->cnt[0], t)) {
+        s->bb = t[0];
+        s->rr = t[1];
+        s->tol2 = rel ? tol * tol * t[0] : tol * tol;
+        s->scale = t[1] > 0.0 ? 1.0 / sqrt(t[1]) : 0.0;
+        s->iter += 1;
+        set_start_flags(s, t[0], t[1]);
+    }
+}
+
+// x += ||r|| d  (d: the inner FP32 solution of A d = r / ||r||).
+__global__ void __launch_bounds__(kPThreads)
+    ir_correct_kernel(double *__restrict__ x, const float *__restrict__ d, int64_t n, const PcgScal *__restrict__ s) {
+    const double nr = s->scale > 0.0 ? 1.0 / s->scale : 0.0;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
-        W.p[l] = fma(beta, W.p[l], dinv[l] * W.r[l]);
+        x[l] = fma((double)d[l], nr, x[l]);
 }
 
-static size_t pcg_scratch(const sem_mesh *m) {
-    return align_up(sizeof(double) * m->nloc) * 3 + align_up(sizeof(double) * 4 * kPBlocks) +
-           align_up(sizeof(PcgScal));
+// block partials of the vector kernels ([4][kPBlocks]) and of the fused operator
+constexpr size_t kPartialBytes = sizeof(double) * (4 * kPBlocks + kAxMaxGrid);
+
+static size_t pcg_scratch_f64(const sem_mesh *m) {
+    return align_up(sizeof(double) * m->nloc) * 3 + align_up(kPartialBytes) + align_up(sizeof(PcgScal));
 }
 
-static PcgWork carve(const sem_mesh *m, void *scratch) {
+// mixed: FP64 r, w; FP32 d, r, p, w; two partial blocks; two scalar blocks
+static size_t pcg_scratch_mixed(const sem_mesh *m) {
+    return align_up(sizeof(double) * m->nloc) * 2 + align_up(sizeof(float) * m->nloc) * 4 +
+           2 * align_up(kPartialBytes) + 2 * align_up(sizeof(PcgScal));
+}
+
+static size_t pcg_scratch(const sem_mesh *m, const sem_pcg_opts *o) {
+    return (o && o->precision == SEM_PCG_MIXED) ? pcg_scratch_mixed(m) : pcg_scratch_f64(m);
+}
+
+static PcgWork<double> carve_f64(const sem_mesh *m, void *scratch) {
     char *p = static_cast<char *>(scratch);
-    PcgWork W;
+    PcgWork<double> W;
     const size_t vb = align_up(sizeof(double) * m->nloc);
     W.r = reinterpret_cast<double *>(p);
     W.p = reinterpret_cast<double *>(p + vb);
     W.w = reinterpret_cast<double *>(p + 2 * vb);
     W.partial = reinterpret_cast<double *>(p + 3 * vb);
-    W.scal = reinterpret_cast<PcgScal *>(p + 3 * vb + align_up(sizeof(double) * 4 * kPBlocks));
+    W.scal = reinterpret_cast<PcgScal *>(p + 3 * vb + align_up(kPartialBytes));
     return W;
+}
+
+struct MixedWork {
+    double *r64, *w64;
+    float *d32;
+    double *partial_out;
+    PcgScal *scal_out;
+    PcgWork<float> in;
+};
+
+static MixedWork carve_mixed(const sem_mesh *m, void *scratch) {
+    char *p = static_cast<char *>(scratch);
+    const size_t vd = align_up(sizeof(double) * m->nloc), vf = align_up(sizeof(float) * m->nloc);
+    const size_t pb = align_up(kPartialBytes), sb = align_up(sizeof(PcgScal));
+    MixedWork M;
+    M.r64 = reinterpret_cast<double *>(p);
+    M.w64 = reinterpret_cast<double *>(p + vd);
+    p += 2 * vd;
+    M.d32 = reinterpret_cast<float *>(p);
+    M.in.r = reinterpret_cast<float *>(p + vf);
+    M.in.p = reinterpret_cast<float *>(p + 2 * vf);
+    M.in.w = reinterpret_cast<float *>(p + 3 * vf);
+    p += 4 * vf;
+    M.partial_out = reinterpret_cast<double *>(p);
+    M.in.partial = reinterpret_cast<double *>(p + pb);
+    p += 2 * pb;
+    M.scal_out = reinterpret_cast<PcgScal *>(p);
+    M.in.scal = reinterpret_cast<PcgScal *>(p + sb);
+    return M;
 }
 
 // Event pairs recorded on the launching stream around selected kernels;
@@ -249,23 +329,95 @@ struct SolveCtx {
     int launches = 0, ax_launches = 0;
 };
 
-static int apply_assembled_timed(const sem_mesh *m, const double *x, double *y, double h1, double h2,
-                                 cudaStream_t st, SolveCtx &c) {
+// Assembled operator y = M Q Q^T (h1 A_L + h2 B) x in precision T, timed.
+template <typename T>
+static int apply_assembled_timed(const sem_mesh *m, const T *x, T *y, double h1, double h2, cudaStream_t st,
+                                 SolveCtx &c) {
     c.tax.start(st);
-    int s = ax_launch_f64(m, x, y, h1, h2, st);
+    int s;
+    if (sizeof(T) == 8)
+        s = ax_launch_f64(m, reinterpret_cast<const double *>(x), reinterpret_cast<double *>(y), h1, h2, st);
+    else
+        s = ax_launch_f32(m, reinterpret_cast<const float *>(x), reinterpret_cast<float *>(y), st);
     c.tax.stop(st);
     if (s != SEM_OK) return s;
     c.tgs.start(st);
-    s = gs_launch(m, y, SEM_F64, kGsSumMask, st);
+    s = gs_launch(m, y, sizeof(T) == 8 ? SEM_F64 : SEM_F32, kGsSumMask, st);
     c.tgs.stop(st);
     c.launches += 2;
     c.ax_launches += 1;
     return s;
 }
 
+template <typename T>
+static const T *minv_of(const sem_mesh *m);
+template <>
+const double *minv_of<double>(const sem_mesh *m) { return m->minv; }
+template <>
+const float *minv_of<float>(const sem_mesh *m) { return m->minv32; }
+template <typename T>
+static const T *dinv_of(const sem_mesh *m);
+template <>
+const double *dinv_of<double>(const sem_mesh *m) { return m->dinv; }
+template <>
+const float *dinv_of<float>(const sem_mesh *m) { return m->dinv32; }
+
+// CG iterations after an init kernel: three kernels per iteration (fused
+// operator, gather-scatter, fused update), with a host check every `check`
+// iterations.  Leaves the final scalars in *h.
+template <typename T>
+static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, int max_iter, int check, double h1, double h2,
+                   cudaStream_t st, SolveCtx &c, PcgScal *h) {
+    const T *dinv = dinv_of<T>(m);
+    const T *minv = minv_of<T>(m);
+    CgFuse<T> cg{W.r, dinv, W.p, W.scal, W.partial + 4 * kPBlocks};
+    int launched = 0;
+    while (true) {
+        SEM_CUDA_CHECK(cudaMemcpyAsync(h, W.scal, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        c.tax.harvest();
+        c.tgs.harvest();
+        if (h->done || launched >= max_iter) break;
+        for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
+            // p <- dinv r + beta p; w = A_L p; alpha = rho / <p, w>   (one kernel)
+            c.tax.start(st);
+            int s = (sizeof(T) == 8)
+                        ? ax_cg_launch_f64(m, reinterpret_cast<const CgFuse<double> &>(cg),
+                                           reinterpret_cast<double *>(W.w), h1, h2, st)
+                        : ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg),
+                                           reinterpret_cast<float *>(W.w), st);
+            c.tax.stop(st);
+            if (s != SEM_OK) return s;
+            // w <- M Q Q^T w
+            c.tgs.start(st);
+            s = gs_launch(m, W.w, sizeof(T) == 8 ? SEM_F64 : SEM_F32, kGsSumMask, st);
+            c.tgs.stop(st);
+            if (s != SEM_OK) return s;
+            // x += alpha p; r -= alpha w; rr, rz; beta; convergence flag
+            pcg_update_kernel<T><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, m->nloc, W);
+            SEM_CUDA_CHECK(cudaGetLastError());
+            c.launches += 3;
+            c.ax_launches += 1;
+        }
+    }
+    return SEM_OK;
+}
+
+static int finish_stats(const sem_mesh *m, cudaStream_t st, sem_pcg_stats *stats, const SolveCtx &c, int status) {
+    int derr = 0;
+    SEM_CUDA_CHECK(cudaMemcpyAsync(&derr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+    stats->ax_ms = c.tax.total_ms;
+    stats->gs_ms = c.tgs.total_ms;
+    stats->ax_launches = c.ax_launches;
+    stats->kernel_launches = c.launches;
+    if (derr != 0) status = SEM_ERR_TIMEOUT;
+    return status;
+}
+
 static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
                    void *scratch, cudaStream_t st) {
-    PcgWork W = carve(m, scratch);
+    PcgWork<double> W = carve_f64(m, scratch);
     const int64_t n = m->nloc;
     const int check = o->check_every > 0 ? o->check_every : 16;
     SolveCtx c;
@@ -275,55 +427,122 @@ static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_
     SEM_CUDA_CHECK(cudaMemsetAsync(W.scal, 0, sizeof(PcgScal), st));
     const double *ax0 = nullptr;
     if (o->use_initial_guess) {
-        int s = apply_assembled_timed(m, x, W.w, o->h1, o->h2, st, c);
+        int s = apply_assembled_timed<double>(m, x, W.w, o->h1, o->h2, st, c);
         if (s != SEM_OK) return s;
         ax0 = W.w;
     } else {
         SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     }
-    pcg_init_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, ax0, m->dinv, m->minv, n, W, o->tol,
-                                                    o->tol_is_relative, o->max_iter);
+    pcg_init_kernel<double, double><<<kPBlocks, kPThreads, 0, st>>>(b, ax0, m->dinv, m->minv, n, W, nullptr,
+                                                                    o->tol, o->tol_is_relative, o->max_iter);
     SEM_CUDA_CHECK(cudaGetLastError());
     c.launches += 1;
     PcgScal h{};
-    int launched = 0;
-    while (true) {
-        SEM_CUDA_CHECK(cudaMemcpyAsync(&h, W.scal, sizeof(h), cudaMemcpyDeviceToHost, st));
-        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
-        c.tax.harvest();
-        c.tgs.harvest();
-        if (h.done || launched >= o->max_iter) break;
-        for (int q = 0; q < check && launched < o->max_iter; ++q, ++launched) {
-            int s = apply_assembled_timed(m, W.p, W.w, o->h1, o->h2, st, c);
-            if (s != SEM_OK) return s;
-            pcg_pw_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->minv, n, W);
-            pcg_update_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, m->dinv, m->minv, n, W);
-            pcg_p_kernel<<<kPBlocks, kPThreads, 0, st>>>(m->dinv, n, W);
-            SEM_CUDA_CHECK(cudaGetLastError());
-            c.launches += 3;
-        }
-    }
-    int derr = 0;
-    SEM_CUDA_CHECK(cudaMemcpyAsync(&derr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+    int s = cg_loop<double>(m, W, x, o->max_iter, check, o->h1, o->h2, st, c, &h);
+    if (s != SEM_OK) return s;
     stats->iters = h.iter;
     stats->outer_iters = 0;
     stats->bnorm = std::sqrt(h.bb);
     stats->abs_res = std::sqrt(h.rr);
     stats->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : stats->abs_res;
-    stats->ax_ms = c.tax.total_ms;
-    stats->gs_ms = c.tgs.total_ms;
-    stats->ax_launches = c.ax_launches;
-    stats->kernel_launches = c.launches;
-    int status = h.done ? h.status : SEM_ERR_NOT_CONVERGED;
-    if (derr != 0) status = SEM_ERR_TIMEOUT;
-    return status;
+    return finish_stats(m, st, stats, c, h.done ? h.status : SEM_ERR_NOT_CONVERGED);
 }
 
-static int check_opts(const sem_pcg_opts *o) {
-    if (o->precision != SEM_PCG_F64) return fail(SEM_ERR_UNSUPPORTED, "precision mode not built");
+// FP64 iterative refinement around FP32 Jacobi-PCG:
+//   r = b - A x (FP64);  repeat { solve A d = r/||r|| in FP32 to inner_tol;
+//   x += ||r|| d (FP64);  r = b - A x (FP64) }  until ||r|| <= tol ||b||.
+static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
+                     void *scratch, cudaStream_t st) {
+    MixedWork M = carve_mixed(m, scratch);
+    const int64_t n = m->nloc;
+    const int check = o->check_every > 0 ? o->check_every : 16;
+    const double inner_tol = o->inner_tol > 0.0 ? o->inner_tol : 1e-4;
+    SolveCtx c, cin;
+    int s0 = c.tax.init(o->profile != 0, 4);
+    if (s0 == SEM_OK) s0 = c.tgs.init(o->profile != 0, 4);
+    if (s0 == SEM_OK) s0 = cin.tax.init(o->profile != 0, check + 1);
+    if (s0 == SEM_OK) s0 = cin.tgs.init(o->profile != 0, check + 1);
+    if (s0 != SEM_OK) return s0;
+    SEM_CUDA_CHECK(cudaMemsetAsync(M.scal_out, 0, sizeof(PcgScal), st));
+    SEM_CUDA_CHECK(cudaMemsetAsync(M.in.scal, 0, sizeof(PcgScal), st));
+    const double *w0 = nullptr;
+    if (o->use_initial_guess) {
+        int s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
+        if (s != SEM_OK) return s;
+        w0 = M.w64;
+    } else {
+        SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    }
+    ir_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, w0, M.r64, m->minv, n, M.partial_out, M.scal_out, o->tol,
+                                                       o->tol_is_relative);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    c.launches += 1;
+    PcgScal ho{}, hi{};
+    int inner_total = 0, outer = 0, status = SEM_ERR_NOT_CONVERGED;
+    double prev_rr = -1.0;
+    while (true) {
+        SEM_CUDA_CHECK(cudaMemcpyAsync(&ho, M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        c.tax.harvest();
+        c.tgs.harvest();
+        if (ho.done) {
+            status = ho.status;
+            break;
+        }
+        if (inner_total >= o->max_iter) break;
+        // stagnation guard: the FP64 residual must keep falling
+        if (prev_rr >= 0.0 && !(ho.rr < 0.25 * prev_rr)) break;
+        prev_rr = ho.rr;
+        // inner FP32 solve of A d = r / ||r||, from d = 0
+        SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
+        pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
+            M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total);
+        SEM_CUDA_CHECK(cudaGetLastError());
+        cin.launches += 1;
+        int s = cg_loop<float>(m, M.in, M.d32, o->max_iter - inner_total, check, o->h1, o->h2, st, cin, &hi);
+        if (s != SEM_OK) return s;
+        inner_total += hi.iter;
+        // x += ||r|| d; r = b - A x in FP64
+        ir_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, M.d32, n, M.scal_out);
+        s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
+        if (s != SEM_OK) return s;
+        ir_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, M.w64, M.r64, m->minv, n, M.partial_out, M.scal_out,
+                                                           o->tol, o->tol_is_relative);
+        SEM_CUDA_CHECK(cudaGetLastError());
+        c.launches += 2;
+        ++outer;
+    }
+    stats->iters = inner_total;
+    stats->outer_iters = outer;
+    stats->bnorm = std::sqrt(ho.bb);
+    stats->abs_res = std::sqrt(ho.rr);
+    stats->rel_res = ho.bb > 0 ? std::sqrt(ho.rr / ho.bb) : stats->abs_res;
+    // the operator timings: inner FP32 launches (ax_ms) and FP64 outer ones
+    SolveCtx tot;
+    tot.launches = c.launches + cin.launches;
+    tot.ax_launches = cin.ax_launches;
+    tot.tax.total_ms = cin.tax.total_ms;
+    tot.tgs.total_ms = cin.tgs.total_ms;
+    stats->outer_ax_ms = c.tax.total_ms;
+    stats->outer_ax_launches = c.ax_launches;
+    return finish_stats(m, st, stats, tot, status);
+}
+
+static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
+    if (o->precision != SEM_PCG_F64 && o->precision != SEM_PCG_MIXED)
+        return fail(SEM_ERR_UNSUPPORTED, "unknown precision mode");
+    if (o->precision == SEM_PCG_MIXED && !m->G32)
+        return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_MIXED needs a mesh built with SEM_GEOM_F32");
+    if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0))
+        return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_MIXED solves the Poisson operator (h1 = 1, h2 = 0)");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     return SEM_OK;
+}
+
+static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o,
+                          sem_pcg_stats *stats, void *scratch, cudaStream_t st) {
+    if (o->precision == SEM_PCG_MIXED) return pcg_mixed(m, b, x, o, stats, scratch, st);
+    return pcg_f64(m, b, x, o, stats, scratch, st);
 }
 
 }  // namespace sem
@@ -334,8 +553,7 @@ extern "C" {
 
 size_t sem_pcg_scratch_bytes(const sem_mesh *m, const sem_pcg_opts *o) {
     if (!m) return 0;
-    (void)o;
-    return pcg_scratch(m);
+    return pcg_scratch(m, o);
 }
 
 size_t sem_pcg_host_scratch_bytes(const sem_mesh *m, const sem_pcg_opts *o) {
@@ -348,11 +566,11 @@ int sem_pcg_solve(const sem_mesh *m, const double *b, double *x, const sem_pcg_o
     const auto t0 = std::chrono::steady_clock::now();
     if (!m || !b || !x || !o || !stats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     *stats = sem_pcg_stats{};
-    int s = check_opts(o);
+    int s = check_opts(m, o);
     if (s != SEM_OK) return s;
     if (scratch_bytes < sem_pcg_scratch_bytes(m, o) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
         return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_scratch_bytes or not 256-byte aligned");
-    s = pcg_f64(m, b, x, o, stats, scratch, as_stream(stream));
+    s = solve_dispatch(m, b, x, o, stats, scratch, as_stream(stream));
     stats->status = s;
     stats->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (s != SEM_OK && s != SEM_ERR_CUDA) set_error(sem_status_string(s));
@@ -364,7 +582,7 @@ int sem_pcg_solve_host(const sem_mesh *m, const double *hb, double *hx, const se
     const auto t0 = std::chrono::steady_clock::now();
     if (!m || !hb || !hx || !o || !stats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     *stats = sem_pcg_stats{};
-    int s = check_opts(o);
+    int s = check_opts(m, o);
     if (s != SEM_OK) return s;
     if (scratch_bytes < sem_pcg_host_scratch_bytes(m, o) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
         return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_host_scratch_bytes or not 256-byte aligned");
@@ -377,7 +595,7 @@ int sem_pcg_solve_host(const sem_mesh *m, const double *hb, double *hx, const se
     SEM_CUDA_CHECK(cudaMemcpyAsync(db, hb, sizeof(double) * m->nloc, cudaMemcpyHostToDevice, st));
     if (o->use_initial_guess)
         SEM_CUDA_CHECK(cudaMemcpyAsync(dx, hx, sizeof(double) * m->nloc, cudaMemcpyHostToDevice, st));
-    s = pcg_f64(m, db, dx, o, stats, inner, st);
+    s = solve_dispatch(m, db, dx, o, stats, inner, st);
     if (s == SEM_OK || s == SEM_ERR_NOT_CONVERGED) {
         SEM_CUDA_CHECK(cudaMemcpyAsync(hx, dx, sizeof(double) * m->nloc, cudaMemcpyDeviceToHost, st));
         SEM_CUDA_CHECK(cudaStreamSynchronize(st));

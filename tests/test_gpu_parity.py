@@ -250,3 +250,74 @@ def test_full_size_pcg_true_residual(channel32):
     t = _dev(u)
     gm.dssum(t, mask=True)
     np.testing.assert_array_equal(_host(t), om.apply_mask(om.dssum(u)))
+
+
+# ------------------------------------------------------------------ FP32 operator and mixed precision
+# FP32 storage and accumulation: the operator error is a few units of FP32
+# rounding (2^-24 = 6e-8) times the ~3(N+1) terms of each contraction chain,
+# so 5e-6 in the relative 2-norm bounds it for N <= 11.
+F32_AX_TOL = 5e-6
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c.N in (1, 3, 5, 7, 9, 11)],
+                         ids=[c.name for c in CASES if c.N in (1, 3, 5, 7, 9, 11)])
+def test_ax_f32_matches_oracle(case):
+    torch = _torch()
+    om, gm = _pair(case, geom_f32=True)
+    u = np.random.default_rng(12).standard_normal(om.nloc).astype(np.float32)
+    w = _host(gm.ax(torch.from_numpy(u).cuda())).astype(np.float64)
+    assert _rel(w, om.ax_local(u.astype(np.float64))) <= F32_AX_TOL
+
+
+@pytest.mark.parametrize("case", CASES[:7], ids=IDS[:7])
+def test_dssum_f32(case):
+    torch = _torch()
+    om, gm = _pair(case, geom_f32=True)
+    u = np.random.default_rng(6).standard_normal(om.nloc).astype(np.float32)
+    t = torch.from_numpy(u).cuda()
+    gm.dssum(t, mask=True)
+    ref = om.apply_mask(om.dssum(u.astype(np.float64)))
+    np.testing.assert_allclose(_host(t), ref, rtol=0, atol=4 * 2.0 ** -24 * 8 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("case", [inputs.channel(5, 7), inputs.deformed_cube(6, 5),
+                                  inputs.BoxCase("n9", 9, (3, 4, 3), (0, 0, 0), inputs.ALL_FACES,
+                                                 perturb_amp=0.05, seed=2)], ids=["channel5", "deformed6", "n9"])
+def test_pcg_mixed_matches_oracle(case):
+    om, gm = _pair(case, geom_f32=True)
+    b = om.scatter(case.rhs_global())
+    xo, ito, _, sto = om.pcg(b, tol=1e-12, max_iter=20000)
+    xg, st = gm.pcg(_dev(b), tol=1e-12, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-4)
+    assert sto == 0 and st["status"] == 0, st
+    assert st["rel_res"] <= 1e-12 and st["outer_iters"] >= 2
+    assert _rel(_host(xg), xo) <= SOL_TOL
+    # the reported FP64 residual is the true one
+    r = b - om.apply(_host(xg))
+    assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 1.5e-12
+
+
+def test_pcg_mixed_needs_f32_geometry_and_poisson():
+    case = inputs.deformed_cube(3, 3)
+    om, gm = _pair(case)
+    b = _dev(om.scatter(case.rhs_global()))
+    with pytest.raises(binding.SemError) as ei:
+        gm.pcg(b, precision=binding.SEM_PCG_MIXED)
+    assert ei.value.status == binding.SEM_ERR_INVALID_ARG
+    om, gm = _pair(case, geom_f32=True)
+    with pytest.raises(binding.SemError) as ei:
+        gm.pcg(b, precision=binding.SEM_PCG_MIXED, h2=1.0)
+    assert ei.value.status == binding.SEM_ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_full_size_pcg_mixed_true_residual():
+    case = inputs.channel(32, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    xg, st = gm.pcg(_dev(b), tol=1e-8, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-4)
+    assert st["status"] == 0
+    r = b - om.apply(_host(xg))
+    rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
+    assert rel <= 1.05e-8, rel
