@@ -78,6 +78,8 @@ def _load():
                                    ctypes.c_double, _L, ctypes.c_long, _U8, _D, _D, _D, _D,
                                    ctypes.c_double, ctypes.c_int, _I, _D, _D]
             lib.or_pcg.restype = ctypes.c_int
+            lib.or_inverse_jacobian.argtypes = [ctypes.c_int, ctypes.c_long, _D, _D, _D, _D]
+            lib.or_inverse_jacobian.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -128,6 +130,19 @@ def geometry(N: int, verts: np.ndarray):
     st = _load().or_geometry(N, E, _p(verts, _D), _p(xi, _D), _p(rho, _D), _p(D, _D),
                              _p(xyz, _D), _p(G, _D), _p(B, _D))
     return xyz, G, B, st
+
+
+def inverse_jacobian(N: int, verts: np.ndarray) -> np.ndarray:
+    """RX[e, 3a+m, p] = dr_a/dx_m at the GLL points (trilinear hexahedra)."""
+    verts = _f64(verts).reshape(-1, 8, 3)
+    E = verts.shape[0]
+    xi, _ = gll(N)
+    D = deriv(N, xi)
+    RX = np.zeros((E, 9, (N + 1) ** 3))
+    st = _load().or_inverse_jacobian(N, E, _p(verts, _D), _p(xi, _D), _p(D, _D), _p(RX, _D))
+    if st != OK:
+        raise ValueError("det J <= 0")
+    return RX
 
 
 def box_numbering(N: int, nel, periodic) -> tuple[np.ndarray, int]:

@@ -24,6 +24,7 @@
  *   local stiffness .......... or_ax_local, or_helmholtz_local
  *   Jacobi diagonal .......... or_jacobi_diag_local
  *   Jacobi-PCG ............... or_pcg
+ *   inverse Jacobian ......... or_inverse_jacobian (for gradients / divergence)
  *
  * Layout: a field is stored element by element, u[e][k][j][i] with i fastest
  * (local point p = i + (N+1)*(j + (N+1)*k)); geometric factors are
@@ -425,4 +426,65 @@ int or_pcg(int N, long E, const double *D, const double *G, const double *B,
         for (long l = 0; l < nloc; ++l) p[l] = z[l] + beta * p[l];
     }
     return OR_ENOTCONV;
+}
+
+/* Inverse Jacobian dr_a/dx_m at every GLL point of trilinear hexahedra:
+ * RX[e][3a+m][p], from J = dx/dr obtained (as in or_geometry) by applying D
+ * to the vertex-relative coordinates.  Returns -3 if det J <= 0. */
+int or_inverse_jacobian(int N, long E, const double *verts, const double *xi, const double *D, double *RX)
+{
+    int n1 = N + 1;
+    long npt = (long)n1 * n1 * n1;
+    double *X = (double *)malloc(sizeof(double) * 3 * npt);
+    int status = OR_OK;
+    for (long e = 0; e < E; ++e) {
+        const double *V = verts + e * 24;
+        for (int k = 0; k < n1; ++k)
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n1; ++i) {
+                    double fr[2] = {0.5 * (1.0 - xi[i]), 0.5 * (1.0 + xi[i])};
+                    double fs[2] = {0.5 * (1.0 - xi[j]), 0.5 * (1.0 + xi[j])};
+                    double ft[2] = {0.5 * (1.0 - xi[k]), 0.5 * (1.0 + xi[k])};
+                    for (int a = 0; a < 3; ++a) {
+                        double x = 0.0;
+                        for (int v = 0; v < 8; ++v)
+                            x += (V[v * 3 + a] - V[a]) * fr[v & 1] * fs[(v >> 1) & 1] * ft[(v >> 2) & 1];
+                        X[a * npt + i + n1 * (j + n1 * k)] = x;
+                    }
+                }
+        for (int k = 0; k < n1; ++k)
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n1; ++i) {
+                    long p = i + n1 * (j + n1 * k);
+                    double J[3][3];
+                    for (int a = 0; a < 3; ++a) {
+                        const double *Xa = X + a * npt;
+                        double dr = 0.0, ds = 0.0, dt = 0.0;
+                        for (int l = 0; l < n1; ++l) {
+                            dr += D[i * n1 + l] * Xa[l + n1 * (j + n1 * k)];
+                            ds += D[j * n1 + l] * Xa[i + n1 * (l + n1 * k)];
+                            dt += D[k * n1 + l] * Xa[i + n1 * (j + n1 * l)];
+                        }
+                        J[a][0] = dr; J[a][1] = ds; J[a][2] = dt;
+                    }
+                    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+                               - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+                               + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                    if (!(det > 0.0)) status = OR_EMESH;
+                    double R[3][3];
+                    R[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+                    R[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+                    R[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+                    R[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+                    R[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+                    R[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+                    R[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+                    R[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+                    R[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+                    for (int a = 0; a < 3; ++a)
+                        for (int m = 0; m < 3; ++m) RX[(e * 9 + 3 * a + m) * npt + p] = R[a][m];
+                }
+    }
+    free(X);
+    return status;
 }
