@@ -57,6 +57,9 @@ extern "C" {
 /* Extra precision copies of the geometric factors that sem_mesh_create
  * builds (bitmask; FP64 factors are always built). */
 #define SEM_GEOM_F32 1             /* FP32 factors for the FP32 operator */
+#define SEM_GEOM_RX 2              /* inverse Jacobian dr_a/dx_m (9 per point, FP64):
+                                      needed by sem_gradient, sem_advect,
+                                      sem_weak_div and the sem_ns_* stepper */
 
 typedef struct sem_mesh sem_mesh;  /* opaque; freed by sem_mesh_destroy */
 
@@ -190,6 +193,8 @@ typedef struct {
     int use_initial_guess; /* 1: x holds x0 on entry; 0: start from x = 0 */
     int profile;           /* 1: time the operator kernels with CUDA events
                               recorded on `stream` (fills ax_ms / gs_ms) */
+    const double *dinv;    /* optional device array (nloc): inverse Jacobi diagonal to
+                              use instead of the mesh's Poisson one (FP64 solves) */
 } sem_pcg_opts;
 
 typedef struct {
@@ -226,6 +231,56 @@ int sem_pcg_solve(const sem_mesh *mesh, const double *b, double *x, const sem_pc
 size_t sem_pcg_host_scratch_bytes(const sem_mesh *mesh, const sem_pcg_opts *opts);
 int sem_pcg_solve_host(const sem_mesh *mesh, const double *h_b, double *h_x, const sem_pcg_opts *opts,
                        sem_pcg_stats *stats, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* ---- Navier-Stokes building blocks (section 3, Eq. 1) --------------------
+ * All need a mesh built with SEM_GEOM_RX; device FP64 E-layout arrays. */
+
+/* Collocation gradient g[m][l] = sum_a (dr_a/dx_m) (D_a f)[l], m = x, y, z
+ * (g: 3*nloc).  Element-local (not assembled). */
+int sem_gradient(const sem_mesh *mesh, const double *f, double *g, void *stream);
+
+/* Advection term nl[c] = -sum_m u[m] d u[c]/dx_m (u, nl: 3*nloc),
+ * collocation, no dealiasing. */
+int sem_advect(const sem_mesh *mesh, const double *u, double *nl, void *stream);
+
+/* Local weak divergence w_i = int grad(phi_i) . F (F: 3*nloc) by GLL
+ * quadrature: sum_a D_a^T [B sum_m (dr_a/dx_m) F_m].  Not assembled. */
+int sem_weak_div(const sem_mesh *mesh, const double *F, double *w, void *stream);
+
+/* Incompressible Navier-Stokes time stepper on a fully periodic box mesh
+ * (section 3.1: velocity-pressure splitting, Krylov pressure solve each step,
+ * CG for the velocity).  Scheme: BDF_k / EXT_k, k = min(step+1, 2), P_N-P_N:
+ *   F = sum_j (b_j/dt) u^{n+1-j} + sum_j a_j NL^{n+1-j},  NL = -(u.grad)u
+ *   A p = Q Q^T wdiv(F) - mean        (singular; p shifted to zero mean)
+ *   (nu A + (b0/dt) B) u_c = Q Q^T [B (F_c - dp/dx_c)],  nu = 1/Re
+ * The state lives in a caller workspace; pressures of the last three steps
+ * are kept (for extrapolated or learned initial guesses). */
+typedef struct sem_ns sem_ns;
+size_t sem_ns_workspace_bytes(const sem_mesh *mesh);
+int sem_ns_create(const sem_mesh *mesh, double Re, void *d_workspace, size_t bytes, void *stream,
+                  sem_ns **out);
+int sem_ns_destroy(sem_ns *ns);
+/* Set the velocity (device, 3*nloc, continuous), clear the history. */
+int sem_ns_set_velocity(sem_ns *ns, const double *u, void *stream);
+/* Copy a state field to dst (device, nloc): 0..2 velocity, 3 pressure p^n,
+ * 4 pressure p^{n-1}, 5 pressure p^{n-2}, 6 the last pressure right-hand
+ * side (assembled, zero mean). */
+int sem_ns_get(const sem_ns *ns, int which, double *dst, void *stream);
+/* Scratch for sem_ns_step with these solver options. */
+size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts);
+/* One time step.  popts / vopts: pressure / velocity solver options (the
+ * velocity solves use h1 = nu, h2 = b0/dt and their own Jacobi diagonal;
+ * those fields of vopts are ignored).  Initial guess of the pressure:
+ * p_guess (device, nloc) if non-NULL, else the previous pressure when
+ * popts->use_initial_guess, else zero.  pstats: 1 entry, vstats: 3 entries
+ * (host).  Waits for `stream`. */
+int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_opts *vopts,
+                const double *p_guess, sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *d_scratch,
+                size_t scratch_bytes, void *stream);
+/* Kinetic energy (1/2V) int |u|^2 and its GLL quadrature, on the host
+ * (waits for `stream`). */
+int sem_ns_kinetic_energy(const sem_ns *ns, double *energy, void *d_scratch, size_t scratch_bytes,
+                          void *stream);
 
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */

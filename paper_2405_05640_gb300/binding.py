@@ -25,6 +25,7 @@ SEM_ERR_TIMEOUT = -7
 SEM_ERR_UNSUPPORTED = -8
 SEM_F64, SEM_F32 = 0, 1
 SEM_GEOM_F32 = 1
+SEM_GEOM_RX = 2
 SEM_PCG_F64, SEM_PCG_MIXED = 0, 1
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
@@ -47,7 +48,7 @@ class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_is_relative", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p)]
 
 
 class PcgStats(ctypes.Structure):
@@ -85,6 +86,18 @@ _SIGS = {
     "sem_pcg_solve_host": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP,
                             ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
+    "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_weak_div": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_ns_workspace_bytes": ([_VP], ctypes.c_size_t),
+    "sem_ns_create": ([_VP, ctypes.c_double, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "sem_ns_destroy": ([_VP], ctypes.c_int),
+    "sem_ns_set_velocity": ([_VP, _VP, _VP], ctypes.c_int),
+    "sem_ns_get": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "sem_ns_scratch_bytes": ([_VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
+    "sem_ns_step": ([_VP, ctypes.c_double, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgOpts), _VP,
+                     ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_ns_kinetic_energy": ([_VP, ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -136,7 +149,7 @@ def _ptr(t):
 class Mesh:
     """A box mesh living in a caller-owned (PyTorch) device workspace."""
 
-    def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False):
+    def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False, geom_rx: bool = False):
         import numpy as np
         import torch
         self._verts = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 8, 3)
@@ -146,7 +159,7 @@ class Mesh:
         d.periodic[:] = [int(bool(a)) for a in periodic]
         d.dirichlet_faces = int(faces)
         d.vertices = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        d.geom_flags = SEM_GEOM_F32 if geom_f32 else 0
+        d.geom_flags = (SEM_GEOM_F32 if geom_f32 else 0) | (SEM_GEOM_RX if geom_rx else 0)
         self.desc = d
         nbytes = lib().sem_mesh_workspace_bytes(ctypes.byref(d))
         if nbytes == 0:
@@ -276,7 +289,79 @@ class Mesh:
             raise SemError(status, "sem_pcg_solve_host")
         return x_host, st.as_dict()
 
+    # ---- Navier-Stokes building blocks
+    def gradient(self, f):
+        import torch
+        g = torch.empty((3, self.nloc), dtype=torch.float64, device="cuda")
+        check(lib().sem_gradient(self.handle, _ptr(f), _ptr(g), _stream()), "sem_gradient")
+        return g
+
+    def advect(self, u):
+        import torch
+        nl = torch.empty((3, self.nloc), dtype=torch.float64, device="cuda")
+        check(lib().sem_advect(self.handle, _ptr(u), _ptr(nl), _stream()), "sem_advect")
+        return nl
+
+    def weak_div(self, F):
+        import torch
+        w = torch.empty(self.nloc, dtype=torch.float64, device="cuda")
+        check(lib().sem_weak_div(self.handle, _ptr(F), _ptr(w), _stream()), "sem_weak_div")
+        return w
+
     def check_device_error(self) -> int:
         c = ctypes.c_int()
         check(lib().sem_mesh_check_device_error(self.handle, ctypes.byref(c), _stream()), "check_device_error")
         return c.value
+
+
+class NSState:
+    """sem_ns_* time stepper on a fully periodic mesh (built with geom_rx)."""
+
+    def __init__(self, mesh: Mesh, Re: float):
+        import torch
+        self.mesh = mesh
+        n = lib().sem_ns_workspace_bytes(mesh.handle)
+        self.workspace = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        check(lib().sem_ns_create(mesh.handle, float(Re), _VP(base), n, _stream(), ctypes.byref(h)), "sem_ns_create")
+        self.handle = h
+        self._scratch = None
+        self._scratch_key = None
+        self._red = torch.empty(32768 + 256, dtype=torch.uint8, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sem_ns_destroy(h)
+            self.handle = None
+
+    def set_velocity(self, u):
+        check(lib().sem_ns_set_velocity(self.handle, _ptr(u), _stream()), "sem_ns_set_velocity")
+
+    def get(self, which: int):
+        import torch
+        out = torch.empty(self.mesh.nloc, dtype=torch.float64, device="cuda")
+        check(lib().sem_ns_get(self.handle, int(which), _ptr(out), _stream()), "sem_ns_get")
+        return out
+
+    def step(self, dt, popts: PcgOpts, vopts: PcgOpts, p_guess=None):
+        import torch
+        need = lib().sem_ns_scratch_bytes(self.handle, ctypes.byref(popts), ctypes.byref(vopts))
+        if self._scratch is None or self._scratch.numel() < need + 256:
+            self._scratch = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        base = (self._scratch.data_ptr() + 255) // 256 * 256
+        nbytes = self._scratch.numel() - (base - self._scratch.data_ptr())
+        ps = PcgStats()
+        vs = (PcgStats * 3)()
+        guess = _ptr(p_guess) if p_guess is not None else None
+        check(lib().sem_ns_step(self.handle, float(dt), ctypes.byref(popts), ctypes.byref(vopts), guess,
+                                ctypes.byref(ps), vs, _VP(base), nbytes, _stream()), "sem_ns_step")
+        return ps.as_dict(), [v.as_dict() for v in vs]
+
+    def kinetic_energy(self) -> float:
+        e = ctypes.c_double()
+        base = (self._red.data_ptr() + 255) // 256 * 256
+        check(lib().sem_ns_kinetic_energy(self.handle, ctypes.byref(e), _VP(base), 32768, _stream()),
+              "sem_ns_kinetic_energy")
+        return e.value

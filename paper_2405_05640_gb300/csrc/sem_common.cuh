@@ -66,6 +66,7 @@ struct sem_mesh {
     double *dinv;        // [nloc] inverse assembled Jacobi diagonal (0 on Dirichlet)
     float *dinv32;       // [nloc] same in FP32 (when G32 built)
     float *minv32;       // [nloc]
+    double *rx;          // [E][9][npt] dr_a/dx_m (a-major) or nullptr
     int *gs_off;         // [ngroups + 1]
     int *gs_idx;         // [nentries]
     int *d_err;          // device error word

@@ -210,12 +210,12 @@ static int validate(const sem_mesh_desc *d) {
     int64_t E = (int64_t)d->nel[0] * d->nel[1] * d->nel[2];
     int64_t nloc = E * (d->N + 1) * (d->N + 1) * (d->N + 1);
     if (nloc >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "E*(N+1)^3 must be < 2^31");
-    if (d->geom_flags & ~SEM_GEOM_F32) return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
+    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX)) return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
     return SEM_OK;
 }
 
 struct Layout {
-    size_t verts, G, G32, B, mult, minv, dinv, dinv32, minv32, off, idx, err, total;
+    size_t verts, G, G32, B, mult, minv, dinv, dinv32, minv32, rx, off, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -235,6 +235,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.dinv = take(sizeof(double) * nloc);
     L.dinv32 = f32 ? take(sizeof(float) * nloc) : 0;
     L.minv32 = f32 ? take(sizeof(float) * nloc) : 0;
+    L.rx = (d->geom_flags & SEM_GEOM_RX) ? take(sizeof(double) * 9 * nloc) : 0;
     L.off = take(sizeof(int) * (c.ngroups + 1));
     L.idx = take(sizeof(int) * (c.nentries > 0 ? c.nentries : 1));
     L.err = take(sizeof(int) * 8);
@@ -258,7 +259,7 @@ struct GllConst {
 // Jacobian J_ab = dx_a/dr_b is the analytic derivative of the trilinear map.
 __global__ void geometry_kernel(const double *__restrict__ verts, int64_t E, int N, GllConst g,
                                 double *__restrict__ G, double *__restrict__ B,
-                                float *__restrict__ G32, int *__restrict__ err) {
+                                float *__restrict__ G32, double *__restrict__ rx, int *__restrict__ err) {
     const int n1 = N + 1;
     const int64_t npt = (int64_t)n1 * n1 * n1;
     const int64_t nloc = E * npt;
@@ -318,6 +319,13 @@ __global__ void geometry_kernel(const double *__restrict__ verts, int64_t E, int
             for (int c = 0; c < 6; ++c) Gf[c * npt + p] = (float)gg[c];
         }
         B[l] = wq * det;
+        if (rx) {
+            // dr_a/dx_m = (J^-1)[a][m] = C[m][a] / det, stored [e][3a+m][p]
+            double *Re = rx + e * 9 * npt;
+            const double id = 1.0 / det;
+            for (int a = 0; a < 3; ++a)
+                for (int mm = 0; mm < 3; ++mm) Re[(3 * a + mm) * npt + p] = C[mm][a] * id;
+        }
     }
 }
 
@@ -463,6 +471,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->dinv = reinterpret_cast<double *>(base + L.dinv);
     m->dinv32 = m->G32 ? reinterpret_cast<float *>(base + L.dinv32) : nullptr;
     m->minv32 = m->G32 ? reinterpret_cast<float *>(base + L.minv32) : nullptr;
+    m->rx = (d->geom_flags & SEM_GEOM_RX) ? reinterpret_cast<double *>(base + L.rx) : nullptr;
     m->gs_off = reinterpret_cast<int *>(base + L.off);
     m->gs_idx = reinterpret_cast<int *>(base + L.idx);
     m->d_err = reinterpret_cast<int *>(base + L.err);
@@ -496,7 +505,8 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
         g.xi[i] = m->xi[i];
         g.rho[i] = m->rho[i];
     }
-    geometry_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->verts, m->E, m->N, g, m->G, m->B, m->G32, m->d_err);
+    geometry_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->verts, m->E, m->N, g, m->G, m->B, m->G32, m->rx,
+                                                      m->d_err);
     CK(cudaGetLastError());
     // multiplicity = Q Q^T 1
     fill_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->mult, m->nloc, 1.0);

@@ -355,20 +355,13 @@ template <>
 const double *minv_of<double>(const sem_mesh *m) { return m->minv; }
 template <>
 const float *minv_of<float>(const sem_mesh *m) { return m->minv32; }
-template <typename T>
-static const T *dinv_of(const sem_mesh *m);
-template <>
-const double *dinv_of<double>(const sem_mesh *m) { return m->dinv; }
-template <>
-const float *dinv_of<float>(const sem_mesh *m) { return m->dinv32; }
 
 // CG iterations after an init kernel: three kernels per iteration (fused
 // operator, gather-scatter, fused update), with a host check every `check`
 // iterations.  Leaves the final scalars in *h.
 template <typename T>
-static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, int max_iter, int check, double h1, double h2,
-                   cudaStream_t st, SolveCtx &c, PcgScal *h) {
-    const T *dinv = dinv_of<T>(m);
+static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max_iter, int check, double h1,
+                   double h2, cudaStream_t st, SolveCtx &c, PcgScal *h) {
     const T *minv = minv_of<T>(m);
     CgFuse<T> cg{W.r, dinv, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
@@ -433,12 +426,13 @@ static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_
     } else {
         SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     }
-    pcg_init_kernel<double, double><<<kPBlocks, kPThreads, 0, st>>>(b, ax0, m->dinv, m->minv, n, W, nullptr,
+    const double *dinv = o->dinv ? o->dinv : m->dinv;
+    pcg_init_kernel<double, double><<<kPBlocks, kPThreads, 0, st>>>(b, ax0, dinv, m->minv, n, W, nullptr,
                                                                     o->tol, o->tol_is_relative, o->max_iter);
     SEM_CUDA_CHECK(cudaGetLastError());
     c.launches += 1;
     PcgScal h{};
-    int s = cg_loop<double>(m, W, x, o->max_iter, check, o->h1, o->h2, st, c, &h);
+    int s = cg_loop<double>(m, W, x, dinv, o->max_iter, check, o->h1, o->h2, st, c, &h);
     if (s != SEM_OK) return s;
     stats->iters = h.iter;
     stats->outer_iters = 0;
@@ -499,7 +493,8 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
             M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total);
         SEM_CUDA_CHECK(cudaGetLastError());
         cin.launches += 1;
-        int s = cg_loop<float>(m, M.in, M.d32, o->max_iter - inner_total, check, o->h1, o->h2, st, cin, &hi);
+        int s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st,
+                               cin, &hi);
         if (s != SEM_OK) return s;
         inner_total += hi.iter;
         // x += ||r|| d; r = b - A x in FP64
@@ -533,8 +528,8 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_UNSUPPORTED, "unknown precision mode");
     if (o->precision == SEM_PCG_MIXED && !m->G32)
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_MIXED needs a mesh built with SEM_GEOM_F32");
-    if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0))
-        return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_MIXED solves the Poisson operator (h1 = 1, h2 = 0)");
+    if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
+        return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_MIXED solves the Poisson operator (h1 = 1, h2 = 0, mesh diagonal)");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     return SEM_OK;
 }
