@@ -176,10 +176,11 @@ int sem_glsc3_noalloc(const sem_mesh *mesh, const double *a, const double *b, do
  * and zero on Dirichlet nodes.  Stops when ||r|| <= tol ||b|| (tol_is_
  * relative) or ||r|| <= tol, with ||.|| the unique-node norm.
  * precision = SEM_PCG_F64: all FP64.
- * precision = SEM_PCG_MIXED: FP64 iterative refinement around inner FP32
- *   PCG solves (FP32 operator and vectors, FP32 accumulation), each to
- *   inner_tol relative; the outer residual b - A x, the outer dot products
- *   and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh. */
+ * precision = SEM_PCG_MIXED: FP64 iterative refinement around FP32 PCG
+ *   (FP32 operator and vectors, FP32 accumulation): every time the FP32
+ *   residual has fallen by inner_tol, the FP32 increment is added to the FP64
+ *   solution and the FP64 residual b - A x is recomputed; the outer dot
+ *   products and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh. */
 #define SEM_PCG_F64 0
 #define SEM_PCG_MIXED 1
 typedef struct {
@@ -195,6 +196,10 @@ typedef struct {
                               recorded on `stream` (fills ax_ms / gs_ms) */
     const double *dinv;    /* optional device array (nloc): inverse Jacobi diagonal to
                               use instead of the mesh's Poisson one (FP64 solves) */
+    int mixed_restart;     /* SEM_PCG_MIXED: 0 (default) keeps the FP32 search
+                              direction across FP64 refinements (the FP64 true
+                              residual replaces the FP32 one, p is rescaled); 1
+                              restarts the inner CG at every refinement */
 } sem_pcg_opts;
 
 typedef struct {

@@ -48,7 +48,7 @@ class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_is_relative", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
-                ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int)]
 
 
 class PcgStats(ctypes.Structure):
@@ -239,9 +239,11 @@ class Mesh:
         return float(self._res.item())
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
-                 check_every=16, use_initial_guess=False, relative=True, profile=False) -> PcgOpts:
+                 check_every=16, use_initial_guess=False, relative=True, profile=False,
+                 mixed_restart=False) -> PcgOpts:
         o = PcgOpts()
         o.profile = int(bool(profile))
+        o.mixed_restart = int(bool(mixed_restart))
         o.tol, o.tol_is_relative, o.max_iter, o.precision = float(tol), int(relative), int(max_iter), int(precision)
         o.inner_tol, o.h1, o.h2 = float(inner_tol), float(h1), float(h2)
         o.check_every, o.use_initial_guess = int(check_every), int(bool(use_initial_guess))

@@ -26,7 +26,9 @@ struct DMatF {
 // Device-resident scalars of one CG solve (read by the fused kernels).
 struct PcgScal {
     double bb, rr, rho, pw, alpha, beta, tol2, rr0;
-    double scale;  // mixed precision: 1/||r|| of the outer residual (inner init)
+    double scale;       // mixed precision: 1/||r|| of the outer residual (inner init)
+    double scale_prev;  // mixed precision: the previous 1/||r||
+    double rho_prev;    // rho of the iteration before the last update
     int iter, done, status, max_iter;
     unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
 };

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kPThreads)
         PcgScal *s = W.scal;
         s->rr = t[0];
         s->beta = t[1] / s->rho;
+        s->rho_prev = s->rho;
         s->rho = t[1];
         s->iter += 1;
         if (!isfinite(t[0])) {
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kPThreads)
         s->bb = t[0];
         s->rr = t[1];
         s->tol2 = rel ? tol * tol * t[0] : tol * tol;
+        s->scale_prev = s->scale;
         s->scale = t[1] > 0.0 ? 1.0 / sqrt(t[1]) : 0.0;
         s->iter += 1;
         set_start_flags(s, t[0], t[1]);
@@ -228,10 +230,49 @@ __global__ void __launch_bounds__(kPThreads)
 
 // x += ||r|| d  (d: the inner FP32 solution of A d = r / ||r||).
 __global__ void __launch_bounds__(kPThreads)
-    ir_correct_kernel(double *__restrict__ x, const float *__restrict__ d, int64_t n, const PcgScal *__restrict__ s) {
+    ir_correct_kernel(double *__restrict__ x, float *__restrict__ d, int64_t n, const PcgScal *__restrict__ s) {
     const double nr = s->scale > 0.0 ? 1.0 / s->scale : 0.0;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
         x[l] = fma((double)d[l], nr, x[l]);
+        d[l] = 0.0f;
+    }
+}
+
+// Refinement without restart: the FP32 residual becomes the new FP64
+// residual r / ||r||; the FP32 search direction is rescaled by
+// c = ||r_old|| / ||r_new|| to stay consistent with it; rho and beta are
+// recomputed from the new residual (beta = rho / (rho_prev c^2)); the inner
+// loop resumes until its residual has fallen by `delta` again.
+__global__ void __launch_bounds__(kPThreads)
+    ir_reliable_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
+                       int64_t n, PcgWork<float> W, const PcgScal *__restrict__ so, double delta) {
+    const double inv = so->scale;
+    const float c = (float)(so->scale / so->scale_prev);
+    float f0 = 0.f, f1 = 0.f;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const float r = (float)(r64[l] * inv);
+        W.r[l] = r;
+        W.p[l] *= c;
+        const float mi = minv[l];
+        f0 = fmaf(r * r, mi, f0);
+        f1 = fmaf(r * (dinv[l] * r), mi, f1);
+    }
+    double v[2] = {(double)f0, (double)f1}, t[2];
+    if (grid_reduce<2>(v, W.partial + 2 * kPBlocks, &W.scal->cnt[2], t)) {
+        PcgScal *s = W.scal;
+        const double cc = (double)c * (double)c;
+        s->rr = t[0];
+        s->beta = t[1] / (s->rho_prev * cc);
+        s->rho = t[1];
+        s->tol2 = delta * delta * t[0];
+        if (!isfinite(t[0])) {
+            s->done = 1;
+            s->status = SEM_ERR_NAN;
+        } else {
+            s->done = 0;
+            s->status = SEM_ERR_NOT_CONVERGED;
+        }
+    }
 }
 
 // block partials of the vector kernels ([4][kPBlocks]) and of the fused operator
@@ -487,16 +528,22 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         // stagnation guard: the FP64 residual must keep falling
         if (prev_rr >= 0.0 && !(ho.rr < 0.25 * prev_rr)) break;
         prev_rr = ho.rr;
-        // inner FP32 solve of A d = r / ||r||, from d = 0
-        SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
-        pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
-            M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total);
+        if (outer == 0 || o->mixed_restart) {
+            // inner FP32 solve of A d = r / ||r||, from d = 0
+            SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
+            pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
+                M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total);
+        } else {
+            // keep the search direction: swap in the FP64 residual and go on
+            ir_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(M.r64, m->dinv32, m->minv32, n, M.in, M.scal_out,
+                                                               inner_tol);
+        }
         SEM_CUDA_CHECK(cudaGetLastError());
         cin.launches += 1;
         int s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st,
                                cin, &hi);
         if (s != SEM_OK) return s;
-        inner_total += hi.iter;
+        inner_total = o->mixed_restart ? inner_total + hi.iter : hi.iter;
         // x += ||r|| d; r = b - A x in FP64
         ir_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, M.d32, n, M.scal_out);
         s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
