@@ -287,6 +287,18 @@ int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_
 int sem_ns_kinetic_energy(const sem_ns *ns, double *energy, void *d_scratch, size_t scratch_bytes,
                           void *stream);
 
+/* ---- BF16 GEMM on the tensor cores (element-local network) ---------------
+ * C[M x N] = act(A . B^T + bias): A [M x K] and B [N x K] row-major BF16
+ * (device, 16-byte aligned, K contiguous), FP32 accumulation; act 0 =
+ * identity, 1 = ReLU; bias [N] FP32 or NULL; C32 (FP32) and/or C16 (BF16)
+ * row-major with leading dimension ldc (>= N, multiple of 4).  M % 128 == 0,
+ * N % 128 == 0, K % 64 == 0.  d_err: device int that receives a non-zero code
+ * if a bounded wait gave up (check it with a stream synchronisation).
+ * Stream-ordered, asynchronous.  Not from the paper: the learned initial
+ * guess of the pressure solve uses it. */
+int sem_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *C32,
+                  void *C16, int ldc, int *d_err, void *stream);
+
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */
 int sem_mesh_check_device_error(const sem_mesh *mesh, int *code, void *stream);

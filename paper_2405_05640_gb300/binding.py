@@ -86,6 +86,8 @@ _SIGS = {
     "sem_pcg_solve_host": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP,
                             ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
+    "sem_gemm_bf16": ([_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                       ctypes.c_int, _VP, _VP], ctypes.c_int),
     "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_weak_div": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -367,3 +369,19 @@ class NSState:
         check(lib().sem_ns_kinetic_energy(self.handle, ctypes.byref(e), _VP(base), 32768, _stream()),
               "sem_ns_kinetic_energy")
         return e.value
+
+
+def gemm_bf16(A, B, bias=None, act=0, out32=True, out16=False, err=None):
+    """sem_gemm_bf16: act(A @ B^T + bias) with A [M, K], B [N, K] bfloat16
+    CUDA tensors; returns (C32 or None, C16 or None)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    c32 = torch.empty((M, N), dtype=torch.float32, device="cuda") if out32 else None
+    c16 = torch.empty((M, N), dtype=torch.bfloat16, device="cuda") if out16 else None
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    check(lib().sem_gemm_bf16(_ptr(A), _ptr(B), M, N, K, _ptr(bias) if bias is not None else None, int(act),
+                              _ptr(c32) if c32 is not None else None, _ptr(c16) if c16 is not None else None,
+                              N, _ptr(err), _stream()), "sem_gemm_bf16")
+    return c32, c16
