@@ -299,6 +299,50 @@ int sem_ns_kinetic_energy(const sem_ns *ns, double *energy, void *d_scratch, siz
 int sem_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *C32,
                   void *C16, int ldc, int *d_err, void *stream);
 
+/* ---- Element-local network for the learned initial guess ----------------
+ * Not from the paper.  Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 per row
+ * (one row per element); loss (1/(2 R O)) sum (Y - T)^2 over the first R
+ * rows and O outputs; Adam.  Training and inference GEMMs run on
+ * sem_gemm_bf16 (BF16 operands, FP32 accumulation); master parameters,
+ * gradients and Adam moments are FP32 in one flat array ordered W1 [H x I],
+ * b1 [H], W2 [H x H], b2 [H], W3 [O x H], b3 [O].  I, H, O and the row
+ * counts passed below must be multiples of 128 (pad with zeros). */
+typedef struct sem_mlp sem_mlp;
+size_t sem_mlp_workspace_bytes(int n_in, int n_hidden, int n_out, int max_rows);
+int sem_mlp_create(int n_in, int n_hidden, int n_out, int max_rows, void *d_workspace, size_t bytes,
+                   sem_mlp **out);
+int sem_mlp_destroy(sem_mlp *mlp);
+size_t sem_mlp_num_params(const sem_mlp *mlp);
+/* Parameters from / to a host FP32 array of sem_mlp_num_params values;
+ * set also clears the Adam moments. */
+int sem_mlp_set_params(sem_mlp *mlp, const float *host, void *stream);
+int sem_mlp_get_params(const sem_mlp *mlp, float *host, void *stream);
+int sem_mlp_get_grads(const sem_mlp *mlp, float *host, void *stream);
+/* Y [rows x O] (device FP32) from X [rows x I] (device BF16). */
+int sem_mlp_forward(sem_mlp *mlp, const void *X, int rows, float *Y, void *stream);
+/* Forward and backward on X, T [rows x O] (device FP32); gradients kept in
+ * the network; *loss (host) over rows_real rows and outs_real outputs.
+ * Waits for `stream`. */
+int sem_mlp_grad(sem_mlp *mlp, const void *X, const float *T, int rows, int rows_real, int outs_real,
+                 double *loss, void *stream);
+/* One Adam step with the stored gradients. */
+int sem_mlp_adam(sem_mlp *mlp, double lr, double beta1, double beta2, double eps, void *stream);
+
+/* Features of the guess network for every element e (row e of X, BF16,
+ * leading dimension ldx >= 4 npt): the last three pressures p1, p2, p3
+ * divided by pscale and the pressure right-hand side divided by rscale
+ * (E-layout device FP64 inputs). */
+int sem_guess_features(const sem_mesh *mesh, const double *p1, const double *p2, const double *p3,
+                       const double *rhs, double pscale, double rscale, void *X, int ldx, void *stream);
+/* Training target T[e][q] = (p - (3 p1 - 3 p2 + p3)) / pscale (FP32, ldt >= npt):
+ * the correction to the cubic extrapolation. */
+int sem_guess_target(const sem_mesh *mesh, const double *p, const double *p1, const double *p2,
+                     const double *p3, double pscale, float *T, int ldt, void *stream);
+/* Guess = (Q Q^T g) / mult with g = 3 p1 - 3 p2 + p3 + pscale Y (continuous
+ * FP64 E-layout output). */
+int sem_guess_apply(const sem_mesh *mesh, const float *Y, int ldy, const double *p1, const double *p2,
+                    const double *p3, double pscale, double *guess, void *stream);
+
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */
 int sem_mesh_check_device_error(const sem_mesh *mesh, int *code, void *stream);

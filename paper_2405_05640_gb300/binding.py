@@ -88,6 +88,22 @@ _SIGS = {
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
     "sem_gemm_bf16": ([_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                        ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "sem_mlp_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "sem_mlp_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t,
+                        ctypes.POINTER(_VP)], ctypes.c_int),
+    "sem_mlp_destroy": ([_VP], ctypes.c_int),
+    "sem_mlp_num_params": ([_VP], ctypes.c_size_t),
+    "sem_mlp_set_params": ([_VP, _VP, _VP], ctypes.c_int),
+    "sem_mlp_get_params": ([_VP, _VP, _VP], ctypes.c_int),
+    "sem_mlp_get_grads": ([_VP, _VP, _VP], ctypes.c_int),
+    "sem_mlp_forward": ([_VP, _VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "sem_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                      _VP], ctypes.c_int),
+    "sem_mlp_adam": ([_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
+    "sem_guess_features": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, ctypes.c_int, _VP],
+                           ctypes.c_int),
+    "sem_guess_target": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int, _VP], ctypes.c_int),
+    "sem_guess_apply": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, _VP, _VP], ctypes.c_int),
     "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_weak_div": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -385,3 +401,95 @@ def gemm_bf16(A, B, bias=None, act=0, out32=True, out16=False, err=None):
                               _ptr(c32) if c32 is not None else None, _ptr(c16) if c16 is not None else None,
                               N, _ptr(err), _stream()), "sem_gemm_bf16")
     return c32, c16
+
+
+class MLP:
+    """sem_mlp_*: the element-local guess network (dimensions multiples of 128)."""
+    ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+    def __init__(self, n_in, n_hidden, n_out, max_rows):
+        import torch
+        self.I, self.H, self.O, self.R = int(n_in), int(n_hidden), int(n_out), int(max_rows)
+        n = lib().sem_mlp_workspace_bytes(self.I, self.H, self.O, self.R)
+        if n == 0:
+            raise SemError(SEM_ERR_INVALID_ARG, "sem_mlp_workspace_bytes")
+        self.workspace = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        check(lib().sem_mlp_create(self.I, self.H, self.O, self.R, _VP(base), n, ctypes.byref(h)), "sem_mlp_create")
+        self.handle = h
+        self.P = lib().sem_mlp_num_params(h)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sem_mlp_destroy(h)
+            self.handle = None
+
+    def _flat(self, params):
+        import numpy as np
+        return np.ascontiguousarray(np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                                                    for k in self.ORDER]))
+
+    def _unflat(self, flat):
+        shapes = {"W1": (self.H, self.I), "b1": (self.H,), "W2": (self.H, self.H), "b2": (self.H,),
+                  "W3": (self.O, self.H), "b3": (self.O,)}
+        out, o = {}, 0
+        for k in self.ORDER:
+            n = 1
+            for s in shapes[k]:
+                n *= s
+            out[k] = flat[o:o + n].reshape(shapes[k]).copy()
+            o += n
+        return out
+
+    def set_params(self, params):
+        flat = self._flat(params)
+        assert flat.size == self.P
+        check(lib().sem_mlp_set_params(self.handle, flat.ctypes.data_as(_VP), _stream()), "sem_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        flat = np.zeros(self.P, np.float32)
+        check(lib().sem_mlp_get_params(self.handle, flat.ctypes.data_as(_VP), _stream()), "sem_mlp_get_params")
+        return self._unflat(flat)
+
+    def get_grads(self):
+        import numpy as np
+        flat = np.zeros(self.P, np.float32)
+        check(lib().sem_mlp_get_grads(self.handle, flat.ctypes.data_as(_VP), _stream()), "sem_mlp_get_grads")
+        return self._unflat(flat)
+
+    def forward(self, X, Y=None):
+        import torch
+        rows = X.shape[0]
+        if Y is None:
+            Y = torch.empty((rows, self.O), dtype=torch.float32, device="cuda")
+        check(lib().sem_mlp_forward(self.handle, _ptr(X), rows, _ptr(Y), _stream()), "sem_mlp_forward")
+        return Y
+
+    def grad(self, X, T, rows_real=None, outs_real=None):
+        rows = X.shape[0]
+        loss = ctypes.c_double()
+        check(lib().sem_mlp_grad(self.handle, _ptr(X), _ptr(T), rows, int(rows_real or rows),
+                                 int(outs_real or self.O), ctypes.byref(loss), _stream()), "sem_mlp_grad")
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(lib().sem_mlp_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps), _stream()),
+              "sem_mlp_adam")
+
+
+def guess_features(mesh, p1, p2, p3, rhs, pscale, rscale, X):
+    check(lib().sem_guess_features(mesh.handle, _ptr(p1), _ptr(p2), _ptr(p3), _ptr(rhs), float(pscale),
+                                   float(rscale), _ptr(X), X.shape[1], _stream()), "sem_guess_features")
+
+
+def guess_target(mesh, p, p1, p2, p3, pscale, T):
+    check(lib().sem_guess_target(mesh.handle, _ptr(p), _ptr(p1), _ptr(p2), _ptr(p3), float(pscale), _ptr(T),
+                                 T.shape[1], _stream()), "sem_guess_target")
+
+
+def guess_apply(mesh, Y, p1, p2, p3, pscale, out):
+    check(lib().sem_guess_apply(mesh.handle, _ptr(Y), Y.shape[1], _ptr(p1), _ptr(p2), _ptr(p3), float(pscale),
+                                _ptr(out), _stream()), "sem_guess_apply")

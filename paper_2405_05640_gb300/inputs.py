@@ -214,3 +214,18 @@ def batched_cases(nsolve: int = 64, seed: int = 0, emin: int = 8 ** 3, emax: int
         out.append(BoxCase(f"batched_{s}", N, (nx, nx, nz), (0, 0, 0), ALL_FACES,
                            perturb_amp=0.05, seed=int(rng.integers(0, 2 ** 31))))
     return out
+
+
+def mlp_init(n_in: int, n_hidden: int, n_out: int, seed: int = 0) -> dict:
+    """Seeded initial parameters of the element-local network (He-uniform
+    weights, zero biases), FP32: W1 [H, I], b1 [H], W2 [H, H], b2 [H],
+    W3 [O, H], b3 [O]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def he(o, i):
+        lim = math.sqrt(6.0 / i)
+        return rng.uniform(-lim, lim, size=(o, i)).astype(np.float32)
+
+    return {"W1": he(n_hidden, n_in), "b1": np.zeros(n_hidden, np.float32),
+            "W2": he(n_hidden, n_hidden), "b2": np.zeros(n_hidden, np.float32),
+            "W3": he(n_out, n_hidden) * np.float32(0.1), "b3": np.zeros(n_out, np.float32)}
