@@ -71,6 +71,11 @@ def parse_args(argv=None):
     p.add_argument("--plain-steps", type=int, default=2, help="plain FP64 solves timed for comparison")
     p.add_argument("--op", choices=["ax-f64", "ax-f32", "dssum-f64", "dssum-f32"], default=None,
                    help="time one entry point alone instead of the solve")
+    p.add_argument("--workload", choices=["channel", "tgv-learned"], default="channel")
+    p.add_argument("--train-steps", type=int, default=100)
+    p.add_argument("--eval-steps", type=int, default=100)
+    p.add_argument("--epochs", type=int, default=30)
+    p.add_argument("--variant", choices=["p1", "d3"], default="p1")
     return p.parse_args(argv)
 
 
@@ -431,9 +436,30 @@ def run_op(args):
                       "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}), flush=True)
 
 
+def run_tgv_learned(args):
+    """The learned-initial-guess workload: TGV Re=1600, 32^3, N=7, dt=1e-3,
+    network trained on steps 1-100, pressure solves of steps 101-200 timed
+    per method (plain FP64 from p^{n-1}; FP64 refinement around FP32 PCG from
+    p^{n-1}, from the cubic extrapolation, from the learned guess)."""
+    from paper_2405_05640_gb300 import build as _build
+    from paper_2405_05640_gb300 import tgv_learned
+    _build.build()
+    out = tgv_learned.run(nel=args.nel, N=args.order, train_steps=args.train_steps, eval_steps=args.eval_steps,
+                          epochs=args.epochs, variant=args.variant)
+    m = out["methods"]
+    rec = {"metric": "pressure-solve wall time to 1e-8 over the evaluated TGV steps, learned guess + mixed "
+                     "precision vs plain FP64 (x0 = previous pressure)",
+           "value": m["chosen_learned"]["speedup_vs_plain_f64_prev"], "unit": "x (speedup)",
+           "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 network / f32 inner / f64 refinement",
+           "data": "synthetic", "config": {"workload": out["workload"]}, **out}
+    print(json.dumps(rec), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.op:
+    if args.workload == "tgv-learned":
+        run_tgv_learned(args)
+    elif args.op:
         run_op(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -216,6 +216,7 @@ typedef struct {
     int kernel_launches;   /* all kernel launches of the call */
     double outer_ax_ms;    /* MIXED + profile: device time of the FP64 outer operators */
     int outer_ax_launches; /* MIXED: FP64 outer operator launches */
+    double init_rel_res;   /* ||b - A x0|| / ||b|| of the initial guess */
 } sem_pcg_stats;
 
 /* Scratch bytes sem_pcg_solve needs (device). */
@@ -267,10 +268,15 @@ int sem_ns_create(const sem_mesh *mesh, double Re, void *d_workspace, size_t byt
 int sem_ns_destroy(sem_ns *ns);
 /* Set the velocity (device, 3*nloc, continuous), clear the history. */
 int sem_ns_set_velocity(sem_ns *ns, const double *u, void *stream);
-/* Copy a state field to dst (device, nloc): 0..2 velocity, 3 pressure p^n,
- * 4 pressure p^{n-1}, 5 pressure p^{n-2}, 6 the last pressure right-hand
- * side (assembled, zero mean). */
+/* Copy a state field to dst (device, nloc): 0..2 velocity u^n, 3 pressure
+ * p^n, 4 pressure p^{n-1}, 5 pressure p^{n-2}, 6 the last pressure right-
+ * hand side (assembled, zero mean), 7..9 velocity u^{n-1}, 10..12 advection
+ * term NL^{n-1}.  sem_ns_set writes the same slots (checkpoint restore);
+ * with sem_ns_get_steps / sem_ns_set_steps they hold the whole state. */
 int sem_ns_get(const sem_ns *ns, int which, double *dst, void *stream);
+int sem_ns_set(sem_ns *ns, int which, const double *src, void *stream);
+int sem_ns_get_steps(const sem_ns *ns);
+int sem_ns_set_steps(sem_ns *ns, int steps);
 /* Scratch for sem_ns_step with these solver options. */
 size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts);
 /* One time step.  popts / vopts: pressure / velocity solver options (the
@@ -282,6 +288,15 @@ size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const s
 int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_opts *vopts,
                 const double *p_guess, sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *d_scratch,
                 size_t scratch_bytes, void *stream);
+/* The same step in two calls, so that an initial guess can be built from
+ * the new pressure right-hand side (slot 6) before the solves:
+ * sem_ns_step_begin forms the advection term, the forcing and the pressure
+ * right-hand side; sem_ns_step_finish does the solves and the history
+ * update (arguments as sem_ns_step). */
+int sem_ns_step_begin(sem_ns *ns, double dt, void *stream);
+int sem_ns_step_finish(sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts,
+                       const double *p_guess, sem_pcg_stats *pstats, sem_pcg_stats *vstats,
+                       void *d_scratch, size_t scratch_bytes, void *stream);
 /* Kinetic energy (1/2V) int |u|^2 and its GLL quadrature, on the host
  * (waits for `stream`). */
 int sem_ns_kinetic_energy(const sem_ns *ns, double *energy, void *d_scratch, size_t scratch_bytes,
@@ -328,20 +343,25 @@ int sem_mlp_grad(sem_mlp *mlp, const void *X, const float *T, int rows, int rows
 /* One Adam step with the stored gradients. */
 int sem_mlp_adam(sem_mlp *mlp, double lr, double beta1, double beta2, double eps, void *stream);
 
-/* Features of the guess network for every element e (row e of X, BF16,
- * leading dimension ldx >= 4 npt): the last three pressures p1, p2, p3
- * divided by pscale and the pressure right-hand side divided by rscale
- * (E-layout device FP64 inputs). */
+/* The guess corrects the cubic extrapolation p_ext = 3 p1 - 3 p2 + p3 of the
+ * last three pressures.  sem_guess_residual: r = b - M Q Q^T A_L p_ext
+ * (FP64; work: nloc doubles, receives p_ext).  The error the guess must
+ * remove, e = p - p_ext, satisfies A e = r. */
+int sem_guess_residual(const sem_mesh *mesh, const double *b, const double *p1, const double *p2,
+                       const double *p3, double *r, double *work, void *stream);
+/* Features for every element e (row e of X, BF16, ldx >= 4 npt):
+ * (p1 - p2)/sd, (p2 - p3)/sd, r/sr and, with p4 (the pressure four steps
+ * back) given, the previous step's extrapolation error (third difference)
+ * (p1 - 3 p2 + 3 p3 - p4)/s4, else p1/s4, at the element's points. */
 int sem_guess_features(const sem_mesh *mesh, const double *p1, const double *p2, const double *p3,
-                       const double *rhs, double pscale, double rscale, void *X, int ldx, void *stream);
-/* Training target T[e][q] = (p - (3 p1 - 3 p2 + p3)) / pscale (FP32, ldt >= npt):
- * the correction to the cubic extrapolation. */
+                       const double *p4, const double *r, double sd, double sr, double s4, void *X, int ldx,
+                       void *stream);
+/* Training target T[e][q] = (p - p_ext) / se (FP32, ldt >= npt). */
 int sem_guess_target(const sem_mesh *mesh, const double *p, const double *p1, const double *p2,
-                     const double *p3, double pscale, float *T, int ldt, void *stream);
-/* Guess = (Q Q^T g) / mult with g = 3 p1 - 3 p2 + p3 + pscale Y (continuous
- * FP64 E-layout output). */
+                     const double *p3, double se, float *T, int ldt, void *stream);
+/* Guess = (Q Q^T g) / mult with g = p_ext + se Y (continuous FP64 E-layout). */
 int sem_guess_apply(const sem_mesh *mesh, const float *Y, int ldy, const double *p1, const double *p2,
-                    const double *p3, double pscale, double *guess, void *stream);
+                    const double *p3, double se, double *guess, void *stream);
 
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */

@@ -56,7 +56,8 @@ class PcgStats(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("abs_res", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("ax_ms", ctypes.c_double), ("gs_ms", ctypes.c_double),
                 ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
-                ("outer_ax_ms", ctypes.c_double), ("outer_ax_launches", ctypes.c_int)]
+                ("outer_ax_ms", ctypes.c_double), ("outer_ax_launches", ctypes.c_int),
+                ("init_rel_res", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,8 +101,15 @@ _SIGS = {
     "sem_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                       _VP], ctypes.c_int),
     "sem_mlp_adam": ([_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
-    "sem_guess_features": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, ctypes.c_int, _VP],
-                           ctypes.c_int),
+    "sem_guess_residual": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_guess_features": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            _VP, ctypes.c_int, _VP], ctypes.c_int),
+    "sem_ns_step_begin": ([_VP, ctypes.c_double, _VP], ctypes.c_int),
+    "sem_ns_step_finish": ([_VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgOpts), _VP, ctypes.POINTER(PcgStats),
+                            ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_ns_set": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "sem_ns_get_steps": ([_VP], ctypes.c_int),
+    "sem_ns_set_steps": ([_VP, ctypes.c_int], ctypes.c_int),
     "sem_guess_target": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int, _VP], ctypes.c_int),
     "sem_guess_apply": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, _VP, _VP], ctypes.c_int),
     "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -379,6 +387,35 @@ class NSState:
                                 ctypes.byref(ps), vs, _VP(base), nbytes, _stream()), "sem_ns_step")
         return ps.as_dict(), [v.as_dict() for v in vs]
 
+    def step_begin(self, dt):
+        check(lib().sem_ns_step_begin(self.handle, float(dt), _stream()), "sem_ns_step_begin")
+
+    def step_finish(self, popts: PcgOpts, vopts: PcgOpts, p_guess=None):
+        import torch
+        need = lib().sem_ns_scratch_bytes(self.handle, ctypes.byref(popts), ctypes.byref(vopts))
+        if self._scratch is None or self._scratch.numel() < need + 256:
+            self._scratch = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        base = (self._scratch.data_ptr() + 255) // 256 * 256
+        nbytes = self._scratch.numel() - (base - self._scratch.data_ptr())
+        ps = PcgStats()
+        vs = (PcgStats * 3)()
+        guess = _ptr(p_guess) if p_guess is not None else None
+        check(lib().sem_ns_step_finish(self.handle, ctypes.byref(popts), ctypes.byref(vopts), guess,
+                                       ctypes.byref(ps), vs, _VP(base), nbytes, _stream()), "sem_ns_step_finish")
+        return ps.as_dict(), [v.as_dict() for v in vs]
+
+    SLOTS = 13
+
+    def checkpoint(self):
+        """Device copies of every state field plus the step count."""
+        return [self.get(w) for w in range(self.SLOTS)], lib().sem_ns_get_steps(self.handle)
+
+    def restore(self, ck):
+        fields, steps = ck
+        for w, f in enumerate(fields):
+            check(lib().sem_ns_set(self.handle, w, _ptr(f), _stream()), "sem_ns_set")
+        check(lib().sem_ns_set_steps(self.handle, int(steps)), "sem_ns_set_steps")
+
     def kinetic_energy(self) -> float:
         e = ctypes.c_double()
         base = (self._red.data_ptr() + 255) // 256 * 256
@@ -480,9 +517,15 @@ class MLP:
               "sem_mlp_adam")
 
 
-def guess_features(mesh, p1, p2, p3, rhs, pscale, rscale, X):
-    check(lib().sem_guess_features(mesh.handle, _ptr(p1), _ptr(p2), _ptr(p3), _ptr(rhs), float(pscale),
-                                   float(rscale), _ptr(X), X.shape[1], _stream()), "sem_guess_features")
+def guess_residual(mesh, b, p1, p2, p3, r, work):
+    check(lib().sem_guess_residual(mesh.handle, _ptr(b), _ptr(p1), _ptr(p2), _ptr(p3), _ptr(r), _ptr(work),
+                                   _stream()), "sem_guess_residual")
+
+
+def guess_features(mesh, p1, p2, p3, p4, r, sd, sr, s3, X):
+    check(lib().sem_guess_features(mesh.handle, _ptr(p1), _ptr(p2), _ptr(p3),
+                                   _ptr(p4) if p4 is not None else None, _ptr(r), float(sd), float(sr), float(s3),
+                                   _ptr(X), X.shape[1], _stream()), "sem_guess_features")
 
 
 def guess_target(mesh, p, p1, p2, p3, pscale, T):

@@ -10,10 +10,11 @@
 // FP32 accumulation); the FP32 master parameters, gradients and Adam moments
 // live in one flat array [W1, b1, W2, b2, W3, b3].
 //
-// The guess itself (features from the last three pressures and the
-// right-hand side, target = correction to the cubic extrapolation, and the
-// continuous guess from the network output) is built by the sem_guess_*
-// kernels at the end of this file.
+// The guess corrects the cubic extrapolation p_ext = 3 p1 - 3 p2 + p3 of the
+// last three pressures; the sem_guess_* kernels at the end of this file form
+// the residual r = b - A p_ext, the per-element features ((p1-p2), (p2-p3),
+// r and the previous third difference, each with its own scale), the
+// training target (p - p_ext)/se and the continuous guess p_ext + se Y.
 
 #include <cuda_bf16.h>
 
@@ -367,21 +368,36 @@ int sem_mlp_adam(sem_mlp *n, double lr, double beta1, double beta2, double eps, 
 
 namespace sem {
 
-// X[e][q], q < 4 npt: (p1, p2, p3) / pscale and rhs / rscale of element e;
-// columns beyond 4 npt are left as they are (zero from the caller).
+// X[e][q], q < 4 npt: (p1 - p2)/sd, (p2 - p3)/sd, r/sr and
+// (p1 - 3 p2 + 3 p3 - p4)/s3 (p1/s3 when p4 is null) of element e; columns
+// beyond 4 npt are left as they are (zero from the caller).
 __global__ void guess_features_kernel(const double *__restrict__ p1, const double *__restrict__ p2,
-                                      const double *__restrict__ p3, const double *__restrict__ rhs, int64_t E,
-                                      int npt, double ips, double irs, bf16 *__restrict__ X, int ldx) {
+                                      const double *__restrict__ p3, const double *__restrict__ p4,
+                                      const double *__restrict__ r, int64_t E, int npt, double isd, double isr,
+                                      double is3, bf16 *__restrict__ X, int ldx) {
     const int64_t n = E * npt;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = l / npt;
         const int q = (int)(l - e * npt);
         bf16 *row = X + e * ldx;
-        row[q] = __float2bfloat16_rn((float)(p1[l] * ips));
-        row[npt + q] = __float2bfloat16_rn((float)(p2[l] * ips));
-        row[2 * npt + q] = __float2bfloat16_rn((float)(p3[l] * ips));
-        row[3 * npt + q] = __float2bfloat16_rn((float)(rhs[l] * irs));
+        row[q] = __float2bfloat16_rn((float)((p1[l] - p2[l]) * isd));
+        row[npt + q] = __float2bfloat16_rn((float)((p2[l] - p3[l]) * isd));
+        row[2 * npt + q] = __float2bfloat16_rn((float)(r[l] * isr));
+        const double f4 = p4 ? p1[l] - 3.0 * p2[l] + 3.0 * p3[l] - p4[l] : p1[l];
+        row[3 * npt + q] = __float2bfloat16_rn((float)(f4 * is3));
     }
+}
+
+__global__ void extrap_kernel(const double *__restrict__ p1, const double *__restrict__ p2,
+                              const double *__restrict__ p3, int64_t n, double *__restrict__ out) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+        out[l] = 3.0 * p1[l] - 3.0 * p2[l] + p3[l];
+}
+
+__global__ void sub_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                           double *__restrict__ out) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+        out[l] = a[l] - b[l];
 }
 
 // T[e][q] = (p - (3 p1 - 3 p2 + p3)) / pscale
@@ -417,12 +433,28 @@ __global__ void scale_by_kernel(double *__restrict__ g, const double *__restrict
 
 extern "C" {
 
-int sem_guess_features(const sem_mesh *m, const double *p1, const double *p2, const double *p3, const double *rhs,
-                       double pscale, double rscale, void *X, int ldx, void *stream) {
-    if (!m || !p1 || !p2 || !p3 || !rhs || !X) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
-    if (ldx < 4 * m->npt || !(pscale > 0) || !(rscale > 0)) return fail(SEM_ERR_INVALID_ARG, "ldx < 4 npt or scale <= 0");
-    guess_features_kernel<<<gridn(m->nloc), 256, 0, as_stream(stream)>>>(p1, p2, p3, rhs, m->E, m->npt, 1.0 / pscale,
-                                                                          1.0 / rscale, static_cast<bf16 *>(X), ldx);
+int sem_guess_residual(const sem_mesh *m, const double *b, const double *p1, const double *p2, const double *p3,
+                       double *r, double *work, void *stream) {
+    if (!m || !b || !p1 || !p2 || !p3 || !r || !work || r == work) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = as_stream(stream);
+    extrap_kernel<<<gridn(m->nloc), 256, 0, st>>>(p1, p2, p3, m->nloc, work);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    int s = ax_launch_f64(m, work, r, 1.0, 0.0, st);
+    if (s != SEM_OK) return s;
+    s = gs_launch(m, r, SEM_F64, kGsSumMask, st);
+    if (s != SEM_OK) return s;
+    sub_kernel<<<gridn(m->nloc), 256, 0, st>>>(b, r, m->nloc, r);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+int sem_guess_features(const sem_mesh *m, const double *p1, const double *p2, const double *p3, const double *p4,
+                       const double *r, double sd, double sr, double s3, void *X, int ldx, void *stream) {
+    if (!m || !p1 || !p2 || !p3 || !r || !X) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (ldx < 4 * m->npt || !(sd > 0) || !(sr > 0) || !(s3 > 0))
+        return fail(SEM_ERR_INVALID_ARG, "ldx < 4 npt or a scale <= 0");
+    guess_features_kernel<<<gridn(m->nloc), 256, 0, as_stream(stream)>>>(
+        p1, p2, p3, p4, r, m->E, m->npt, 1.0 / sd, 1.0 / sr, 1.0 / s3, static_cast<bf16 *>(X), ldx);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }

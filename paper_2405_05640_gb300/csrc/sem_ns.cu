@@ -37,6 +37,8 @@ struct sem_ns {
     double *red;    // reduction partials and results
     double last_h2;
     size_t ws_bytes;
+    int begun;        // sem_ns_step_begin done, finish pending
+    double begun_dt;
 };
 
 namespace sem {
@@ -386,6 +388,8 @@ static size_t ns_red_bytes() { return align_up(sizeof(double) * (2 * kNsRedBlock
 
 using namespace sem;
 
+static double *ns_slot(const sem_ns *ns, int which);
+
 extern "C" {
 
 int sem_gradient(const sem_mesh *m, const double *f, double *g, void *stream) {
@@ -490,11 +494,8 @@ int sem_ns_set_velocity(sem_ns *ns, const double *u, void *stream) {
 
 int sem_ns_get(const sem_ns *ns, int which, double *dst, void *stream) {
     if (!ns || !dst) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
-    const double *src = nullptr;
-    if (which >= 0 && which < 3) src = ns->u[which];
-    else if (which >= 3 && which < 6) src = ns->ph[which - 3];
-    else if (which == 6) src = ns->bp;
-    else return fail(SEM_ERR_INVALID_ARG, "unknown field");
+    const double *src = ns_slot(ns, which);
+    if (!src) return fail(SEM_ERR_INVALID_ARG, "unknown field");
     SEM_CUDA_CHECK(cudaMemcpyAsync(dst, src, sizeof(double) * ns->m->nloc, cudaMemcpyDeviceToDevice,
                                    as_stream(stream)));
     return SEM_OK;
@@ -506,20 +507,15 @@ size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const s
     return a > b ? a : b;
 }
 
-int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_opts *vopts,
-                const double *p_guess, sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *scratch,
-                size_t scratch_bytes, void *stream) {
-    if (!ns || !popts || !vopts || !pstats || !vstats || !scratch || !(dt > 0.0))
-        return fail(SEM_ERR_INVALID_ARG, "NULL argument or dt <= 0");
+int sem_ns_step_begin(sem_ns *ns, double dt, void *stream) {
+    if (!ns || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "NULL state or dt <= 0");
     const sem_mesh *m = ns->m;
     cudaStream_t st = as_stream(stream);
     const int k = ns->steps == 0 ? 1 : 2;
-    const double b0 = k == 1 ? 1.0 : 1.5;
     const double s1 = (k == 1 ? 1.0 : 2.0) / dt, s2 = (k == 1 ? 0.0 : -0.5) / dt;
     const double a1 = k == 1 ? 1.0 : 2.0, a2 = k == 1 ? 0.0 : -1.0;
-    int s;
     // advection at t^n, forcing, weak divergence -> pressure right-hand side
-    s = launch_advect(m, ns->u, ns->nl, st);
+    int s = launch_advect(m, ns->u, ns->nl, st);
     if (s != SEM_OK) return s;
     s = launch_force_wdiv(m, ns->u, ns->uprev, ns->nl, ns->nlprev, s1, s2, a1, a2, k, ns->F, ns->bp, st);
     if (s != SEM_OK) return s;
@@ -527,6 +523,21 @@ int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_
     if (s != SEM_OK) return s;
     s = remove_mean(m, ns->bp, ns->red, st);
     if (s != SEM_OK) return s;
+    ns->begun = 1;
+    ns->begun_dt = dt;
+    return SEM_OK;
+}
+
+int sem_ns_step_finish(sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts, const double *p_guess,
+                       sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *scratch, size_t scratch_bytes,
+                       void *stream) {
+    if (!ns || !popts || !vopts || !pstats || !vstats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (!ns->begun) return fail(SEM_ERR_INVALID_ARG, "sem_ns_step_finish without sem_ns_step_begin");
+    const sem_mesh *m = ns->m;
+    cudaStream_t st = as_stream(stream);
+    const double dt = ns->begun_dt;
+    const double b0 = ns->steps == 0 ? 1.0 : 1.5;
+    int s;
     // pressure: solve into the oldest history slot
     double *pn = ns->ph[2];
     sem_pcg_opts po = *popts;
@@ -584,6 +595,46 @@ int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_
     ns->ph[1] = ns->ph[0];
     ns->ph[0] = pold;
     ns->steps += 1;
+    ns->begun = 0;
+    return SEM_OK;
+}
+
+int sem_ns_step(sem_ns *ns, double dt, const sem_pcg_opts *popts, const sem_pcg_opts *vopts,
+                const double *p_guess, sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *scratch,
+                size_t scratch_bytes, void *stream) {
+    int s = sem_ns_step_begin(ns, dt, stream);
+    if (s != SEM_OK) return s;
+    return sem_ns_step_finish(ns, popts, vopts, p_guess, pstats, vstats, scratch, scratch_bytes, stream);
+}
+
+}  // extern "C"
+
+static double *ns_slot(const sem_ns *ns, int which) {
+    if (which >= 0 && which < 3) return ns->u[which];
+    if (which >= 3 && which < 6) return ns->ph[which - 3];
+    if (which == 6) return ns->bp;
+    if (which >= 7 && which < 10) return ns->uprev[which - 7];
+    if (which >= 10 && which < 13) return ns->nlprev[which - 10];
+    return nullptr;
+}
+
+extern "C" {
+
+int sem_ns_set(sem_ns *ns, int which, const double *src, void *stream) {
+    if (!ns || !src) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    double *dst = ns_slot(ns, which);
+    if (!dst) return fail(SEM_ERR_INVALID_ARG, "unknown field");
+    SEM_CUDA_CHECK(cudaMemcpyAsync(dst, src, sizeof(double) * ns->m->nloc, cudaMemcpyDeviceToDevice,
+                                   as_stream(stream)));
+    return SEM_OK;
+}
+
+int sem_ns_get_steps(const sem_ns *ns) { return ns ? ns->steps : -1; }
+
+int sem_ns_set_steps(sem_ns *ns, int steps) {
+    if (!ns || steps < 0) return fail(SEM_ERR_INVALID_ARG, "NULL state or steps < 0");
+    ns->steps = steps;
+    ns->begun = 0;
     return SEM_OK;
 }
 

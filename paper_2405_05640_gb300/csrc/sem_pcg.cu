@@ -477,6 +477,7 @@ static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_
     if (s != SEM_OK) return s;
     stats->iters = h.iter;
     stats->outer_iters = 0;
+    stats->init_rel_res = h.bb > 0 ? std::sqrt(h.rr0 / h.bb) : std::sqrt(h.rr0);
     stats->bnorm = std::sqrt(h.bb);
     stats->abs_res = std::sqrt(h.rr);
     stats->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : stats->abs_res;
@@ -518,6 +519,7 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
     while (true) {
         SEM_CUDA_CHECK(cudaMemcpyAsync(&ho, M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
         SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        if (outer == 0) stats->init_rel_res = ho.bb > 0 ? std::sqrt(ho.rr / ho.bb) : std::sqrt(ho.rr);
         c.tax.harvest();
         c.tgs.harvest();
         if (ho.done) {

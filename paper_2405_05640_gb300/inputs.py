@@ -218,7 +218,8 @@ def batched_cases(nsolve: int = 64, seed: int = 0, emin: int = 8 ** 3, emax: int
 
 def mlp_init(n_in: int, n_hidden: int, n_out: int, seed: int = 0) -> dict:
     """Seeded initial parameters of the element-local network (He-uniform
-    weights, zero biases), FP32: W1 [H, I], b1 [H], W2 [H, H], b2 [H],
+    weights, the output layer scaled by 0.01 so that training starts near the
+    zero correction; zero biases), FP32: W1 [H, I], b1 [H], W2 [H, H], b2 [H],
     W3 [O, H], b3 [O]."""
     rng = np.random.Generator(np.random.PCG64(seed))
 
@@ -228,4 +229,4 @@ def mlp_init(n_in: int, n_hidden: int, n_out: int, seed: int = 0) -> dict:
 
     return {"W1": he(n_hidden, n_in), "b1": np.zeros(n_hidden, np.float32),
             "W2": he(n_hidden, n_hidden), "b2": np.zeros(n_hidden, np.float32),
-            "W3": he(n_out, n_hidden) * np.float32(0.1), "b3": np.zeros(n_out, np.float32)}
+            "W3": he(n_out, n_hidden) * np.float32(0.01), "b3": np.zeros(n_out, np.float32)}

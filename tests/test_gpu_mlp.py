@@ -81,27 +81,38 @@ def test_training_reduces_loss():
 
 def test_guess_kernels_match_definitions():
     torch = _t()
+    import oracle
     case = inputs.tgv_box(3, 5)
     gm = binding.Mesh(5, case.nel, case.periodic, case.faces, case.vertices())
+    om = oracle.Mesh(5, case.nel, case.periodic, case.faces, case.vertices())
     E, npt = gm.E, gm.npt
     rng = np.random.default_rng(9)
-    f = [rng.standard_normal(gm.nloc) for _ in range(5)]
+    f = [om.scatter(rng.standard_normal(om.nglob)) for _ in range(5)]  # continuous fields
     d = [torch.from_numpy(a).cuda() for a in f]
+    ext = 3 * f[0] - 3 * f[1] + f[2]
+    # residual of the extrapolation: b - A p_ext
+    r = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
+    work = torch.empty_like(r)
+    binding.guess_residual(gm, d[3], d[0], d[1], d[2], r, work)
+    ref_r = f[3] - om.apply(ext)
+    assert np.linalg.norm(r.cpu().numpy() - ref_r) <= 1e-12 * np.linalg.norm(ref_r)
     ldx = 4 * npt + 40
     X = torch.zeros((E, ldx), dtype=torch.bfloat16, device="cuda")
-    binding.guess_features(gm, d[0], d[1], d[2], d[3], 2.0, 4.0, X)
-    Xr = np.concatenate([f[0].reshape(E, npt) / 2, f[1].reshape(E, npt) / 2, f[2].reshape(E, npt) / 2,
-                         f[3].reshape(E, npt) / 4], axis=1)
+    binding.guess_features(gm, d[0], d[1], d[2], d[4], r, 2.0, 4.0, 8.0, X)
+    rr = r.cpu().numpy()
+    d3 = f[0] - 3 * f[1] + 3 * f[2] - f[4]
+    Xr = np.concatenate([((f[0] - f[1]) / 2).reshape(E, npt), ((f[1] - f[2]) / 2).reshape(E, npt),
+                         (rr / 4).reshape(E, npt), (d3 / 8).reshape(E, npt)], axis=1)
     np.testing.assert_array_equal(X[:, :4 * npt].float().cpu().numpy(), _bf16_round(Xr))
     assert float(X[:, 4 * npt:].abs().max()) == 0.0
+    binding.guess_features(gm, d[0], d[1], d[2], None, r, 2.0, 4.0, 8.0, X)  # fourth field p1
+    Xr[:, 3 * npt:] = (f[0] / 8).reshape(E, npt)
+    np.testing.assert_array_equal(X[:, :4 * npt].float().cpu().numpy(), _bf16_round(Xr))
     T = torch.zeros((E, npt + 8), dtype=torch.float32, device="cuda")
     binding.guess_target(gm, d[4], d[0], d[1], d[2], 2.0, T)
-    ext = 3 * f[0] - 3 * f[1] + f[2]
     np.testing.assert_allclose(T[:, :npt].cpu().numpy(), ((f[4] - ext) / 2).reshape(E, npt), rtol=1e-6, atol=1e-6)
     Y = torch.from_numpy(rng.standard_normal((E, npt + 8)).astype(np.float32)).cuda()
     g = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
     binding.guess_apply(gm, Y, d[0], d[1], d[2], 2.0, g)
     loc = ext + 2.0 * Y[:, :npt].double().cpu().numpy().reshape(-1)
-    import oracle
-    om = oracle.Mesh(5, case.nel, case.periodic, case.faces, case.vertices())
-    np.testing.assert_allclose(g.cpu().numpy(), om.dssum(loc) / om.mult, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(g.cpu().numpy(), om.dssum(loc) / om.mult, rtol=1e-13, atol=1e-13)
