@@ -363,6 +363,41 @@ int sem_guess_target(const sem_mesh *mesh, const double *p, const double *p1, co
 int sem_guess_apply(const sem_mesh *mesh, const float *Y, int ldy, const double *p1, const double *p2,
                     const double *p3, double se, double *guess, void *stream);
 
+/* ---- Batched solves ------------------------------------------------------
+ * nsolve independent systems (meshes[i], b[i], x[i]; device FP64 E-layout;
+ * meshes may differ in size and order) solved together by the mixed solver
+ * (opts->precision must be SEM_PCG_MIXED, every mesh built with
+ * SEM_GEOM_F32, x starts from 0).  All decisions of the solver run on the
+ * device per solve; check_every FP32 iterations of every unfinished solve
+ * plus one FP64 refinement stage form a round, captured once into a CUDA
+ * graph (each solve a parallel branch) and replayed until every solve has
+ * finished.  stats[i] (host) as for sem_pcg_solve, with wall_ms = the time
+ * from the call until solve i was seen finished (round granularity).
+ * Waits for `stream`.  Returns SEM_OK when all converged. */
+size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, const sem_pcg_opts *opts);
+int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b,
+                          double *const *x, const sem_pcg_opts *opts, sem_pcg_stats *stats,
+                          void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* ---- Autotuner of the operator launch shape -------------------------------
+ * Times the operator of `mesh` (precision dtype, plain or fused CG form)
+ * over pipeline depths {1, 2, 3} x resident-CTAs-per-SM caps {none, 1, 2, 4}
+ * and keeps the fastest for the mesh's order N in the library's launch table
+ * (process-wide, all meshes of that order use it).  Scratch: device,
+ * sem_autotune_scratch_bytes.  Waits for `stream`.  Not from the paper. */
+typedef struct {
+    int best_stages, best_cap;
+    float best_ms;
+    int configs;
+    int stages[16], caps[16];
+    float ms[16];
+} sem_tune_result;
+size_t sem_autotune_scratch_bytes(const sem_mesh *mesh);
+int sem_autotune_operator(const sem_mesh *mesh, int dtype, int fused_cg, void *d_scratch, size_t bytes,
+                          void *stream, sem_tune_result *out);
+/* Back to the default launch shapes (2 stages, occupancy-limited). */
+int sem_autotune_reset(void);
+
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */
 int sem_mesh_check_device_error(const sem_mesh *mesh, int *code, void *stream);

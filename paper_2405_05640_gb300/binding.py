@@ -63,6 +63,12 @@ class PcgStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best_stages", ctypes.c_int), ("best_cap", ctypes.c_int), ("best_ms", ctypes.c_float),
+                ("configs", ctypes.c_int), ("stages", ctypes.c_int * 16), ("caps", ctypes.c_int * 16),
+                ("ms", ctypes.c_float * 16)]
+
+
 _VP = ctypes.c_void_p
 _SIGS = {
     "sem_version": ([], ctypes.c_char_p),
@@ -112,6 +118,13 @@ _SIGS = {
     "sem_ns_set_steps": ([_VP, ctypes.c_int], ctypes.c_int),
     "sem_guess_target": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int, _VP], ctypes.c_int),
     "sem_guess_apply": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, _VP, _VP], ctypes.c_int),
+    "sem_pcg_batched_scratch_bytes": ([_VP, ctypes.c_int, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
+    "sem_pcg_solve_batched": ([_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(PcgOpts), _VP, _VP, ctypes.c_size_t, _VP],
+                              ctypes.c_int),
+    "sem_autotune_scratch_bytes": ([_VP], ctypes.c_size_t),
+    "sem_autotune_operator": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(TuneResult)],
+                              ctypes.c_int),
+    "sem_autotune_reset": ([], ctypes.c_int),
     "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_weak_div": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -316,6 +329,19 @@ class Mesh:
         if raise_on_error and status != SEM_OK:
             raise SemError(status, "sem_pcg_solve_host")
         return x_host, st.as_dict()
+
+    def autotune(self, dtype=SEM_F32, fused_cg=True):
+        """sem_autotune_operator for this mesh's order; returns the result dict."""
+        import torch
+        n = lib().sem_autotune_scratch_bytes(self.handle)
+        scr = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        base = (scr.data_ptr() + 255) // 256 * 256
+        r = TuneResult()
+        check(lib().sem_autotune_operator(self.handle, int(dtype), int(bool(fused_cg)), _VP(base), n, _stream(),
+                                          ctypes.byref(r)), "sem_autotune_operator")
+        k = min(r.configs, 16)
+        return {"best_stages": r.best_stages, "best_cap": r.best_cap, "best_ms": r.best_ms,
+                "table": [(r.stages[i], r.caps[i], r.ms[i]) for i in range(k)]}
 
     # ---- Navier-Stokes building blocks
     def gradient(self, f):
@@ -536,3 +562,26 @@ def guess_target(mesh, p, p1, p2, p3, pscale, T):
 def guess_apply(mesh, Y, p1, p2, p3, pscale, out):
     check(lib().sem_guess_apply(mesh.handle, _ptr(Y), Y.shape[1], _ptr(p1), _ptr(p2), _ptr(p3), float(pscale),
                                 _ptr(out), _stream()), "sem_guess_apply")
+
+
+def pcg_solve_batched(meshes, bs, xs=None, scratch=None, raise_on_error=True, **kw):
+    """sem_pcg_solve_batched over lists of Mesh and device FP64 right-hand
+    sides; returns (xs, list of stats dicts)."""
+    import torch
+    n = len(meshes)
+    opts = meshes[0].pcg_opts(precision=SEM_PCG_MIXED, **kw)
+    mh = (_VP * n)(*[m.handle.value for m in meshes])
+    if xs is None:
+        xs = [torch.empty_like(bi) for bi in bs]
+    bh = (_VP * n)(*[bi.data_ptr() for bi in bs])
+    xh = (_VP * n)(*[xi.data_ptr() for xi in xs])
+    need = lib().sem_pcg_batched_scratch_bytes(mh, n, ctypes.byref(opts))
+    if scratch is None or scratch.numel() < need + 256:
+        scratch = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    base = (scratch.data_ptr() + 255) // 256 * 256
+    stats = (PcgStats * n)()
+    st = lib().sem_pcg_solve_batched(mh, n, bh, xh, ctypes.byref(opts), stats, _VP(base),
+                                     scratch.numel() - (base - scratch.data_ptr()), _stream())
+    if raise_on_error and st != SEM_OK:
+        raise SemError(st, "sem_pcg_solve_batched")
+    return xs, [s.as_dict() for s in stats]

@@ -46,7 +46,20 @@ struct AxArgs {
     int nst;      // pipeline stages (1..3)
     int use_tma;  // 1: bulk-copy staging; 0: plain cooperative loads
     double h1, h2;
+    const int *guard;  // if set, the kernel runs only when *guard == guard_value
+    int guard_value;
 };
+
+// Launch shape of the operator per (precision, Helmholtz, fused CG, N):
+// pipeline stages and a cap on resident CTAs per SM (0 = occupancy limit).
+// Defaults: 2 stages, no cap; sem_autotune_operator measures and sets them.
+AxTune g_ax_tune[2][2][2][kMaxN1] = {};
+
+static AxTune tune_for(int dt, bool helm, bool cg, int N) {
+    AxTune t = g_ax_tune[dt][helm][cg][N];
+    if (t.nst <= 0) t.nst = 2;
+    return t;
+}
 
 // One element per CTA at a time (persistent grid).  Modes:
 //   plain / HELM: w = A_L u  (or h1 A_L u + h2 B u);
@@ -61,7 +74,8 @@ __global__ void __launch_bounds__(ax_threads<N>())
     constexpr int SB = ax_stage_bytes<N, T, HELM, CG>();
     constexpr int NIN = CG ? 3 : 1;  // input slabs
     extern __shared__ __align__(128) unsigned char smem[];
-    if (CG && cg.scal->done) return;  // uniform: the solve has converged
+    if (CG && cg.scal->done) return;  // uniform: the solve has converged or paused
+    if (args.guard && *args.guard != args.guard_value) return;  // uniform: not this phase
     const int nst = args.nst;
     T *svr = reinterpret_cast<T *>(smem + nst * SB);
     T *svs = svr + NPT;
@@ -253,13 +267,14 @@ __global__ void __launch_bounds__(ax_threads<N>())
 
 template <int N, typename T, bool HELM, bool CG, typename DM>
 static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
-                       const DM &Dm, const CgFuse<T> &cg, cudaStream_t st) {
+                       const DM &Dm, const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st) {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
     constexpr int threads = ax_threads<N>();
     auto kern = ax_kernel<N, T, HELM, CG, DM>;
     int dev_max = 0;
     SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    int nst = 2;
+    const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, N);
+    int nst = tune.nst < 1 ? 1 : (tune.nst > 3 ? 3 : tune.nst);
     while (nst > 1 && ax_smem_bytes<N, T, HELM, CG>(nst) > dev_max) --nst;
     const int smem = ax_smem_bytes<N, T, HELM, CG>(nst);
     if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
@@ -267,6 +282,7 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
     int per_sm = 0;
     SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) per_sm = 1;
+    if (tune.per_sm_cap > 0 && per_sm > tune.per_sm_cap) per_sm = tune.per_sm_cap;
     int64_t grid = (int64_t)m->num_sms * per_sm;
     if (grid > kAxMaxGrid) grid = kAxMaxGrid;
     if (grid > m->E) grid = m->E;
@@ -275,6 +291,8 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
     a.nst = nst;
     a.h1 = h1;
     a.h2 = h2;
+    a.guard = guard;
+    a.guard_value = gval;
     uintptr_t al = reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(m->B);
     if (CG)
         al |= reinterpret_cast<uintptr_t>(cg.r) | reinterpret_cast<uintptr_t>(cg.dinv) |
@@ -289,10 +307,11 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
 
 template <typename T, bool HELM, bool CG, typename DM>
 static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
-                       const DM &Dm, const CgFuse<T> &cg, cudaStream_t st) {
+                       const DM &Dm, const CgFuse<T> &cg, cudaStream_t st, const int *guard = nullptr,
+                       int gval = 0) {
     switch (m->N) {
 #define SEM_AX_CASE(n) \
-    case n: return launch_ax_n<n, T, HELM, CG, DM>(m, u, w, G, h1, h2, Dm, cg, st);
+    case n: return launch_ax_n<n, T, HELM, CG, DM>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st);
         SEM_AX_CASE(1) SEM_AX_CASE(2) SEM_AX_CASE(3) SEM_AX_CASE(4) SEM_AX_CASE(5)
         SEM_AX_CASE(6) SEM_AX_CASE(7) SEM_AX_CASE(8) SEM_AX_CASE(9) SEM_AX_CASE(10) SEM_AX_CASE(11)
 #undef SEM_AX_CASE
@@ -300,10 +319,12 @@ static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h
     }
 }
 
-int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2, cudaStream_t st) {
+int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2, cudaStream_t st,
+                  const int *guard, int gval) {
     const CgFuse<double> none{};
-    if (h2 != 0.0 || h1 != 1.0) return dispatch_ax<double, true, false>(m, u, w, m->G, h1, h2, m->D, none, st);
-    return dispatch_ax<double, false, false>(m, u, w, m->G, 1.0, 0.0, m->D, none, st);
+    if (h2 != 0.0 || h1 != 1.0)
+        return dispatch_ax<double, true, false>(m, u, w, m->G, h1, h2, m->D, none, st, guard, gval);
+    return dispatch_ax<double, false, false>(m, u, w, m->G, 1.0, 0.0, m->D, none, st, guard, gval);
 }
 
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
@@ -360,9 +381,115 @@ int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st) {
     return SEM_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+// Time `reps` launches of the operator of mesh m (mode: plain or fused CG,
+// FP32 or FP64) with the current table entry; returns ms per launch.
+template <typename T, bool CG, typename DM>
+static int time_operator(const sem_mesh *m, const T *G, const DM &Dm, T *bufs, PcgScal *scal, double *partial,
+                         int reps, cudaStream_t st, float *ms) {
+    const int64_t n = m->nloc;
+    T *u = bufs, *w = bufs + n, *dinv = bufs + 2 * n, *pp = bufs + 3 * n;
+    CgFuse<T> cg{u, dinv, pp, scal, partial};
+    auto once = [&]() { return dispatch_ax<T, false, CG>(m, u, w, G, 1.0, 0.0, Dm, cg, st); };
+    for (int q = 0; q < 2; ++q) {
+        int s = once();
+        if (s != SEM_OK) return s;
+    }
+    cudaEvent_t a, b;
+    SEM_CUDA_CHECK(cudaEventCreate(&a));
+    SEM_CUDA_CHECK(cudaEventCreate(&b));
+    cudaEventRecord(a, st);
+    int s = SEM_OK;
+    for (int q = 0; q < reps && s == SEM_OK; ++q) s = once();
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != SEM_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    *ms = t / reps;
+    return SEM_OK;
+}
+
 }  // namespace sem
 
 using namespace sem;
+
+extern "C" {
+
+size_t sem_autotune_scratch_bytes(const sem_mesh *m) {
+    if (!m) return 0;
+    return align_up(sizeof(double) * 4 * m->nloc) + align_up(sizeof(PcgScal)) + align_up(sizeof(double) * kAxMaxGrid);
+}
+
+int sem_autotune_operator(const sem_mesh *m, int dtype, int fused_cg, void *scratch, size_t bytes, void *stream,
+                          sem_tune_result *out) {
+    if (!m || !scratch || !out) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (dtype != SEM_F64 && dtype != SEM_F32) return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
+    if (dtype == SEM_F32 && !m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
+    if (bytes < sem_autotune_scratch_bytes(m) || reinterpret_cast<uintptr_t>(scratch) % kAlign)
+        return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_autotune_scratch_bytes or misaligned");
+    cudaStream_t st = as_stream(stream);
+    char *p = static_cast<char *>(scratch);
+    SEM_CUDA_CHECK(cudaMemsetAsync(p, 0, sem_autotune_scratch_bytes(m), st));
+    void *bufs = p;
+    PcgScal *scal = reinterpret_cast<PcgScal *>(p + align_up(sizeof(double) * 4 * m->nloc));
+    double *partial = reinterpret_cast<double *>(p + align_up(sizeof(double) * 4 * m->nloc) + align_up(sizeof(PcgScal)));
+    const int dt = dtype == SEM_F64 ? 0 : 1, cg = fused_cg ? 1 : 0, N = m->N;
+    AxTune &slot = g_ax_tune[dt][0][cg][N];
+    const AxTune saved = slot;
+    const int stages[3] = {1, 2, 3}, caps[4] = {0, 1, 2, 4};
+    float best = 1e30f;
+    AxTune bt{2, 0};
+    out->configs = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 4; ++c) {
+            slot = AxTune{stages[a], caps[c]};
+            float ms = 0.f;
+            int s;
+            if (dt == 1 && cg)
+                s = time_operator<float, true>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st, &ms);
+            else if (dt == 1)
+                s = time_operator<float, false>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st, &ms);
+            else if (cg)
+                s = time_operator<double, true>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st, &ms);
+            else
+                s = time_operator<double, false>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st, &ms);
+            if (s != SEM_OK) {
+                slot = saved;
+                return s;
+            }
+            if (out->configs < 16) {
+                out->stages[out->configs] = stages[a];
+                out->caps[out->configs] = caps[c];
+                out->ms[out->configs] = ms;
+            }
+            ++out->configs;
+            if (ms < best) {
+                best = ms;
+                bt = slot;
+            }
+        }
+    slot = bt;
+    out->best_stages = bt.nst;
+    out->best_cap = bt.per_sm_cap;
+    out->best_ms = best;
+    return SEM_OK;
+}
+
+int sem_autotune_reset(void) {
+    for (auto &a : g_ax_tune)
+        for (auto &b : a)
+            for (auto &c : b)
+                for (auto &d : c) d = AxTune{0, 0};
+    return SEM_OK;
+}
+
+}  // extern "C"
+
 
 extern "C" {
 

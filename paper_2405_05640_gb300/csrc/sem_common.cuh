@@ -29,7 +29,9 @@ struct PcgScal {
     double scale;       // mixed precision: 1/||r|| of the outer residual (inner init)
     double scale_prev;  // mixed precision: the previous 1/||r||
     double rho_prev;    // rho of the iteration before the last update
+    double prev_rr;     // batched solver: FP64 residual of the previous refinement
     int iter, done, status, max_iter;
+    int phase;          // batched solver: kBt* state of this solve
     unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
 };
 
@@ -167,14 +169,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ---------------------------------------------------------------- host helpers
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
-                  cudaStream_t st);
+                  cudaStream_t st, const int *guard = nullptr, int gval = 0);
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st);
 // Fused CG operator (see CgFuse); w receives the local (unassembled) A_L p.
 int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
                      cudaStream_t st);
 int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st);
 constexpr int kAxMaxGrid = 152 * 32;  // upper bound of the operator grid (partials of the fused kernel)
-int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st);
+int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, const int *guard = nullptr,
+              int gval = 0);
+
+// Operator launch shape (see sem_ax.cu); g_ax_tune[dtype][helm][cg][N].
+struct AxTune {
+    int nst;         // pipeline stages, 0 = default (2)
+    int per_sm_cap;  // resident CTAs per SM cap, 0 = occupancy limit
+};
+extern AxTune g_ax_tune[2][2][2][kMaxN1];
 int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);
 
 // gather-scatter modes

@@ -22,7 +22,8 @@ namespace sem {
 
 template <typename T>
 __global__ void gs_kernel(T *__restrict__ u, const int *__restrict__ off, const int *__restrict__ idx,
-                          int64_t ngroups, int64_t nmasked, int mode) {
+                          int64_t ngroups, int64_t nmasked, int mode, const int *__restrict__ guard, int gval) {
+    if (guard && *guard != gval) return;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int a = off[g], b = off[g + 1];
@@ -37,17 +38,17 @@ __global__ void gs_kernel(T *__restrict__ u, const int *__restrict__ off, const 
     }
 }
 
-int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st) {
+int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, const int *guard, int gval) {
     const int64_t n = (mode == kGsMaskOnly) ? m->nmasked : m->ngroups;
     if (n == 0) return SEM_OK;
     int64_t g = (n + 255) / 256;
     if (g > (int64_t)m->num_sms * 32) g = (int64_t)m->num_sms * 32;
     if (dtype == SEM_F64)
         gs_kernel<double><<<(int)g, 256, 0, st>>>(static_cast<double *>(u), m->gs_off, m->gs_idx, n,
-                                                  m->nmasked, mode);
+                                                  m->nmasked, mode, guard, gval);
     else if (dtype == SEM_F32)
         gs_kernel<float><<<(int)g, 256, 0, st>>>(static_cast<float *>(u), m->gs_off, m->gs_idx, n,
-                                                 m->nmasked, mode);
+                                                 m->nmasked, mode, guard, gval);
     else
         return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
     SEM_CUDA_CHECK(cudaGetLastError());

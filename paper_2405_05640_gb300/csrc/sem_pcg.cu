@@ -589,6 +589,170 @@ static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const s
     return pcg_f64(m, b, x, o, stats, scratch, st);
 }
 
+// ---------------------------------------------------------------- batched solves
+//
+// Many independent mixed-precision solves advance together.  Every decision
+// of the solver runs on the device, per solve, as a phase:
+//   kBtIterate  FP32 CG iterations (the kernels return at once when the
+//               inner solve has paused: its residual fell by inner_tol);
+//   kBtRefine   x += ||r|| d (FP64), r = b - A x (FP64), convergence /
+//               stagnation / budget decision;
+//   kBtReliable swap the FP64 residual into the FP32 iteration, rescale p,
+//               recompute beta, resume;
+//   kBtFinished nothing more to do.
+// One "round" = K iterations of every solve followed by one refinement
+// stage; a round is captured once into a CUDA graph (each solve a parallel
+// branch) and replayed; the host reads the per-solve phases after each
+// replay (for completion times) and re-captures when half of the captured
+// solves have finished.
+
+constexpr int kBtIterate = 0, kBtRefine = 1, kBtReliable = 2, kBtFinished = 3;
+
+__global__ void bt_pause_kernel(const PcgScal *__restrict__ in, PcgScal *__restrict__ out) {
+    if (threadIdx.x == 0 && out->phase == kBtIterate && in->done) {
+        if (in->status == SEM_ERR_NAN) {
+            out->phase = kBtFinished;
+            out->status = SEM_ERR_NAN;
+        } else {
+            out->phase = kBtRefine;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPThreads)
+    bt_correct_kernel(double *__restrict__ x, float *__restrict__ d, int64_t n, const PcgScal *__restrict__ s) {
+    if (s->phase != kBtRefine) return;
+    const double nr = s->scale > 0.0 ? 1.0 / s->scale : 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        x[l] = fma((double)d[l], nr, x[l]);
+        d[l] = 0.0f;
+    }
+}
+
+// r = b - w (FP64); decide: converged -> finished (OK); inner budget spent
+// or no progress -> finished (not converged); else -> reliable update.
+__global__ void __launch_bounds__(kPThreads)
+    bt_residual_kernel(const double *__restrict__ b, const double *__restrict__ w, double *__restrict__ r,
+                       const double *__restrict__ minv, int64_t n, double *partial, PcgScal *s,
+                       const PcgScal *__restrict__ in) {
+    if (s->phase != kBtRefine) return;
+    double v[1] = {0.0};
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const double rl = b[l] - w[l];
+        r[l] = rl;
+        v[0] = fma(rl * rl, minv[l], v[0]);
+    }
+    double t[1];
+    if (grid_reduce<1>(v, partial, &s->cnt[0], t)) {
+        const double rr = t[0];
+        s->rr = rr;
+        s->scale_prev = s->scale;
+        s->scale = rr > 0.0 ? 1.0 / sqrt(rr) : 0.0;
+        s->iter += 1;  // refinements
+        if (!isfinite(rr)) {
+            s->phase = kBtFinished;
+            s->status = SEM_ERR_NAN;
+        } else if (rr <= s->tol2) {
+            s->phase = kBtFinished;
+            s->status = SEM_OK;
+        } else if (in->iter >= in->max_iter || (s->prev_rr > 0.0 && !(rr < 0.25 * s->prev_rr))) {
+            s->phase = kBtFinished;
+            s->status = SEM_ERR_NOT_CONVERGED;
+        } else {
+            s->phase = kBtReliable;
+        }
+        s->prev_rr = rr;
+    }
+}
+
+// the reliable update of ir_reliable_kernel, run only in phase kBtReliable;
+// the last block resumes the iteration.
+__global__ void __launch_bounds__(kPThreads)
+    bt_reliable_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
+                       int64_t n, PcgWork<float> W, PcgScal *so, double delta) {
+    if (so->phase != kBtReliable) return;
+    const double inv = so->scale;
+    const float c = (float)(so->scale / so->scale_prev);
+    float f0 = 0.f, f1 = 0.f;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const float r = (float)(r64[l] * inv);
+        W.r[l] = r;
+        W.p[l] *= c;
+        const float mi = minv[l];
+        f0 = fmaf(r * r, mi, f0);
+        f1 = fmaf(r * (dinv[l] * r), mi, f1);
+    }
+    double v[2] = {(double)f0, (double)f1}, t[2];
+    if (grid_reduce<2>(v, W.partial + 2 * kPBlocks, &W.scal->cnt[2], t)) {
+        PcgScal *s = W.scal;
+        const double cc = (double)c * (double)c;
+        s->rr = t[0];
+        s->beta = t[1] / (s->rho_prev * cc);
+        s->rho = t[1];
+        s->tol2 = delta * delta * t[0];
+        s->done = 0;
+        s->status = SEM_ERR_NOT_CONVERGED;
+        so->phase = kBtIterate;
+    }
+}
+
+// after the start: a solve whose right-hand side is already converged (or
+// holds a NaN) is finished, the others iterate
+__global__ void bt_start_kernel(PcgScal *s) {
+    if (threadIdx.x == 0) {
+        s->prev_rr = s->rr;
+        s->phase = s->done ? kBtFinished : kBtIterate;
+    }
+}
+
+// phases of all solves -> host-visible array and the unfinished count
+__global__ void bt_collect_kernel(PcgScal *const *__restrict__ outs, int nsolve, int *__restrict__ phases,
+                                  int *__restrict__ unfinished) {
+    if (blockIdx.x != 0) return;
+    int cnt = 0;
+    for (int i = threadIdx.x; i < nsolve; i += blockDim.x) {
+        const int ph = outs[i]->phase;
+        phases[i] = ph;
+        cnt += ph != kBtFinished;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (threadIdx.x == 0) *unfinished = cnt;
+}
+
+struct BtSolve {
+    const sem_mesh *m;
+    const double *b;
+    double *x;
+    MixedWork M;
+};
+
+// One round of solve i on stream st: K FP32 iterations, then the guarded
+// refinement stage.  Launch-time host work only; all state on the device.
+static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
+    const sem_mesh *m = S.m;
+    const int64_t n = m->nloc;
+    CgFuse<float> cg{S.M.in.r, m->dinv32, S.M.in.p, S.M.in.scal, S.M.in.partial + 4 * kPBlocks};
+    for (int q = 0; q < K; ++q) {
+        int s = ax_cg_launch_f32(m, cg, S.M.in.w, st);
+        if (s != SEM_OK) return s;
+        s = gs_launch(m, S.M.in.w, SEM_F32, kGsSumMask, st, &S.M.in.scal->done, 0);
+        if (s != SEM_OK) return s;
+        pcg_update_kernel<float><<<kPBlocks, kPThreads, 0, st>>>(S.M.d32, m->dinv32, m->minv32, n, S.M.in);
+    }
+    bt_pause_kernel<<<1, 32, 0, st>>>(S.M.in.scal, S.M.scal_out);
+    bt_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.x, S.M.d32, n, S.M.scal_out);
+    int s = ax_launch_f64(m, S.x, S.M.w64, 1.0, 0.0, st, &S.M.scal_out->phase, kBtRefine);
+    if (s != SEM_OK) return s;
+    s = gs_launch(m, S.M.w64, SEM_F64, kGsSumMask, st, &S.M.scal_out->phase, kBtRefine);
+    if (s != SEM_OK) return s;
+    bt_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.b, S.M.w64, S.M.r64, m->minv, n, S.M.partial_out,
+                                                       S.M.scal_out, S.M.in.scal);
+    bt_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
+                                                       o->inner_tol > 0.0 ? o->inner_tol : 1e-2);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
 }  // namespace sem
 
 using namespace sem;
@@ -648,6 +812,188 @@ int sem_pcg_solve_host(const sem_mesh *m, const double *hb, double *hx, const se
     stats->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (s != SEM_OK && s != SEM_ERR_CUDA) set_error(sem_status_string(s));
     return s;
+}
+
+
+size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, const sem_pcg_opts *o) {
+    if (!meshes || nsolve <= 0) return 0;
+    size_t t = align_up(sizeof(PcgScal *) * nsolve) + align_up(sizeof(int) * (nsolve + 1));
+    for (int i = 0; i < nsolve; ++i) {
+        if (!meshes[i]) return 0;
+        t += align_up(pcg_scratch_mixed(meshes[i]));
+    }
+    (void)o;
+    return t;
+}
+
+int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b, double *const *x,
+                          const sem_pcg_opts *o, sem_pcg_stats *stats, void *scratch, size_t scratch_bytes,
+                          void *stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!meshes || nsolve <= 0 || !b || !x || !o || !stats || !scratch)
+        return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");
+    if (o->precision != SEM_PCG_MIXED) return fail(SEM_ERR_UNSUPPORTED, "batched solves use SEM_PCG_MIXED");
+    if (o->use_initial_guess) return fail(SEM_ERR_UNSUPPORTED, "batched solves start from x = 0");
+    if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
+    for (int i = 0; i < nsolve; ++i) {
+        if (!meshes[i] || !b[i] || !x[i]) return fail(SEM_ERR_INVALID_ARG, "NULL mesh, b or x");
+        if (!meshes[i]->G32) return fail(SEM_ERR_INVALID_ARG, "batched solves need meshes built with SEM_GEOM_F32");
+        if (meshes[i]->device != meshes[0]->device) return fail(SEM_ERR_INVALID_ARG, "meshes on different devices");
+    }
+    if (scratch_bytes < sem_pcg_batched_scratch_bytes(meshes, nsolve, o) ||
+        reinterpret_cast<uintptr_t>(scratch) % kAlign)
+        return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_batched_scratch_bytes or misaligned");
+    cudaStream_t st = as_stream(stream);
+    char *p = static_cast<char *>(scratch);
+    PcgScal **d_outs = reinterpret_cast<PcgScal **>(p);
+    p += align_up(sizeof(PcgScal *) * nsolve);
+    int *d_phases = reinterpret_cast<int *>(p);  // [nsolve] + unfinished count
+    p += align_up(sizeof(int) * (nsolve + 1));
+    std::vector<BtSolve> S(nsolve);
+    std::vector<PcgScal *> outs(nsolve);
+    for (int i = 0; i < nsolve; ++i) {
+        S[i].m = meshes[i];
+        S[i].b = b[i];
+        S[i].x = x[i];
+        S[i].M = carve_mixed(meshes[i], p);
+        p += align_up(pcg_scratch_mixed(meshes[i]));
+        outs[i] = S[i].M.scal_out;
+    }
+    SEM_CUDA_CHECK(cudaMemcpyAsync(d_outs, outs.data(), sizeof(PcgScal *) * nsolve, cudaMemcpyHostToDevice, st));
+    // start every solve: x = 0, r = b, inner FP32 start from r / ||r||
+    const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
+    for (int i = 0; i < nsolve; ++i) {
+        const sem_mesh *m = S[i].m;
+        const int64_t n = m->nloc;
+        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.scal_out, 0, sizeof(PcgScal), st));
+        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.in.scal, 0, sizeof(PcgScal), st));
+        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].x, 0, sizeof(double) * n, st));
+        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.d32, 0, sizeof(float) * n, st));
+        ir_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(S[i].b, nullptr, S[i].M.r64, m->minv, n,
+                                                           S[i].M.partial_out, S[i].M.scal_out, o->tol,
+                                                           o->tol_is_relative);
+        pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(S[i].M.r64, nullptr, m->dinv32, m->minv32, n,
+                                                                       S[i].M.in, S[i].M.scal_out, itol, 1,
+                                                                       o->max_iter);
+        SEM_CUDA_CHECK(cudaGetLastError());
+    }
+    // solves already converged at the start (b = 0) are finished; the rest iterate
+    for (int i = 0; i < nsolve; ++i) {
+        bt_start_kernel<<<1, 32, 0, st>>>(S[i].M.scal_out);
+    }
+    SEM_CUDA_CHECK(cudaGetLastError());
+
+    const int K = o->check_every > 0 ? o->check_every : 16;
+    const int nstreams = nsolve < 16 ? nsolve : 16;
+    // capture happens on a stream of our own (the caller's may be the legacy
+    // default stream, which cannot be captured); the graph runs on `st`
+    std::vector<cudaStream_t> ss(nstreams + 1);
+    std::vector<cudaEvent_t> ev(nstreams + 1);
+    for (auto &q : ss) SEM_CUDA_CHECK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    for (auto &e : ev) SEM_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t cs = ss[nstreams];
+    auto cleanup = [&]() {
+        for (auto &q : ss) cudaStreamDestroy(q);
+        for (auto &e : ev) cudaEventDestroy(e);
+    };
+    std::vector<int> active(nsolve), hph(nsolve + 1, kBtIterate);
+    for (int i = 0; i < nsolve; ++i) active[i] = i;
+    std::vector<double> done_ms(nsolve, -1.0);
+    cudaGraphExec_t exec = nullptr;
+    int captured = 0, rounds = 0, status = SEM_OK;
+    const int max_rounds = o->max_iter / K + 64;
+    while (true) {
+        if (!exec) {
+            // capture one round of the active solves as parallel branches
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+            if (ce != cudaSuccess) {
+                cleanup();
+                return cuda_fail(ce, "cudaStreamBeginCapture");
+            }
+            cudaEventRecord(ev[nstreams], cs);
+            int s = SEM_OK;
+            for (int q = 0; q < nstreams && s == SEM_OK; ++q) {
+                cudaStreamWaitEvent(ss[q], ev[nstreams], 0);
+                for (size_t a = q; a < active.size() && s == SEM_OK; a += nstreams)
+                    s = bt_round(S[active[a]], o, K, ss[q]);
+                cudaEventRecord(ev[q], ss[q]);
+                cudaStreamWaitEvent(cs, ev[q], 0);
+            }
+            bt_collect_kernel<<<1, 32, 0, cs>>>(d_outs, nsolve, d_phases, d_phases + nsolve);
+            ce = cudaStreamEndCapture(cs, &g);
+            if (s != SEM_OK || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cleanup();
+                return s != SEM_OK ? s : cuda_fail(ce, "cudaStreamEndCapture");
+            }
+            ce = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                cleanup();
+                return cuda_fail(ce, "cudaGraphInstantiate");
+            }
+            captured = (int)active.size();
+        }
+        cudaError_t ce = cudaGraphLaunch(exec, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hph.data(), d_phases, sizeof(int) * (nsolve + 1),
+                                                    cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            cleanup();
+            return cuda_fail(ce, "batched round");
+        }
+        ++rounds;
+        const double now = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        std::vector<int> still;
+        for (int i : active) {
+            if (hph[i] == kBtFinished) {
+                if (done_ms[i] < 0) done_ms[i] = now;
+            } else {
+                still.push_back(i);
+            }
+        }
+        active.swap(still);
+        if (active.empty()) break;
+        if (rounds >= max_rounds) {
+            status = SEM_ERR_NOT_CONVERGED;
+            break;
+        }
+        if ((int)active.size() * 2 <= captured) {  // re-capture the smaller active set
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cleanup();
+    // per-solve statistics
+    int derr = 0;
+    for (int i = 0; i < nsolve; ++i) {
+        PcgScal ho{}, hi{};
+        SEM_CUDA_CHECK(cudaMemcpyAsync(&ho, S[i].M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaMemcpyAsync(&hi, S[i].M.in.scal, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        int e = 0;
+        SEM_CUDA_CHECK(cudaMemcpyAsync(&e, meshes[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        derr |= e;
+        sem_pcg_stats &t = stats[i];
+        t = sem_pcg_stats{};
+        t.iters = hi.iter;
+        t.outer_iters = ho.iter > 0 ? ho.iter - 1 : 0;
+        t.bnorm = std::sqrt(ho.bb);
+        t.abs_res = std::sqrt(ho.rr);
+        t.rel_res = ho.bb > 0 ? std::sqrt(ho.rr / ho.bb) : t.abs_res;
+        t.init_rel_res = 1.0;
+        t.status = ho.phase == kBtFinished ? ho.status : SEM_ERR_NOT_CONVERGED;
+        if (e) t.status = SEM_ERR_TIMEOUT;
+        t.wall_ms = done_ms[i];
+        t.kernel_launches = rounds;
+        if (t.status != SEM_OK && status == SEM_OK) status = t.status;
+    }
+    if (derr) status = SEM_ERR_TIMEOUT;
+    if (status != SEM_OK) set_error(sem_status_string(status));
+    return status;
 }
 
 }  // extern "C"
