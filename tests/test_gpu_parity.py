@@ -321,3 +321,25 @@ def test_full_size_pcg_mixed_true_residual():
     r = b - om.apply(_host(xg))
     rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
     assert rel <= 1.05e-8, rel
+
+
+@pytest.mark.slow
+def test_full_size_deformed64_mixed_true_residual():
+    """The 64^3 deformed cube (134 M local points): the chosen solver's
+    solution has an oracle-computed true residual within the tolerance, and
+    agrees with the FP64 solution."""
+    case = inputs.deformed_cube(64, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    bg = case.rhs_global()
+    b = _dev(bg)
+    b = gm.scatter(b)
+    x, st = gm.pcg(b, tol=1e-8, max_iter=100000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, check_every=32)
+    assert st["status"] == 0
+    xh = _host(x)
+    bh = _host(b)
+    del x, b, gm
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    r = bh - om.apply(xh)
+    rel = np.sqrt(om.glsc3(r, r) / om.glsc3(bh, bh))
+    assert rel <= 1.05e-8, rel
