@@ -14,6 +14,7 @@ namespace sem {
 constexpr int kMaxN = SEM_MAX_ORDER;
 constexpr int kMaxN1 = kMaxN + 1;
 constexpr int kAlign = 256;
+constexpr int kJac32 = 36;  // floats per element in the FP32 operator's geometry table
 
 // Derivative matrix passed by value to kernels (copied to shared memory).
 struct DMat {
@@ -63,18 +64,19 @@ struct sem_mesh {
     // device arrays (inside the caller's workspace)
     double *verts;       // [E][8][3]
     double *G;           // [E][6][npt]
-    float *G32;          // [E][6][npt] or nullptr
+    float *G32;          // [E][6][npt] FP32 geometric factors, or nullptr
+    float *jac32;        // [E][kJac32] trilinear edge vectors (FP32 operator forming its own factors)
     double *B;           // [E][npt]
     double *mult;        // [nloc]
     double *minv;        // [nloc] 1/mult
     double *dinv;        // [nloc] inverse assembled Jacobi diagonal (0 on Dirichlet)
-    float *dinv32;       // [nloc] same in FP32 (when G32 built)
+    float *dinv32;       // [nloc] same in FP32 (SEM_GEOM_F32)
     float *minv32;       // [nloc]
     double *rx;          // [E][9][npt] dr_a/dx_m (a-major) or nullptr
-    int *gs_off;         // [ngroups + 1]
-    int *gs_idx;         // [nentries]
+    int *gs_idx;         // group copies, bucketed by group size (see sem_mesh.cu)
     int *d_err;          // device error word
     int64_t ngroups, nmasked, nentries;
+    int64_t gs_n[4], gs_nm[4], gs_start[4];  // bucket b (2^b copies): groups, masked groups, first int
     size_t ws_bytes;
     int device;
     int num_sms;

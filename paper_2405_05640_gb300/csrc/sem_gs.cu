@@ -8,11 +8,13 @@
 // the communication kernel and the strong-scaling bottleneck.
 //
 // Data structure: "groups" = global nodes that have more than one local copy
-// or lie on a Dirichlet face.  gs_off/gs_idx is a CSR list of the local
-// indices of each group, ascending; groups [0, nmasked) are the Dirichlet
-// ones.  Interior element nodes are never touched.  One thread per group sums
-// its copies in ascending local index (deterministic; every copy receives
-// bit-identical values) and writes the sum back.
+// or lie on a Dirichlet face, stored by size in four buckets (2^b copies in
+// bucket b; size 1 only for masked nodes), the local indices of each group
+// ascending, each bucket's Dirichlet groups first.  Interior element nodes are
+// never touched.  One thread per group: it loads the group's indices with one
+// vector load (int2 / int4 / two int4), all copies at once, sums them in
+// ascending local index (deterministic; every copy receives bit-identical
+// values) and writes the sum back -- two dependent memory levels.
 
 #include <mutex>
 
@@ -20,35 +22,102 @@
 
 namespace sem {
 
+struct GsPlan {
+    const int *idx;
+    int64_t start[4];  // first int of bucket b
+    int64_t nm[4];     // masked groups at the head of bucket b
+    int64_t t0[5];     // bucket b's groups [0, t0[b+1] - t0[b]) run on threads [t0[b], t0[b+1])
+};
+
 template <typename T>
-__global__ void gs_kernel(T *__restrict__ u, const int *__restrict__ off, const int *__restrict__ idx,
-                          int64_t ngroups, int64_t nmasked, int mode, const int *__restrict__ guard, int gval) {
+__global__ void __launch_bounds__(256)
+    gs_kernel(T *__restrict__ u, GsPlan P, int mode, const int *__restrict__ guard, int gval) {
     if (guard && *guard != gval) return;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int a = off[g], b = off[g + 1];
-        const bool masked = g < nmasked;
-        if (masked && mode != kGsSum) {
-            for (int q = a; q < b; ++q) u[idx[q]] = T(0);
-        } else if (mode != kGsMaskOnly && b - a > 1) {
-            T s = u[idx[a]];
-            for (int q = a + 1; q < b; ++q) s += u[idx[q]];
-            for (int q = a; q < b; ++q) u[idx[q]] = s;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= P.t0[4]) return;
+    const bool zero_masked = mode != kGsSum;
+    if (t < P.t0[1]) {  // single copies: always Dirichlet
+        u[P.idx[P.start[0] + (t - P.t0[0])]] = T(0);
+    } else if (t < P.t0[2]) {
+        const int64_t g = t - P.t0[1];
+        const int2 q = *reinterpret_cast<const int2 *>(P.idx + P.start[1] + 2 * g);
+        if (zero_masked && g < P.nm[1]) {
+            u[q.x] = T(0);
+            u[q.y] = T(0);
+        } else {
+            const T a0 = u[q.x], a1 = u[q.y];
+            const T s = a0 + a1;
+            u[q.x] = s;
+            u[q.y] = s;
+        }
+    } else if (t < P.t0[3]) {
+        const int64_t g = t - P.t0[2];
+        const int4 q = *reinterpret_cast<const int4 *>(P.idx + P.start[2] + 4 * g);
+        if (zero_masked && g < P.nm[2]) {
+            u[q.x] = T(0);
+            u[q.y] = T(0);
+            u[q.z] = T(0);
+            u[q.w] = T(0);
+        } else {
+            const T a0 = u[q.x], a1 = u[q.y], a2 = u[q.z], a3 = u[q.w];
+            const T s = ((a0 + a1) + a2) + a3;
+            u[q.x] = s;
+            u[q.y] = s;
+            u[q.z] = s;
+            u[q.w] = s;
+        }
+    } else {
+        const int64_t g = t - P.t0[3];
+        const int4 *q4 = reinterpret_cast<const int4 *>(P.idx + P.start[3] + 8 * g);
+        const int4 q = q4[0], r = q4[1];
+        if (zero_masked && g < P.nm[3]) {
+            u[q.x] = T(0);
+            u[q.y] = T(0);
+            u[q.z] = T(0);
+            u[q.w] = T(0);
+            u[r.x] = T(0);
+            u[r.y] = T(0);
+            u[r.z] = T(0);
+            u[r.w] = T(0);
+        } else {
+            const T a0 = u[q.x], a1 = u[q.y], a2 = u[q.z], a3 = u[q.w];
+            const T a4 = u[r.x], a5 = u[r.y], a6 = u[r.z], a7 = u[r.w];
+            const T s = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
+            u[q.x] = s;
+            u[q.y] = s;
+            u[q.z] = s;
+            u[q.w] = s;
+            u[r.x] = s;
+            u[r.y] = s;
+            u[r.z] = s;
+            u[r.w] = s;
         }
     }
 }
 
 int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, const int *guard, int gval) {
-    const int64_t n = (mode == kGsMaskOnly) ? m->nmasked : m->ngroups;
+    GsPlan P;
+    P.idx = m->gs_idx;
+    P.t0[0] = 0;
+    for (int b = 0; b < 4; ++b) {
+        P.start[b] = m->gs_start[b];
+        P.nm[b] = m->gs_nm[b];
+        int64_t cnt;
+        if (mode == kGsMaskOnly)
+            cnt = m->gs_nm[b];
+        else if (mode == kGsSum)
+            cnt = b == 0 ? 0 : m->gs_n[b];
+        else
+            cnt = m->gs_n[b];  // bucket 0 holds masked groups only
+        P.t0[b + 1] = P.t0[b] + cnt;
+    }
+    const int64_t n = P.t0[4];
     if (n == 0) return SEM_OK;
-    int64_t g = (n + 255) / 256;
-    if (g > (int64_t)m->num_sms * 32) g = (int64_t)m->num_sms * 32;
+    const int64_t g = (n + 255) / 256;
     if (dtype == SEM_F64)
-        gs_kernel<double><<<(int)g, 256, 0, st>>>(static_cast<double *>(u), m->gs_off, m->gs_idx, n,
-                                                  m->nmasked, mode, guard, gval);
+        gs_kernel<double><<<(unsigned)g, 256, 0, st>>>(static_cast<double *>(u), P, mode, guard, gval);
     else if (dtype == SEM_F32)
-        gs_kernel<float><<<(int)g, 256, 0, st>>>(static_cast<float *>(u), m->gs_off, m->gs_idx, n,
-                                                 m->nmasked, mode, guard, gval);
+        gs_kernel<float><<<(unsigned)g, 256, 0, st>>>(static_cast<float *>(u), P, mode, guard, gval);
     else
         return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
     SEM_CUDA_CHECK(cudaGetLastError());

@@ -134,12 +134,20 @@ static Axis make_axis(int N, int nel, int periodic, int lo_dir, int hi_dir) {
     return a;
 }
 
+// Groups: every global node with more than one copy, or on a Dirichlet face.
+// Group sizes are products of per-axis copy counts (1 or 2): 1, 2, 4 or 8.
+// They are stored in four buckets by size (bucket b holds groups of 2^b
+// copies, size-1 groups only when masked), each bucket's masked groups first,
+// then the rest, each part in lexicographic (I fastest) order of the global
+// node; each bucket starts on a 16-byte boundary.
 struct GsCounts {
     int64_t ngroups = 0, nmasked = 0, nentries = 0;
+    int64_t n[4] = {0, 0, 0, 0}, nm[4] = {0, 0, 0, 0}, start[4] = {0, 0, 0, 0};
+    int64_t ints = 0;  // length of the bucketed index array (with padding)
 };
 
-// Groups: every global node with more than one copy, or on a Dirichlet face.
-// Masked groups first, then the rest, each in lexicographic (I fastest) order.
+static int bucket_of(int m) { return m == 1 ? 0 : m == 2 ? 1 : m == 4 ? 2 : 3; }
+
 static GsCounts gs_count(const Axis ax[3]) {
     // histogram over (copies, dirichlet) per axis, product over axes
     GsCounts c;
@@ -159,18 +167,28 @@ static GsCounts gs_count(const Axis ax[3]) {
                             if (m < 2 && !masked) continue;
                             c.ngroups += n;
                             c.nentries += n * m;
-                            if (masked) c.nmasked += n;
+                            c.n[bucket_of(m)] += n;
+                            if (masked) {
+                                c.nmasked += n;
+                                c.nm[bucket_of(m)] += n;
+                            }
                         }
+    int64_t at = 0;
+    for (int b = 0; b < 4; ++b) {
+        c.start[b] = at;
+        at += c.n[b] << b;
+        at = (at + 3) / 4 * 4;
+    }
+    c.ints = at;
     return c;
 }
 
-static void gs_build(const Axis ax[3], int N, const int nel[3], GsCounts c, std::vector<int> &off,
-                     std::vector<int> &idx) {
+static void gs_build(const Axis ax[3], int N, const int nel[3], const GsCounts &c, std::vector<int> &idx) {
     const int n1 = N + 1;
     const int64_t npt = (int64_t)n1 * n1 * n1;
-    off.assign(c.ngroups + 1, 0);
-    idx.resize(c.nentries);
-    int64_t g = 0, q = 0;
+    idx.assign(c.ints > 0 ? c.ints : 1, 0);
+    int64_t cur[4];
+    for (int b = 0; b < 4; ++b) cur[b] = c.start[b];
     for (int pass = 0; pass < 2; ++pass) {  // pass 0: masked groups, pass 1: the rest
         for (int64_t K = 0; K < ax[2].G; ++K)
             for (int64_t J = 0; J < ax[1].G; ++J)
@@ -193,12 +211,10 @@ static void gs_build(const Axis ax[3], int N, const int nel[3], GsCounts c, std:
                     // ascending local index: the summation order of every group
                     for (int s = 1; s < n; ++s)
                         for (int t = s; t > 0 && loc[t - 1] > loc[t]; --t) std::swap(loc[t - 1], loc[t]);
-                    off[g] = (int)q;
+                    int64_t &q = cur[bucket_of(n)];
                     for (int s = 0; s < n; ++s) idx[q++] = loc[s];
-                    ++g;
                 }
     }
-    off[g] = (int)q;
 }
 
 static int validate(const sem_mesh_desc *d) {
@@ -215,7 +231,7 @@ static int validate(const sem_mesh_desc *d) {
 }
 
 struct Layout {
-    size_t verts, G, G32, B, mult, minv, dinv, dinv32, minv32, rx, off, idx, err, total;
+    size_t verts, G, G32, jac32, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -229,6 +245,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.verts = take(sizeof(double) * E * 24);
     L.G = take(sizeof(double) * E * 6 * npt);
     L.G32 = f32 ? take(sizeof(float) * E * 6 * npt) : 0;
+    L.jac32 = f32 ? take(sizeof(float) * E * kJac32) : 0;
     L.B = take(sizeof(double) * nloc);
     L.mult = take(sizeof(double) * nloc);
     L.minv = take(sizeof(double) * nloc);
@@ -236,8 +253,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.dinv32 = f32 ? take(sizeof(float) * nloc) : 0;
     L.minv32 = f32 ? take(sizeof(float) * nloc) : 0;
     L.rx = (d->geom_flags & SEM_GEOM_RX) ? take(sizeof(double) * 9 * nloc) : 0;
-    L.off = take(sizeof(int) * (c.ngroups + 1));
-    L.idx = take(sizeof(int) * (c.nentries > 0 ? c.nentries : 1));
+    L.idx = take(sizeof(int) * (c.ints > 0 ? c.ints : 1));
     L.err = take(sizeof(int) * 8);
     L.total = o;
     return L;
@@ -326,6 +342,29 @@ __global__ void geometry_kernel(const double *__restrict__ verts, int64_t E, int
             for (int a = 0; a < 3; ++a)
                 for (int mm = 0; mm < 3; ++mm) Re[(3 * a + mm) * npt + p] = C[mm][a] * id;
         }
+    }
+}
+
+// Edge-vector table of the trilinear map for the FP32 operator, which forms
+// the geometric factors itself: with vertex v = bx + 2 by + 4 bz,
+//   dx/dr (s, t) = sum_{by,bz} Er[by][bz] fs[by] ft[bz],  Er = (X_{1,by,bz} - X_{0,by,bz}) / 2
+// and likewise Es[bx][bz] (s-edges), Et[bx][by] (t-edges); fs = ((1-s)/2, (1+s)/2).
+// Stored [e][36]: Er at (2 by + bz) 3 + a, Es at 12 + (2 bx + bz) 3 + a,
+// Et at 24 + (2 bx + by) 3 + a.  Differences in FP64, rounded once.
+__global__ void jac32_kernel(const double *__restrict__ verts, int64_t E, float *__restrict__ jac) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < E * 12;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = q / 12;
+        const int c = (int)(q - e * 12);
+        const int dir = c / 4, b1 = (c >> 1) & 1, b2 = c & 1;  // edge direction, the two other bits
+        int v0;
+        if (dir == 0) v0 = 2 * b1 + 4 * b2;          // (by, bz)
+        else if (dir == 1) v0 = b1 + 4 * b2;         // (bx, bz)
+        else v0 = b1 + 2 * b2;                       // (bx, by)
+        const int v1 = v0 + (1 << dir);
+        const double *V = verts + e * 24;
+        float *o = jac + e * kJac32 + dir * 12 + (2 * b1 + b2) * 3;
+        for (int a = 0; a < 3; ++a) o[a] = (float)(0.5 * (V[v1 * 3 + a] - V[v0 * 3 + a]));
     }
 }
 
@@ -435,7 +474,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     GsCounts c = gs_count(ax);
     Layout L = layout_for(d, c);
     if (bytes < L.total) return fail(SEM_ERR_WORKSPACE, "workspace smaller than sem_mesh_workspace_bytes");
-    if (c.nentries >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "too many shared points");
+    if (c.ints >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "too many shared points");
 
     sem_mesh *m = new (std::nothrow) sem_mesh();
     if (!m) return fail(SEM_ERR_INVALID_ARG, "host allocation failed");
@@ -454,6 +493,11 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->ngroups = c.ngroups;
     m->nmasked = c.nmasked;
     m->nentries = c.nentries;
+    for (int b = 0; b < 4; ++b) {
+        m->gs_n[b] = c.n[b];
+        m->gs_nm[b] = c.nm[b];
+        m->gs_start[b] = c.start[b];
+    }
     m->ws_bytes = L.total;
     gll_host(m->N, m->xi, m->rho);
     std::memset(&m->D, 0, sizeof(m->D));
@@ -465,14 +509,14 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->verts = reinterpret_cast<double *>(base + L.verts);
     m->G = reinterpret_cast<double *>(base + L.G);
     m->G32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.G32) : nullptr;
+    m->jac32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.jac32) : nullptr;
     m->B = reinterpret_cast<double *>(base + L.B);
     m->mult = reinterpret_cast<double *>(base + L.mult);
     m->minv = reinterpret_cast<double *>(base + L.minv);
     m->dinv = reinterpret_cast<double *>(base + L.dinv);
-    m->dinv32 = m->G32 ? reinterpret_cast<float *>(base + L.dinv32) : nullptr;
-    m->minv32 = m->G32 ? reinterpret_cast<float *>(base + L.minv32) : nullptr;
+    m->dinv32 = m->jac32 ? reinterpret_cast<float *>(base + L.dinv32) : nullptr;
+    m->minv32 = m->jac32 ? reinterpret_cast<float *>(base + L.minv32) : nullptr;
     m->rx = (d->geom_flags & SEM_GEOM_RX) ? reinterpret_cast<double *>(base + L.rx) : nullptr;
-    m->gs_off = reinterpret_cast<int *>(base + L.off);
     m->gs_idx = reinterpret_cast<int *>(base + L.idx);
     m->d_err = reinterpret_cast<int *>(base + L.err);
 
@@ -487,8 +531,8 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     ce = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return cleanup(cuda_fail(ce, "cudaDeviceGetAttribute"));
 
-    std::vector<int> off, idx;
-    gs_build(ax, m->N, m->nel, c, off, idx);
+    std::vector<int> idx;
+    gs_build(ax, m->N, m->nel, c, idx);
     cudaStream_t s = as_stream(stream);
 #define CK(call)                                              \
     do {                                                      \
@@ -496,9 +540,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
         if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #call)); \
     } while (0)
     CK(cudaMemcpyAsync(m->verts, d->vertices, sizeof(double) * m->E * 24, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(m->gs_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
-    if (!idx.empty())
-        CK(cudaMemcpyAsync(m->gs_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->gs_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int) * 8, s));
     GllConst g{};
     for (int i = 0; i < m->n1; ++i) {
@@ -508,6 +550,10 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     geometry_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->verts, m->E, m->N, g, m->G, m->B, m->G32, m->rx,
                                                       m->d_err);
     CK(cudaGetLastError());
+    if (m->jac32) {
+        jac32_kernel<<<grid_for(m->E * 12), 256, 0, s>>>(m->verts, m->E, m->jac32);
+        CK(cudaGetLastError());
+    }
     // multiplicity = Q Q^T 1
     fill_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->mult, m->nloc, 1.0);
     CK(cudaGetLastError());
@@ -522,7 +568,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     CK(cudaGetLastError());
     st = gs_launch(m, m->dinv, SEM_F64, kGsMaskOnly, s);
     if (st != SEM_OK) return cleanup(st);
-    if (m->G32) {
+    if (m->jac32) {
         copy_f32_from_f64<<<grid_for(m->nloc), 256, 0, s>>>(m->dinv, m->dinv32, m->nloc);
         CK(cudaGetLastError());
         copy_f32_from_f64<<<grid_for(m->nloc), 256, 0, s>>>(m->minv, m->minv32, m->nloc);

@@ -150,9 +150,54 @@ __global__ void __launch_bounds__(kPThreads)
     }
 }
 
+// 16-byte vector of T (float4 / double2) as an array.
+template <typename T>
+struct V16 {
+    static constexpr int n = 16 / sizeof(T);
+    T a[16 / sizeof(T)];
+};
+template <typename T>
+__device__ __forceinline__ V16<T> ld16(const T *p) {
+    V16<T> v;
+    if (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        reinterpret_cast<float4 &>(v) = q;
+    } else {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        reinterpret_cast<double2 &>(v) = q;
+    }
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ void st16(T *p, const V16<T> &v) {
+    if (sizeof(T) == 4)
+        *reinterpret_cast<float4 *>(p) = reinterpret_cast<const float4 &>(v);
+    else
+        *reinterpret_cast<double2 *>(p) = reinterpret_cast<const double2 &>(v);
+}
+
+// One point of the update: x += alpha p; r -= alpha w; rr and rz partials
+// (per-thread in T for FP32, FP64 for FP64).
+template <typename T>
+__device__ __forceinline__ void update_point(T alpha, T p, T w, T mi, T di, T &x, T &r, double (&v)[2], T &f0,
+                                             T &f1) {
+    x = fma(alpha, p, x);
+    r = fma(-alpha, w, r);
+    if (sizeof(T) == 8) {
+        v[0] = fma((double)(r * r), (double)mi, v[0]);
+        v[1] = fma((double)(r * (di * r)), (double)mi, v[1]);
+    } else {
+        f0 = fma(r * r, mi, f0);
+        f1 = fma(r * (di * r), mi, f1);
+    }
+}
+
 // x += alpha p; r -= alpha w; z = dinv r; rr = <r,r>; rz = <r,z>;
 // last block: beta = rz/rho, rho = rz, iteration count and convergence flag.
-template <typename T>
+// VEC: every array 16-byte aligned; each thread step takes 16 bytes of every
+// array (4 FP32 / 2 FP64 points), the last n mod (16 / sizeof(T)) points
+// one by one.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kPThreads)
     pcg_update_kernel(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
                       PcgWork<T> W) {
@@ -160,19 +205,23 @@ __global__ void __launch_bounds__(kPThreads)
     const T alpha = (T)W.scal->alpha;
     double v[2] = {0.0, 0.0};
     T f0 = T(0), f1 = T(0);
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
-        const T p = W.p[l];
-        x[l] = fma(alpha, p, x[l]);
-        const T r = fma(-alpha, W.w[l], W.r[l]);
-        W.r[l] = r;
-        const T mi = minv[l];
-        if (sizeof(T) == 8) {
-            v[0] = fma((double)(r * r), (double)mi, v[0]);
-            v[1] = fma((double)(r * (dinv[l] * r)), (double)mi, v[1]);
-        } else {
-            f0 = fma(r * r, mi, f0);
-            f1 = fma(r * (dinv[l] * r), mi, f1);
-        }
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    constexpr int V = V16<T>::n;
+    const int64_t nv = VEC ? n / V : 0;
+    for (int64_t q = tid; q < nv; q += stride) {
+        const int64_t l = q * V;
+        const V16<T> p = ld16(W.p + l), w = ld16(W.w + l), mi = ld16(minv + l), di = ld16(dinv + l);
+        V16<T> xv = ld16(x + l), rv = ld16(W.r + l);
+#pragma unroll
+        for (int c = 0; c < V; ++c) update_point(alpha, p.a[c], w.a[c], mi.a[c], di.a[c], xv.a[c], rv.a[c], v, f0, f1);
+        st16(x + l, xv);
+        st16(W.r + l, rv);
+    }
+    for (int64_t l = nv * V + tid; l < n; l += stride) {
+        T xl = x[l], rl = W.r[l];
+        update_point(alpha, W.p[l], W.w[l], minv[l], dinv[l], xl, rl, v, f0, f1);
+        x[l] = xl;
+        W.r[l] = rl;
     }
     if (sizeof(T) == 4) {
         v[0] = (double)f0;
@@ -197,6 +246,18 @@ __global__ void __launch_bounds__(kPThreads)
             s->status = SEM_ERR_NOT_CONVERGED;
         }
     }
+}
+
+static bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <typename T>
+static int launch_update(T *x, const T *dinv, const T *minv, int64_t n, const PcgWork<T> &W, cudaStream_t st) {
+    if (al16(x) && al16(dinv) && al16(minv) && al16(W.p) && al16(W.w) && al16(W.r))
+        pcg_update_kernel<T, true><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
+    else
+        pcg_update_kernel<T, false><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
 }
 
 // ---- FP64 outer loop of the mixed solver ----
@@ -428,8 +489,8 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
             c.tgs.stop(st);
             if (s != SEM_OK) return s;
             // x += alpha p; r -= alpha w; rr, rz; beta; convergence flag
-            pcg_update_kernel<T><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, m->nloc, W);
-            SEM_CUDA_CHECK(cudaGetLastError());
+            s = launch_update<T>(x, dinv, minv, m->nloc, W, st);
+            if (s != SEM_OK) return s;
             c.launches += 3;
             c.ax_launches += 1;
         }
@@ -737,7 +798,8 @@ static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
         if (s != SEM_OK) return s;
         s = gs_launch(m, S.M.in.w, SEM_F32, kGsSumMask, st, &S.M.in.scal->done, 0);
         if (s != SEM_OK) return s;
-        pcg_update_kernel<float><<<kPBlocks, kPThreads, 0, st>>>(S.M.d32, m->dinv32, m->minv32, n, S.M.in);
+        s = launch_update<float>(S.M.d32, m->dinv32, m->minv32, n, S.M.in, st);
+        if (s != SEM_OK) return s;
     }
     bt_pause_kernel<<<1, 32, 0, st>>>(S.M.in.scal, S.M.scal_out);
     bt_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.x, S.M.d32, n, S.M.scal_out);
