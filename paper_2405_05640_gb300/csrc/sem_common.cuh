@@ -14,7 +14,6 @@ namespace sem {
 constexpr int kMaxN = SEM_MAX_ORDER;
 constexpr int kMaxN1 = kMaxN + 1;
 constexpr int kAlign = 256;
-constexpr int kJac32 = 36;  // floats per element in the FP32 operator's geometry table
 
 // Derivative matrix passed by value to kernels (copied to shared memory).
 struct DMat {
@@ -65,7 +64,6 @@ struct sem_mesh {
     double *verts;       // [E][8][3]
     double *G;           // [E][6][npt]
     float *G32;          // [E][6][npt] FP32 geometric factors, or nullptr
-    float *jac32;        // [E][kJac32] trilinear edge vectors (FP32 operator forming its own factors)
     double *B;           // [E][npt]
     double *mult;        // [nloc]
     double *minv;        // [nloc] 1/mult

@@ -231,7 +231,7 @@ static int validate(const sem_mesh_desc *d) {
 }
 
 struct Layout {
-    size_t verts, G, G32, jac32, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
+    size_t verts, G, G32, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -245,7 +245,6 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.verts = take(sizeof(double) * E * 24);
     L.G = take(sizeof(double) * E * 6 * npt);
     L.G32 = f32 ? take(sizeof(float) * E * 6 * npt) : 0;
-    L.jac32 = f32 ? take(sizeof(float) * E * kJac32) : 0;
     L.B = take(sizeof(double) * nloc);
     L.mult = take(sizeof(double) * nloc);
     L.minv = take(sizeof(double) * nloc);
@@ -342,29 +341,6 @@ __global__ void geometry_kernel(const double *__restrict__ verts, int64_t E, int
             for (int a = 0; a < 3; ++a)
                 for (int mm = 0; mm < 3; ++mm) Re[(3 * a + mm) * npt + p] = C[mm][a] * id;
         }
-    }
-}
-
-// Edge-vector table of the trilinear map for the FP32 operator, which forms
-// the geometric factors itself: with vertex v = bx + 2 by + 4 bz,
-//   dx/dr (s, t) = sum_{by,bz} Er[by][bz] fs[by] ft[bz],  Er = (X_{1,by,bz} - X_{0,by,bz}) / 2
-// and likewise Es[bx][bz] (s-edges), Et[bx][by] (t-edges); fs = ((1-s)/2, (1+s)/2).
-// Stored [e][36]: Er at (2 by + bz) 3 + a, Es at 12 + (2 bx + bz) 3 + a,
-// Et at 24 + (2 bx + by) 3 + a.  Differences in FP64, rounded once.
-__global__ void jac32_kernel(const double *__restrict__ verts, int64_t E, float *__restrict__ jac) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < E * 12;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = q / 12;
-        const int c = (int)(q - e * 12);
-        const int dir = c / 4, b1 = (c >> 1) & 1, b2 = c & 1;  // edge direction, the two other bits
-        int v0;
-        if (dir == 0) v0 = 2 * b1 + 4 * b2;          // (by, bz)
-        else if (dir == 1) v0 = b1 + 4 * b2;         // (bx, bz)
-        else v0 = b1 + 2 * b2;                       // (bx, by)
-        const int v1 = v0 + (1 << dir);
-        const double *V = verts + e * 24;
-        float *o = jac + e * kJac32 + dir * 12 + (2 * b1 + b2) * 3;
-        for (int a = 0; a < 3; ++a) o[a] = (float)(0.5 * (V[v1 * 3 + a] - V[v0 * 3 + a]));
     }
 }
 
@@ -509,13 +485,12 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->verts = reinterpret_cast<double *>(base + L.verts);
     m->G = reinterpret_cast<double *>(base + L.G);
     m->G32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.G32) : nullptr;
-    m->jac32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.jac32) : nullptr;
     m->B = reinterpret_cast<double *>(base + L.B);
     m->mult = reinterpret_cast<double *>(base + L.mult);
     m->minv = reinterpret_cast<double *>(base + L.minv);
     m->dinv = reinterpret_cast<double *>(base + L.dinv);
-    m->dinv32 = m->jac32 ? reinterpret_cast<float *>(base + L.dinv32) : nullptr;
-    m->minv32 = m->jac32 ? reinterpret_cast<float *>(base + L.minv32) : nullptr;
+    m->dinv32 = m->G32 ? reinterpret_cast<float *>(base + L.dinv32) : nullptr;
+    m->minv32 = m->G32 ? reinterpret_cast<float *>(base + L.minv32) : nullptr;
     m->rx = (d->geom_flags & SEM_GEOM_RX) ? reinterpret_cast<double *>(base + L.rx) : nullptr;
     m->gs_idx = reinterpret_cast<int *>(base + L.idx);
     m->d_err = reinterpret_cast<int *>(base + L.err);
@@ -550,10 +525,6 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     geometry_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->verts, m->E, m->N, g, m->G, m->B, m->G32, m->rx,
                                                       m->d_err);
     CK(cudaGetLastError());
-    if (m->jac32) {
-        jac32_kernel<<<grid_for(m->E * 12), 256, 0, s>>>(m->verts, m->E, m->jac32);
-        CK(cudaGetLastError());
-    }
     // multiplicity = Q Q^T 1
     fill_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->mult, m->nloc, 1.0);
     CK(cudaGetLastError());
@@ -568,7 +539,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     CK(cudaGetLastError());
     st = gs_launch(m, m->dinv, SEM_F64, kGsMaskOnly, s);
     if (st != SEM_OK) return cleanup(st);
-    if (m->jac32) {
+    if (m->G32) {
         copy_f32_from_f64<<<grid_for(m->nloc), 256, 0, s>>>(m->dinv, m->dinv32, m->nloc);
         CK(cudaGetLastError());
         copy_f32_from_f64<<<grid_for(m->nloc), 256, 0, s>>>(m->minv, m->minv32, m->nloc);

@@ -343,3 +343,23 @@ def test_full_size_deformed64_mixed_true_residual():
     r = bh - om.apply(xh)
     rel = np.sqrt(om.glsc3(r, r) / om.glsc3(bh, bh))
     assert rel <= 1.05e-8, rel
+
+
+def test_autotune_reports_and_keeps_the_fastest():
+    """The autotuner times every (pipeline depth, CTA cap) of the operator,
+    keeps the fastest in the launch table, and the operator stays correct
+    under it."""
+    torch = _torch()
+    case = inputs.channel(6, 5)
+    om, gm = _pair(case, geom_f32=True)
+    try:
+        for dt, cg in ((binding.SEM_F32, True), (binding.SEM_F64, False)):
+            r = gm.autotune(dt, cg)
+            assert len(r["table"]) == 12
+            best = min(r["table"], key=lambda t: t[2])
+            assert (r["best_stages"], r["best_cap"]) == best[:2]
+            assert r["best_ms"] == pytest.approx(best[2])
+        u = np.random.default_rng(3).standard_normal(om.nloc)
+        assert _rel(_host(gm.ax(_dev(u))), om.ax_local(u)) <= AX_TOL
+    finally:
+        binding.lib().sem_autotune_reset()
