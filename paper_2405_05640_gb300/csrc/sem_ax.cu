@@ -207,13 +207,15 @@ __global__ void __launch_bounds__(ax_threads<N>())
             T *we = w + e * NPT;
 #pragma unroll
             for (int k = 0; k < N1; ++k) {
-                T acc = T(0);
+                // three independent accumulation chains (one per direction)
+                T ar = T(0), as = T(0), at = T(0);
 #pragma unroll
                 for (int l = 0; l < N1; ++l) {
-                    acc = fma(rDti[l], svr[l + N1 * (j + N1 * k)], acc);
-                    acc = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], acc);
-                    acc = fma(sD[l * N1 + k], rvt[l], acc);
+                    ar = fma(rDti[l], svr[l + N1 * (j + N1 * k)], ar);
+                    as = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], as);
+                    at = fma(sD[l * N1 + k], rvt[l], at);
                 }
+                T acc = (ar + as) + at;
                 const int p = i + N1 * (j + N1 * k);
                 if (HELM) acc = (T)(args.h1 * (double)acc + args.h2 * sb[p] * (double)ru[k]);
                 we[p] = acc;
@@ -238,23 +240,36 @@ __global__ void __launch_bounds__(ax_threads<N>())
         }
     }
     if (CG) {
-        // grid reduction of p.w: per-CTA partial, last CTA sums them in order
+        // grid reduction of p.w: per-CTA partials; the last CTA to arrive sums
+        // them with all its threads (thread t takes partials t, t + blockDim,
+        // ... in order, then a fixed shuffle tree and the warps in order: the
+        // same order on every run)
+        __shared__ int s_last;
+        const int lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
         double v = (double)pw_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) sred[tid >> 5] = v;
+        if (lane == 0) sred[wid] = v;
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sred[q];
+            for (int q = 0; q < nw; ++q) t += sred[q];
             cg.partial[blockIdx.x] = t;
             __threadfence();
-            const bool last = atomicAdd(&cg.scal->cnt[3], 1u) == gridDim.x - 1;
-            if (last) {
-                __threadfence();
-                const volatile double *vp = cg.partial;
+            s_last = atomicAdd(&cg.scal->cnt[3], 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double t = 0.0;
+            for (int q = tid; q < (int)gridDim.x; q += blockDim.x) t += __ldcg(cg.partial + q);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) sred[wid] = t;  // thread 0 read sred before the barrier above
+            __syncthreads();
+            if (tid == 0) {
                 double pw = 0.0;
-                for (int q = 0; q < (int)gridDim.x; ++q) pw += vp[q];
+                for (int q = 0; q < nw; ++q) pw += sred[q];
                 cg.scal->pw = pw;
                 cg.scal->alpha = cg.scal->rho / pw;
                 cg.scal->cnt[3] = 0u;
