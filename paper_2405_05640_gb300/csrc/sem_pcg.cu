@@ -29,6 +29,7 @@ namespace sem {
 
 constexpr int kPThreads = 256;
 constexpr int kPBlocks = 1184;  // 152 SMs x 8 blocks: fixed so the reduction order is fixed
+constexpr int kUBlocks = 608;   // vectorised update (62 registers): 152 SMs x 4 resident blocks, one wave
 
 // Vectors of one CG iteration space in precision T.
 template <typename T>
@@ -253,7 +254,7 @@ static bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) =
 template <typename T>
 static int launch_update(T *x, const T *dinv, const T *minv, int64_t n, const PcgWork<T> &W, cudaStream_t st) {
     if (al16(x) && al16(dinv) && al16(minv) && al16(W.p) && al16(W.w) && al16(W.r))
-        pcg_update_kernel<T, true><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
+        pcg_update_kernel<T, true><<<kUBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
     else
         pcg_update_kernel<T, false><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
     SEM_CUDA_CHECK(cudaGetLastError());
