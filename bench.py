@@ -69,7 +69,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations in the CPU sample")
     p.add_argument("--plain-steps", type=int, default=2, help="plain FP64 solves timed for comparison")
-    p.add_argument("--op", choices=["ax-f64", "ax-f32", "dssum-f64", "dssum-f32"], default=None,
+    p.add_argument("--op", choices=["ax-f64", "ax-f32", "ax-f64pair", "dssum-f64", "dssum-f32"], default=None,
                    help="time one entry point alone instead of the solve")
     p.add_argument("--workload", choices=["channel", "tgv-learned", "batched", "deformed"], default="channel")
     p.add_argument("--nsolve", type=int, default=64)
@@ -410,13 +410,16 @@ def run_op(args):
     from paper_2405_05640_gb300 import build as _build
     _build.build()
     case = inputs.channel(args.nel, args.order)
-    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
     kind, dt = args.op.split("-")
-    tdt = torch.float64 if dt == "f64" else torch.float32
+    pair = dt == "f64pair"
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=not pair,
+                      geom_pair=pair)
+    tdt = torch.float32 if dt == "f32" else torch.float64
     u = torch.randn(case.nloc, dtype=tdt, device="cuda")
     w = torch.empty_like(u)
     if kind == "ax":
-        fn, nbytes = (lambda: gm.ax(u, w)), (64 if dt == "f64" else 32) * case.nloc
+        # algorithmic bytes per local point: u in, w out, six factors (FP64 or FP32-pair: 8 B each)
+        fn, nbytes = (lambda: gm.ax(u, w, pair=pair)), (32 if dt == "f32" else 64) * case.nloc
     else:
         fn = lambda: gm.dssum(w, mask=True)
         nbytes = 2 * gm.info.n_shared_points * (8 if dt == "f64" else 4)

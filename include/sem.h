@@ -53,6 +53,8 @@ extern "C" {
 /* Data types of field arguments. */
 #define SEM_F64 0
 #define SEM_F32 1
+#define SEM_F64_PAIR 2             /* FP64 fields; sem_ax evaluates the operator in
+                                      FP32-pair arithmetic (see sem_ax) */
 
 /* Extra precision copies of the geometric factors that sem_mesh_create
  * builds (bitmask; FP64 factors are always built). */
@@ -60,6 +62,8 @@ extern "C" {
 #define SEM_GEOM_RX 2              /* inverse Jacobian dr_a/dx_m (9 per point, FP64):
                                       needed by sem_gradient, sem_advect,
                                       sem_weak_div and the sem_ns_* stepper */
+#define SEM_GEOM_PAIR 4            /* FP32-pair (hi, lo) factors, 48 bytes per point,
+                                      for sem_ax with SEM_F64_PAIR */
 
 typedef struct sem_mesh sem_mesh;  /* opaque; freed by sem_mesh_destroy */
 
@@ -123,9 +127,20 @@ int sem_mesh_field(const sem_mesh *mesh, int which, double *dst, void *stream);
 /* Local (unassembled) stiffness w = A_L u, element by element:
  *   u_r = D u, u_s, u_t along the three directions; v = G (u_r,u_s,u_t);
  *   w = D^T v_r + D^T v_s + D^T v_t.
- * u, w: device, nloc values of `dtype` (SEM_F64, or SEM_F32 when the mesh
- * was built with SEM_GEOM_F32; FP32 accumulation).  u and w must not
- * overlap. */
+ * u, w: device, nloc values of `dtype`:
+ *  - SEM_F64: FP64 fields, FP64 arithmetic;
+ *  - SEM_F32: FP32 fields, FP32 arithmetic (mesh built with SEM_GEOM_F32);
+ *  - SEM_F64_PAIR: FP64 fields (double in, double out); every value is
+ *    carried as an unevaluated sum of two floats (48 significant bits) and
+ *    the contractions run on the FP32 pipes with exact product and sum error
+ *    terms (mesh built with SEM_GEOM_PAIR).  Error about 2^-42 of the
+ *    line-wise magnitudes |D^T||G||D||u| (1e-12 in the relative 2-norm on
+ *    fields without strong cancellation).  Each element is scaled by a power of two
+ *    (exact) before the split, so any magnitude is handled; values below
+ *    2^-74 of the element's largest keep 24 bits, below 2^-126 of it they
+ *    count as zero; FP64 denormals count as zero; an Inf or NaN in an
+ *    element makes its whole output NaN.
+ * u and w must not overlap. */
 int sem_ax(const sem_mesh *mesh, const void *u, void *w, int dtype, void *stream);
 
 /* Local Helmholtz operator w = h1 A_L u + h2 B u (FP64). */

@@ -23,9 +23,10 @@ SEM_ERR_NAN = -5
 SEM_ERR_NOT_CONVERGED = -6
 SEM_ERR_TIMEOUT = -7
 SEM_ERR_UNSUPPORTED = -8
-SEM_F64, SEM_F32 = 0, 1
+SEM_F64, SEM_F32, SEM_F64_PAIR = 0, 1, 2
 SEM_GEOM_F32 = 1
 SEM_GEOM_RX = 2
+SEM_GEOM_PAIR = 4
 SEM_PCG_F64, SEM_PCG_MIXED = 0, 1
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
@@ -188,7 +189,8 @@ def _ptr(t):
 class Mesh:
     """A box mesh living in a caller-owned (PyTorch) device workspace."""
 
-    def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False, geom_rx: bool = False):
+    def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False, geom_rx: bool = False,
+                 geom_pair: bool = False):
         import numpy as np
         import torch
         self._verts = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 8, 3)
@@ -198,7 +200,8 @@ class Mesh:
         d.periodic[:] = [int(bool(a)) for a in periodic]
         d.dirichlet_faces = int(faces)
         d.vertices = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        d.geom_flags = (SEM_GEOM_F32 if geom_f32 else 0) | (SEM_GEOM_RX if geom_rx else 0)
+        d.geom_flags = ((SEM_GEOM_F32 if geom_f32 else 0) | (SEM_GEOM_RX if geom_rx else 0)
+                        | (SEM_GEOM_PAIR if geom_pair else 0))
         self.desc = d
         nbytes = lib().sem_mesh_workspace_bytes(ctypes.byref(d))
         if nbytes == 0:
@@ -238,11 +241,15 @@ class Mesh:
         return out
 
     # ---- operators
-    def ax(self, u, w=None):
+    def ax(self, u, w=None, pair: bool = False):
+        """w = A_L u; FP64 or FP32 by u's dtype; pair=True: FP64 fields with the
+        operator evaluated in FP32-pair arithmetic (SEM_F64_PAIR)."""
         import torch
         if w is None:
             w = torch.empty_like(u)
         dt = SEM_F64 if u.dtype == torch.float64 else SEM_F32
+        if pair:
+            dt = SEM_F64_PAIR
         check(lib().sem_ax(self.handle, _ptr(u), _ptr(w), dt, _stream()), "sem_ax")
         return w
 

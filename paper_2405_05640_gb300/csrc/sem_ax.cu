@@ -516,6 +516,8 @@ int sem_ax(const sem_mesh *m, const void *u, void *w, int dtype, void *stream) {
                              as_stream(stream));
     if (dtype == SEM_F32)
         return ax_launch_f32(m, static_cast<const float *>(u), static_cast<float *>(w), as_stream(stream));
+    if (dtype == SEM_F64_PAIR)
+        return ax_launch_pair(m, static_cast<const double *>(u), static_cast<double *>(w), as_stream(stream));
     return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
 }
 

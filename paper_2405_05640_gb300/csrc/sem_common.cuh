@@ -64,6 +64,7 @@ struct sem_mesh {
     double *verts;       // [E][8][3]
     double *G;           // [E][6][npt]
     float *G32;          // [E][6][npt] FP32 geometric factors, or nullptr
+    float2 *G2;          // [E][6][npt] FP32-pair (hi, lo) geometric factors, or nullptr
     double *B;           // [E][npt]
     double *mult;        // [nloc]
     double *minv;        // [nloc] 1/mult
@@ -171,6 +172,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
                   cudaStream_t st, const int *guard = nullptr, int gval = 0);
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st);
+// FP64 operator in FP32-pair arithmetic (sem_ax_pair.cu); needs m->G2.
+int ax_launch_pair(const sem_mesh *m, const double *u, double *w, cudaStream_t st);
 // Fused CG operator (see CgFuse); w receives the local (unassembled) A_L p.
 int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
                      cudaStream_t st);

@@ -226,12 +226,13 @@ static int validate(const sem_mesh_desc *d) {
     int64_t E = (int64_t)d->nel[0] * d->nel[1] * d->nel[2];
     int64_t nloc = E * (d->N + 1) * (d->N + 1) * (d->N + 1);
     if (nloc >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "E*(N+1)^3 must be < 2^31");
-    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX)) return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
+    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX | SEM_GEOM_PAIR))
+        return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
     return SEM_OK;
 }
 
 struct Layout {
-    size_t verts, G, G32, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
+    size_t verts, G, G32, G2, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -245,6 +246,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.verts = take(sizeof(double) * E * 24);
     L.G = take(sizeof(double) * E * 6 * npt);
     L.G32 = f32 ? take(sizeof(float) * E * 6 * npt) : 0;
+    L.G2 = (d->geom_flags & SEM_GEOM_PAIR) ? take(sizeof(float2) * E * 6 * npt) : 0;
     L.B = take(sizeof(double) * nloc);
     L.mult = take(sizeof(double) * nloc);
     L.minv = take(sizeof(double) * nloc);
@@ -386,6 +388,16 @@ __global__ void invert_kernel(const double *__restrict__ mult, double *__restric
     }
 }
 
+// FP32-pair copy of the geometric factors: g = hi + lo with hi the nearest
+// float and lo the nearest float to the remainder (48 significant bits).
+__global__ void split_pair_kernel(const double *__restrict__ a, float2 *__restrict__ b, int64_t n) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const double g = a[l];
+        const float hi = (float)g;
+        b[l] = make_float2(hi, (float)(g - (double)hi));
+    }
+}
+
 __global__ void copy_f32_from_f64(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
         b[l] = (float)a[l];
@@ -485,6 +497,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->verts = reinterpret_cast<double *>(base + L.verts);
     m->G = reinterpret_cast<double *>(base + L.G);
     m->G32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.G32) : nullptr;
+    m->G2 = (d->geom_flags & SEM_GEOM_PAIR) ? reinterpret_cast<float2 *>(base + L.G2) : nullptr;
     m->B = reinterpret_cast<double *>(base + L.B);
     m->mult = reinterpret_cast<double *>(base + L.mult);
     m->minv = reinterpret_cast<double *>(base + L.minv);
@@ -525,6 +538,10 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     geometry_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->verts, m->E, m->N, g, m->G, m->B, m->G32, m->rx,
                                                       m->d_err);
     CK(cudaGetLastError());
+    if (m->G2) {
+        split_pair_kernel<<<grid_for(m->E * 6 * m->npt), 256, 0, s>>>(m->G, m->G2, m->E * 6 * m->npt);
+        CK(cudaGetLastError());
+    }
     // multiplicity = Q Q^T 1
     fill_kernel<<<grid_for(m->nloc), 256, 0, s>>>(m->mult, m->nloc, 1.0);
     CK(cudaGetLastError());

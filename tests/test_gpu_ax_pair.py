@@ -1,0 +1,106 @@
+"""The FP64 operator evaluated in FP32-pair arithmetic (sem_ax, SEM_F64_PAIR)
+against the FP64 oracle.
+
+Bar: the same 1e-12 relative 2-norm as the FP64 operator on rough fields.
+The pair format carries 48 significant bits and every product and line sum
+keeps its exact rounding error, but the anchored sums and the FP32 low parts
+leave about 2^-42 of the line-wise magnitudes |D^T||G||D||u|; on smooth
+fields, where A u cancels strongly, that measure is the bar (2^-41,
+pointwise) with 1e-11 in the relative 2-norm.  The
+element-wise power-of-two scaling makes the result exactly homogeneous:
+w(2^k u) = 2^k w(u) bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_05640_gb300 import binding, inputs
+
+from test_gpu_parity import AX_TOL, CASES, IDS, _dev, _host, _rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _meshes(case):
+    V = case.vertices()
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_pair=True)
+    return om, gm
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_ax_pair_matches_oracle(case):
+    om, gm = _meshes(case)
+    rng = np.random.default_rng(12)
+    for u in (rng.standard_normal(om.nloc), om.scatter(rng.standard_normal(om.nglob)),
+              rng.uniform(0.0, 1.0, om.nloc)):
+        w = _host(gm.ax(_dev(u), pair=True))
+        assert _rel(w, om.ax_local(u)) <= AX_TOL
+
+
+@pytest.mark.parametrize("case", [CASES[4], CASES[6]], ids=[IDS[4], IDS[6]])
+def test_ax_pair_smooth_field(case):
+    # A smooth continuous field: A u cancels strongly, so the error is bounded
+    # against the line-wise magnitudes |D^T| |G| |D| |u| (pointwise, 2^-41).
+    om, gm = _meshes(case)
+    x, y, z = om.xyz
+    u = (np.sin(np.pi * x) * np.cos(2 * y) * np.sin(np.pi * z + 0.3) + 0.5 * x * y).reshape(-1)
+    ref = om.ax_local(u)
+    mag = oracle.ax_local(om.N, np.abs(om.D), np.abs(om.G), np.abs(u).reshape(om.E, -1)).reshape(-1)
+    wp = _host(gm.ax(_dev(u), pair=True))
+    assert np.all(np.abs(wp - ref) <= 2.0 ** -41 * mag)
+    assert _rel(wp, ref) <= 1e-11
+
+
+def test_ax_pair_exactly_homogeneous_and_scale_free():
+    om, gm = _meshes(CASES[5])
+    u = np.random.default_rng(13).standard_normal(om.nloc)
+    w = _host(gm.ax(_dev(u), pair=True))
+    for k in (-700, -200, 200, 700):
+        wk = _host(gm.ax(_dev(np.ldexp(u, k)), pair=True))
+        np.testing.assert_array_equal(wk, np.ldexp(w, k))
+
+
+def test_ax_pair_mixed_magnitudes_zero_and_nan_elements():
+    om, gm = _meshes(CASES[4])
+    rng = np.random.default_rng(14)
+    u = rng.standard_normal((om.E, om.npt))
+    u[1] *= 1e-30           # a tiny element next to O(1) ones: element-wise accuracy holds
+    u[2] = 0.0              # exact zeros
+    u[3, 5] = np.nan        # a NaN poisons its own element only
+    w = _host(gm.ax(_dev(u.reshape(-1)), pair=True)).reshape(om.E, -1)
+    assert np.isnan(w[3]).all()
+    assert np.array_equal(w[2], np.zeros(om.npt))
+    ok = np.ones(om.E, bool)
+    ok[3] = False
+    ref = oracle.ax_local(om.N, om.D, om.G[ok], u[ok])
+    got = w[ok]
+    assert np.isfinite(got).all()
+    for e in range(got.shape[0]):
+        if np.linalg.norm(ref[e]) > 0:
+            assert _rel(got[e], ref[e]) <= AX_TOL
+
+
+def test_ax_pair_needs_pair_geometry():
+    case = CASES[2]
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    with pytest.raises(binding.SemError) as ei:
+        gm.ax(_dev(np.zeros(gm.nloc)), pair=True)
+    assert ei.value.status == binding.SEM_ERR_INVALID_ARG
+
+
+@pytest.mark.slow
+def test_full_size_ax_pair_sampled_elements():
+    # the 32^3 channel at N = 7 in the benchmark's launch configuration
+    case = inputs.channel(32, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_pair=True)
+    rng = np.random.default_rng(22)
+    u = rng.standard_normal(case.nloc)
+    w = _host(gm.ax(_dev(u), pair=True)).reshape(case.E, -1)
+    sel = np.unique(np.concatenate([[0, case.E - 1], rng.integers(0, case.E, 300)]))
+    _, G, _, st = oracle.geometry(case.N, V[sel])
+    assert st == 0
+    ref = oracle.ax_local(case.N, oracle.deriv(case.N), G, u.reshape(case.E, -1)[sel])
+    assert _rel(w[sel], ref) <= AX_TOL
