@@ -190,6 +190,34 @@ struct AxTune {
 extern AxTune g_ax_tune[2][2][2][kMaxN1];
 int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);
 
+// Box topology for the arithmetic (index-free) gather-scatter of the CG loop:
+// element e = ex + nel0 (ey + nel1 ez), local point i + N1 (j + N1 k).
+struct BoxTopo {
+    int N, N1, NPT;
+    int nel[3], per[3];
+    int faces;  // Dirichlet face bits (2a: low face of axis a, 2a+1: high face)
+    int64_t E;
+};
+inline BoxTopo box_topo(const sem_mesh *m) {
+    BoxTopo b;
+    b.N = m->N;
+    b.N1 = m->n1;
+    b.NPT = m->npt;
+    for (int a = 0; a < 3; ++a) {
+        b.nel[a] = m->nel[a];
+        b.per[a] = m->periodic[a];
+    }
+    b.faces = m->faces;
+    b.E = m->E;
+    return b;
+}
+// Sum the copies shared across y- and z-element faces (edges included), in
+// place, no mask: the first two passes of the axis-by-axis gather-scatter;
+// the x pass and the Dirichlet mask are applied by the CG update that reads
+// the field (sem_pcg.cu).
+int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const int *guard = nullptr,
+                 int gval = 0);
+
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies
 constexpr int kGsSumMask = 1;   // sum copies, then zero Dirichlet nodes

@@ -124,6 +124,117 @@ int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, 
     return SEM_OK;
 }
 
+// ---- axis-by-axis gather-scatter on the box topology (CG loop) --------
+// Summing the copies of every node can be done one axis at a time: after the
+// y pass each copy holds the sum over its y-neighbours, after the z pass over
+// its y and z neighbours, after the x pass over all.  The y and z passes run
+// together here, one thread per (y, z) node group of one x position: the
+// group's 2 or 4 copies are read, summed in a fixed order and written back
+// (every copy gets the same bits).  Indices are computed, not loaded; the
+// fastest thread index runs along x (i, then ex), so each group of N+1
+// threads reads whole 32-byte sectors.
+
+// Copies along one axis of global node index G (0 <= G < nel N + !per):
+// 1 copy (e0, i0) or 2 copies (e0, N) and (e1, 0) on an element boundary.
+__device__ __forceinline__ int axis_copies(int G, int nel, int per, int N, int &e0, int &i0, int &e1) {
+    if (!per && G == nel * N) {
+        e0 = nel - 1;
+        i0 = N;
+        e1 = -1;
+        return 1;
+    }
+    const int e = G / N, i = G - e * N;
+    if (i == 0 && (e > 0 || per)) {
+        e0 = e > 0 ? e - 1 : nel - 1;
+        i0 = N;
+        e1 = e;
+        return 2;
+    }
+    e0 = e;
+    i0 = i;
+    e1 = -1;
+    return 1;
+}
+
+// Thread t (32-bit: t < 2 nloc < 2^32) -> x position (ex, i) = t mod nxl and
+// group q = t / nxl: q < nA: J = the (q / Gz)-th shared y boundary, K = q mod
+// Gz; else J = any y node that is not shared (shared ones are skipped: they
+// belong to the first set), K = a shared z boundary.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    gs_yz_kernel(T *__restrict__ u, BoxTopo B, unsigned nA, unsigned ntot, int nKs, const int *__restrict__ guard,
+                 int gval) {
+    if (guard && *guard != gval) return;
+    const unsigned nxl = (unsigned)(B.nel[0] * B.N1);  // x positions (ex, i)
+    const unsigned Gz = (unsigned)(B.nel[2] * B.N + (B.per[2] ? 0 : 1));
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += gridDim.x * blockDim.x) {
+        const unsigned q = t / nxl;
+        const int xi = (int)(t - q * nxl);
+        const int ex = xi / B.N1, i = xi - ex * B.N1;
+        int J, K;
+        if (q < nA) {
+            const unsigned a = q / Gz;
+            K = (int)(q - a * Gz);
+            J = (int)(B.per[1] ? a : a + 1) * B.N;
+        } else {
+            const unsigned b = q - nA;
+            const unsigned jj = b / (unsigned)nKs;
+            const int c = (int)(b - jj * (unsigned)nKs);
+            J = (int)jj;
+            K = (B.per[2] ? c : c + 1) * B.N;
+        }
+        int ey[2], jy[1], ez[2], kz[1];
+        const int ny = axis_copies(J, B.nel[1], B.per[1], B.N, ey[0], jy[0], ey[1]);
+        if (q >= nA && ny == 2) continue;  // a shared y node: done in the first set
+        const int nz = axis_copies(K, B.nel[2], B.per[2], B.N, ez[0], kz[0], ez[1]);
+        if (ny * nz < 2) continue;
+        auto at = [&](int ay, int bz, int jj, int kk) {
+            const int64_t e = ex + (int64_t)B.nel[0] * (ey[ay] + (int64_t)B.nel[1] * ez[bz]);
+            return e * B.NPT + i + B.N1 * (jj + B.N1 * kk);
+        };
+        // copies in the order (y0,z0), (y1,z0), (y0,z1), (y1,z1); y1 / z1 sit at j / k = 0
+        const int64_t i00 = at(0, 0, jy[0], kz[0]);
+        if (ny == 2 && nz == 2) {
+            const int64_t i10 = at(1, 0, 0, kz[0]), i01 = at(0, 1, jy[0], 0), i11 = at(1, 1, 0, 0);
+            const T s = ((u[i00] + u[i10]) + u[i01]) + u[i11];
+            u[i00] = s;
+            u[i10] = s;
+            u[i01] = s;
+            u[i11] = s;
+        } else {
+            const int64_t i1 = ny == 2 ? at(1, 0, 0, kz[0]) : at(0, 1, jy[0], 0);
+            const T s = u[i00] + u[i1];
+            u[i00] = s;
+            u[i1] = s;
+        }
+    }
+}
+
+int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const int *guard, int gval) {
+    const BoxTopo B = box_topo(m);
+    const int64_t Gy = (int64_t)B.nel[1] * B.N + (B.per[1] ? 0 : 1);
+    const int64_t Gz = (int64_t)B.nel[2] * B.N + (B.per[2] ? 0 : 1);
+    const int nJs = B.per[1] ? B.nel[1] : B.nel[1] - 1;
+    const int nKs = B.per[2] ? B.nel[2] : B.nel[2] - 1;
+    const int64_t nxl = (int64_t)B.nel[0] * B.N1;
+    const int64_t nA = (int64_t)nJs * Gz;
+    const int64_t ntot = (nA + Gy * nKs) * nxl;
+    if (ntot == 0) return SEM_OK;
+    if (ntot >= (int64_t(1) << 32)) return fail(SEM_ERR_UNSUPPORTED, "gs_yz: too many node groups");
+    int64_t g = (ntot + 255) / 256;
+    if (g > (int64_t)m->num_sms * 16) g = (int64_t)m->num_sms * 16;
+    if (dtype == SEM_F64)
+        gs_yz_kernel<double><<<(int)g, 256, 0, st>>>(static_cast<double *>(u), B, (unsigned)nA, (unsigned)ntot, nKs,
+                                                     guard, gval);
+    else if (dtype == SEM_F32)
+        gs_yz_kernel<float><<<(int)g, 256, 0, st>>>(static_cast<float *>(u), B, (unsigned)nA, (unsigned)ntot, nKs,
+                                                    guard, gval);
+    else
+        return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
 __global__ void scatter_kernel(const double *__restrict__ ug, double *__restrict__ ul, int64_t E, int N,
                                int nx, int ny, int64_t Gx, int64_t Gy, int64_t Gz, int px, int py, int pz) {
     const int n1 = N + 1;

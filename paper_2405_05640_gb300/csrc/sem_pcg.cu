@@ -251,6 +251,167 @@ __global__ void __launch_bounds__(kPThreads)
 
 static bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// N1 consecutive values of a line into registers (16-byte vectors when VEC).
+template <typename T, int N1, bool VEC>
+__device__ __forceinline__ void load_line(const T *__restrict__ a, T (&v)[N1]) {
+    if (VEC) {
+#pragma unroll
+        for (int c = 0; c < N1; c += V16<T>::n) {
+            const V16<T> q = ld16(a + c);
+#pragma unroll
+            for (int d = 0; d < V16<T>::n; ++d) v[c + d] = q.a[d];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < N1; ++c) v[c] = a[c];
+    }
+}
+template <typename T, int N1, bool VEC>
+__device__ __forceinline__ void store_line(T *__restrict__ a, const T (&v)[N1]) {
+    if (VEC) {
+#pragma unroll
+        for (int c = 0; c < N1; c += V16<T>::n) {
+            V16<T> q;
+#pragma unroll
+            for (int d = 0; d < V16<T>::n; ++d) q.a[d] = v[c + d];
+            st16(a + c, q);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < N1; ++c) a[c] = v[c];
+    }
+}
+
+// Shared / Dirichlet status of a face point along one axis: the point sits on
+// the low (lo = true) or high face of element index e of nel.
+__device__ __forceinline__ void face_status(int e, int nel, int per, bool lo, int dir_bit_lo, int dir_bit_hi,
+                                           int faces, int &shared, bool &dirichlet) {
+    if (lo) {
+        shared = (e > 0 || per) ? 1 : 0;
+        dirichlet = !per && e == 0 && (faces & dir_bit_lo);
+    } else {
+        shared = (e < nel - 1 || per) ? 1 : 0;
+        dirichlet = !per && e == nel - 1 && (faces & dir_bit_hi);
+    }
+}
+
+// CG update with the last gather-scatter pass folded in.  w holds A_L p after
+// the y and z passes (gs_yz_launch); one thread per r-line (e, j, k):
+//   w(e,0)  <- w(left, N) + w(e, 0)      if e has a left neighbour in x,
+//   w(e,N)  <- w(e, N) + w(right, 0)     if it has a right one
+// (the neighbour's thread forms the same sum from the same operands in the
+// same order, so all copies stay bit-identical); w <- 0 on Dirichlet nodes;
+// then x += alpha p, r -= alpha w and the <r,r>, <r,z> partials with the
+// weight 1/mult computed from the point's position (a power of two, the same
+// value as the mesh's stored 1/mult).
+template <typename T, int N, bool VEC>
+__global__ void __launch_bounds__(kPThreads)
+    pcg_update_box_kernel(T *__restrict__ x, const T *__restrict__ dinv, BoxTopo B, PcgWork<T> W) {
+    if (W.scal->done) return;
+    constexpr int N1 = N + 1, NL = N1 * N1, NPT = NL * N1;
+    const T alpha = (T)W.scal->alpha;
+    double v[2] = {0.0, 0.0};
+    T f0 = T(0), f1 = T(0);
+    const int nx = B.nel[0], ny = B.nel[1];
+    const int64_t nlines = B.E * NL;
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < nlines;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = L / NL;
+        const int jk = (int)(L - e * NL);
+        const int j = jk % N1, k = jk / N1;
+        const int ex = (int)(e % nx);
+        const int64_t eyz = e / nx;
+        const int ey = (int)(eyz % ny), ez = (int)(eyz / ny);
+        const int64_t base = L * N1;
+        T p[N1], w[N1], xv[N1], r[N1], di[N1];
+        load_line<T, N1, VEC>(W.p + base, p);
+        load_line<T, N1, VEC>(W.w + base, w);
+        load_line<T, N1, VEC>(x + base, xv);
+        load_line<T, N1, VEC>(W.r + base, r);
+        load_line<T, N1, VEC>(dinv + base, di);
+        // y and z status of the whole line
+        int sy = 0, sz = 0;
+        bool dy = false, dz = false;
+        if (j == 0 || j == N) face_status(ey, ny, B.per[1], j == 0, 4, 8, B.faces, sy, dy);
+        if (k == 0 || k == N) face_status(ez, B.nel[2], B.per[2], k == 0, 16, 32, B.faces, sz, dz);
+        // x pass at the two ends (neighbour values read before any change)
+        int sx0 = 0, sxN = 0;
+        bool dx0 = false, dxN = false;
+        face_status(ex, nx, B.per[0], true, 1, 2, B.faces, sx0, dx0);
+        face_status(ex, nx, B.per[0], false, 1, 2, B.faces, sxN, dxN);
+        const T wl = sx0 ? W.w[(ex > 0 ? e - 1 : e + nx - 1) * NPT + (int64_t)jk * N1 + N] : T(0);
+        const T wr = sxN ? W.w[(ex < nx - 1 ? e + 1 : e - (nx - 1)) * NPT + (int64_t)jk * N1] : T(0);
+        const T w0 = w[0], wN = w[N];
+        if (sx0) w[0] = wl + w0;
+        if (sxN) w[N] = wN + wr;
+        const bool dyz = dy || dz;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int sx = i == 0 ? sx0 : (i == N ? sxN : 0);
+            const bool dd = dyz || (i == 0 && dx0) || (i == N && dxN);
+            const int sh = sx + sy + sz;
+            const T mi = sh == 0 ? T(1) : (sh == 1 ? T(0.5) : (sh == 2 ? T(0.25) : T(0.125)));
+            const T wt = dd ? T(0) : w[i];
+            update_point(alpha, p[i], wt, mi, di[i], xv[i], r[i], v, f0, f1);
+        }
+        store_line<T, N1, VEC>(x + base, xv);
+        store_line<T, N1, VEC>(W.r + base, r);
+    }
+    if (sizeof(T) == 4) {
+        v[0] = (double)f0;
+        v[1] = (double)f1;
+    }
+    double t[2];
+    if (grid_reduce<2>(v, W.partial + 2 * kPBlocks, &W.scal->cnt[2], t)) {
+        PcgScal *s = W.scal;
+        s->rr = t[0];
+        s->beta = t[1] / s->rho;
+        s->rho_prev = s->rho;
+        s->rho = t[1];
+        s->iter += 1;
+        if (!isfinite(t[0])) {
+            s->done = 1;
+            s->status = SEM_ERR_NAN;
+        } else if (t[0] <= s->tol2) {
+            s->done = 1;
+            s->status = SEM_OK;
+        } else if (s->iter >= s->max_iter) {
+            s->done = 1;
+            s->status = SEM_ERR_NOT_CONVERGED;
+        }
+    }
+}
+
+template <typename T, int N>
+static int launch_update_box_n(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st) {
+    constexpr int N1 = N + 1;
+    const BoxTopo B = box_topo(m);
+    const bool vec = (N1 * sizeof(T)) % 16 == 0 && al16(x) && al16(dinv) && al16(W.p) && al16(W.w) && al16(W.r);
+    auto kv = pcg_update_box_kernel<T, N, ((N1 * sizeof(T)) % 16 == 0)>;
+    auto ks = pcg_update_box_kernel<T, N, false>;
+    auto kern = vec ? kv : ks;
+    // one wave: every resident block takes an equal share of the lines
+    int per_sm = 0;
+    SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, 0));
+    int grid = m->num_sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > kPBlocks) grid = kPBlocks;
+    kern<<<grid, kPThreads, 0, st>>>(x, dinv, B, W);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+template <typename T>
+static int launch_update_box(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st) {
+    switch (m->N) {
+#define SEM_UB_CASE(n) \
+    case n: return launch_update_box_n<T, n>(m, x, dinv, W, st);
+        SEM_UB_CASE(1) SEM_UB_CASE(2) SEM_UB_CASE(3) SEM_UB_CASE(4) SEM_UB_CASE(5)
+        SEM_UB_CASE(6) SEM_UB_CASE(7) SEM_UB_CASE(8) SEM_UB_CASE(9) SEM_UB_CASE(10) SEM_UB_CASE(11)
+#undef SEM_UB_CASE
+        default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
+    }
+}
+
 template <typename T>
 static int launch_update(T *x, const T *dinv, const T *minv, int64_t n, const PcgWork<T> &W, cudaStream_t st) {
     if (al16(x) && al16(dinv) && al16(minv) && al16(W.p) && al16(W.w) && al16(W.r))
@@ -465,7 +626,6 @@ const float *minv_of<float>(const sem_mesh *m) { return m->minv32; }
 template <typename T>
 static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max_iter, int check, double h1,
                    double h2, cudaStream_t st, SolveCtx &c, PcgScal *h) {
-    const T *minv = minv_of<T>(m);
     CgFuse<T> cg{W.r, dinv, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
     while (true) {
@@ -484,13 +644,14 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
                                            reinterpret_cast<float *>(W.w), st);
             c.tax.stop(st);
             if (s != SEM_OK) return s;
-            // w <- M Q Q^T w
+            // w <- M Q Q^T w, axis by axis: the y and z passes here, the x
+            // pass and the mask inside the update
             c.tgs.start(st);
-            s = gs_launch(m, W.w, sizeof(T) == 8 ? SEM_F64 : SEM_F32, kGsSumMask, st);
+            s = gs_yz_launch(m, W.w, sizeof(T) == 8 ? SEM_F64 : SEM_F32, st);
             c.tgs.stop(st);
             if (s != SEM_OK) return s;
             // x += alpha p; r -= alpha w; rr, rz; beta; convergence flag
-            s = launch_update<T>(x, dinv, minv, m->nloc, W, st);
+            s = launch_update_box<T>(m, x, dinv, W, st);
             if (s != SEM_OK) return s;
             c.launches += 3;
             c.ax_launches += 1;

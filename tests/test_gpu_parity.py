@@ -161,6 +161,29 @@ def test_pcg_random_rhs_matches_oracle(case):
     np.testing.assert_array_equal(xh, one[om.gid])
 
 
+# Topologies that stress the axis-by-axis gather-scatter of the CG loop: a
+# single periodic element along x (its two x faces are one node layer), odd
+# N + 1 (no vector loads), N = 2 .. 11, periodic axes mixed with Dirichlet
+# faces on the others.
+TOPO = [c for c in CASES if c.name in ("n2_jitter", "n3_periodic1", "n4_even", "n7_ragged", "n11_deformed")]
+
+
+@pytest.mark.parametrize("mixed", [False, True], ids=["f64", "mixed"])
+@pytest.mark.parametrize("case", TOPO, ids=[c.name for c in TOPO])
+def test_pcg_topologies_match_oracle(case, mixed):
+    om, gm = _pair(case, geom_f32=mixed)
+    b = om.scatter(case.rhs_global())
+    xo, _, _, sto = om.pcg(b, tol=1e-12, max_iter=20000)
+    kw = dict(precision=binding.SEM_PCG_MIXED, inner_tol=1e-4) if mixed else {}
+    xg, st = gm.pcg(_dev(b), tol=1e-12, max_iter=20000, **kw)
+    assert sto == 0 and st["status"] == 0, st
+    xh = _host(xg)
+    assert _rel(xh, xo) <= SOL_TOL
+    one = np.zeros(om.nglob)
+    one[om.gid] = xh
+    np.testing.assert_array_equal(xh, one[om.gid])
+
+
 def test_pcg_initial_guess_and_absolute_tolerance():
     case = inputs.deformed_cube(4, 5)
     om, gm = _pair(case)
