@@ -48,7 +48,7 @@ AX_BYTES_PER_POINT = {"f64": 64}
 # DRAM traffic per launch of the operator kernel from one ncu capture (bytes),
 # keyed by the SHA-256 of the kernel source it was taken on; null once the
 # source changes.
-NCU_TRAFFIC = {"ax_f32_cg": {"bytes_per_launch": 664.0e6, "src_sha": "6a9970ea35dbd9a2",
+NCU_TRAFFIC = {"ax_f32_cg": {"bytes_per_launch": 664.0e6, "src_sha": "8d7d3a6f1233f987",
                              "from": "profiles/ax_f32cg_n7_nel20_ncu_full.md (20^3 case scaled x4.096)"}}
 
 
@@ -252,7 +252,7 @@ def run_ours(args):
     _build.build()
     case = inputs.channel(args.nel, args.order)
     V = case.vertices()
-    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True, geom_pair=True)
     bg = torch.from_numpy(case.rhs_global()).cuda()
     b = gm.scatter(bg)
     base = dict(tol=TOL, max_iter=50000, check_every=32)
@@ -334,6 +334,32 @@ def run_ours(args):
                     "achieved_tflops": round(flops / (f64_ms * 1e-3) / 1e12, 3), "peak_tflops": 1.257,
                     "peak_source": "measured FMA-chain probe on GB300 (FP64)",
                     "gdofs": round(case.n_paper / (f64_ms * 1e-3) / 1e9, 3)}
+    # the FP64 operator in FP32-pair arithmetic (sem_ax, SEM_F64_PAIR): same
+    # 64 algorithmic B/point as the FP64 operator, run on the FP32 pipes
+    u = torch.randn(case.nloc, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(u)
+
+    def _op_ms(pair, reps=20):
+        for _ in range(3):
+            gm.ax(u, w, pair=pair)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for _ in range(reps):
+            gm.ax(u, w, pair=pair)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        return q0.elapsed_time(q1) / reps
+
+    pair_ms, plain64_ms = _op_ms(True), _op_ms(False)
+    pair_bytes = OP_BYTES["f64"] * case.nloc
+    roofline_pair = {"kernel": "ax_pair_kernel<7> (FP64 in/out, FP32-pair arithmetic)", "bound": "issue (fp32 alu)",
+                     "mean_launch_ms": round(pair_ms, 4),
+                     "achieved_gbs": round(pair_bytes / (pair_ms * 1e-3) / 1e9, 1),
+                     "hbm_frac": round(pair_bytes / (pair_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "gdofs": round(case.n_paper / (pair_ms * 1e-3) / 1e9, 3),
+                     "fp64_operator_ms": round(plain64_ms, 4),
+                     "speedup_vs_fp64_operator": round(plain64_ms / pair_ms, 3)}
     st = ser["last"]
     rec = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -342,7 +368,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "E": case.E, "N": case.N, "n_paper": case.n_paper,
                    "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL,
                    "precision": "FP64 iterative refinement around FP32 Jacobi-PCG (inner tol 1e-2)",
-                   "l2": "inputs larger than L2 (FP32 G 403 MB, FP64 G 805 MB)",
+                   "l2": "inputs larger than L2 (FP32 G 403 MB, FP64 G 805 MB, pair G 805 MB)",
                    "parallelism": f"replicas x{world}"},
         "pcg": {"chosen_time_to_1e-8_ms": round(ms_per_step, 3),
                 "plain_fp64_time_to_1e-8_ms": round(plain_ms, 3),
@@ -356,6 +382,7 @@ def run_ours(args):
         "ax_kernel_gdofs": round(case.n_paper / (ax_avg_ms * 1e-3) / 1e9, 3),
         "roofline": roofline,
         "roofline_fp64_operator": roofline_f64,
+        "roofline_fp64_pair_operator": roofline_pair,
         "gpu_launches": ser["launches"],
         "e2e": e2e,
         "clocks": clk.summary(),
