@@ -64,6 +64,14 @@ extern "C" {
                                       sem_weak_div and the sem_ns_* stepper */
 #define SEM_GEOM_PAIR 4            /* FP32-pair (hi, lo) factors, 48 bytes per point,
                                       for sem_ax with SEM_F64_PAIR */
+#define SEM_GEOM_AFFINE 8          /* every element is an axis-aligned box (checked;
+                                      SEM_ERR_MESH otherwise): the FP32 operator
+                                      (sem_ax SEM_F32, the mixed solver's inner loop)
+                                      then forms G = rho_i rho_j rho_k (a, b, c)_e
+                                      from 3 scalars per element instead of reading
+                                      6 factors per point (20 instead of 44 bytes
+                                      per point in the fused CG operator); needs
+                                      SEM_GEOM_F32 */
 
 typedef struct sem_mesh sem_mesh;  /* opaque; freed by sem_mesh_destroy */
 
@@ -412,6 +420,20 @@ int sem_autotune_operator(const sem_mesh *mesh, int dtype, int fused_cg, void *d
                           void *stream, sem_tune_result *out);
 /* Back to the default launch shapes (2 stages, occupancy-limited). */
 int sem_autotune_reset(void);
+
+/* ---- Performance model for splitting one problem over devices -----------
+ * Section 4.1 (Eq. 2-7): a homogeneous cost C (here: element-iterations of a
+ * solve) split over ndev devices; device i computes C_i at its best
+ * performance P_opt[i] (cost per second) and holds at most C_max[i] (C_max
+ * NULL or an entry <= 0: unlimited).  T_min = min over splits with
+ * sum C_i = C, C_i <= C_max[i] of max_i C_i / P_opt[i]: C / sum P_opt when
+ * the proportional split fits every capacity, else the devices whose
+ * capacity binds are filled and the others share the rest in proportion to
+ * P_opt (exact minimiser).  Writes *T_min and C_split[ndev] (host).  Returns
+ * SEM_ERR_INVALID_ARG (ndev < 1, a P_opt <= 0, C < 0) or SEM_ERR_WORKSPACE
+ * (the capacities hold less than C).  Host computation, no GPU. */
+int sem_perf_model(int ndev, const double *P_opt, const double *C_max, double C, double *T_min,
+                   double *C_split);
 
 /* Read and clear the mesh's device error word after waiting for `stream`:
  * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */

@@ -27,6 +27,7 @@ SEM_F64, SEM_F32, SEM_F64_PAIR = 0, 1, 2
 SEM_GEOM_F32 = 1
 SEM_GEOM_RX = 2
 SEM_GEOM_PAIR = 4
+SEM_GEOM_AFFINE = 8
 SEM_PCG_F64, SEM_PCG_MIXED = 0, 1
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
@@ -138,6 +139,8 @@ _SIGS = {
     "sem_ns_step": ([_VP, ctypes.c_double, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgOpts), _VP,
                      ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_ns_kinetic_energy": ([_VP, ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
+                       ctypes.c_int),
 }
 
 _lib = None
@@ -190,7 +193,7 @@ class Mesh:
     """A box mesh living in a caller-owned (PyTorch) device workspace."""
 
     def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False, geom_rx: bool = False,
-                 geom_pair: bool = False):
+                 geom_pair: bool = False, geom_affine: bool = False):
         import numpy as np
         import torch
         self._verts = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 8, 3)
@@ -201,7 +204,7 @@ class Mesh:
         d.dirichlet_faces = int(faces)
         d.vertices = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.geom_flags = ((SEM_GEOM_F32 if geom_f32 else 0) | (SEM_GEOM_RX if geom_rx else 0)
-                        | (SEM_GEOM_PAIR if geom_pair else 0))
+                        | (SEM_GEOM_PAIR if geom_pair else 0) | (SEM_GEOM_AFFINE if geom_affine else 0))
         self.desc = d
         nbytes = lib().sem_mesh_workspace_bytes(ctypes.byref(d))
         if nbytes == 0:
@@ -592,3 +595,16 @@ def pcg_solve_batched(meshes, bs, xs=None, scratch=None, raise_on_error=True, **
     if raise_on_error and st != SEM_OK:
         raise SemError(st, "sem_pcg_solve_batched")
     return xs, [s.as_dict() for s in stats]
+
+
+def perf_model(P_opt, C, C_max=None):
+    """sem_perf_model: (T_min, split) of cost C over devices with best
+    performances P_opt and capacities C_max (None / <= 0: unlimited).  Host."""
+    import numpy as np
+    P = np.ascontiguousarray(P_opt, dtype=np.float64)
+    cap = None if C_max is None else np.ascontiguousarray(C_max, dtype=np.float64)
+    out = np.zeros(len(P))
+    t = ctypes.c_double()
+    check(lib().sem_perf_model(len(P), _VP(P.ctypes.data), None if cap is None else _VP(cap.ctypes.data),
+                               float(C), ctypes.byref(t), _VP(out.ctypes.data)), "sem_perf_model")
+    return t.value, out

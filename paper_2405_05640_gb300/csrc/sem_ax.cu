@@ -22,23 +22,52 @@
 namespace sem {
 
 // Slabs per stage: the input field (u; or r, dinv, p in the fused CG mode),
-// the six geometric factors, and B (Helmholtz, FP64).
-template <int N, typename T, bool HELM, bool CG>
+// the six geometric factors (AFF: the element's 4 affine scalars instead),
+// and B (Helmholtz, FP64).
+template <int N, typename T, bool HELM, bool CG, bool AFF>
 __host__ __device__ constexpr int ax_stage_bytes() {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
-    return ((NPT * ((CG ? 3 : 1) + 6) * (int)sizeof(T) + (HELM ? NPT * 8 : 0)) + 15) / 16 * 16;
+    return ((NPT * ((CG ? 3 : 1) + (AFF ? 0 : 6)) * (int)sizeof(T) + (AFF ? 16 : 0) + (HELM ? NPT * 8 : 0)) + 15) /
+           16 * 16;
 }
 
-template <int N, typename T, bool HELM, bool CG>
+template <int N, typename T, bool HELM, bool CG, bool AFF>
 __host__ __device__ constexpr int ax_smem_bytes(int nst) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    return nst * ax_stage_bytes<N, T, HELM, CG>() + 2 * NPT * (int)sizeof(T) +
+    return nst * ax_stage_bytes<N, T, HELM, CG, AFF>() + 2 * NPT * (int)sizeof(T) +
            ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4 + 64;
 }
 
 template <int N>
 __host__ __device__ constexpr int ax_threads() {
     return ((N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
+// N1 consecutive shared-memory values into registers: 16-byte vector loads
+// when a line is a whole number of 16-byte vectors (lines start 16-byte
+// aligned: every slab is), else scalar loads.
+template <typename T, int N1>
+__device__ __forceinline__ void smem_line(const T *a, T (&v)[N1]) {
+    if constexpr ((N1 * sizeof(T)) % 16 == 0) {
+        constexpr int V = 16 / sizeof(T);
+#pragma unroll
+        for (int c = 0; c < N1; c += V) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(a + c);
+                v[c] = q.x;
+                v[c + 1] = q.y;
+                v[c + 2] = q.z;
+                v[c + 3] = q.w;
+            } else {
+                const double2 q = *reinterpret_cast<const double2 *>(a + c);
+                v[c] = q.x;
+                v[c + 1] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < N1; ++c) v[c] = a[c];
+    }
 }
 
 struct AxArgs {
@@ -48,15 +77,16 @@ struct AxArgs {
     double h1, h2;
     const int *guard;  // if set, the kernel runs only when *guard == guard_value
     int guard_value;
+    float rho[kMaxN1];  // GLL weights (affine mode: G = rho_i rho_j rho_k (a, b, c)_e)
 };
 
 // Launch shape of the operator per (precision, Helmholtz, fused CG, N):
 // pipeline stages and a cap on resident CTAs per SM (0 = occupancy limit).
 // Defaults: 2 stages, no cap; sem_autotune_operator measures and sets them.
-AxTune g_ax_tune[2][2][2][kMaxN1] = {};
+AxTune g_ax_tune[2][2][2][2][kMaxN1] = {};
 
-static AxTune tune_for(int dt, bool helm, bool cg, int N) {
-    AxTune t = g_ax_tune[dt][helm][cg][N];
+static AxTune tune_for(int dt, bool helm, bool cg, bool aff, int N) {
+    AxTune t = g_ax_tune[dt][helm][cg][aff][N];
     if (t.nst <= 0) t.nst = 2;
     return t;
 }
@@ -64,14 +94,21 @@ static AxTune tune_for(int dt, bool helm, bool cg, int N) {
 // One element per CTA at a time (persistent grid).  Modes:
 //   plain / HELM: w = A_L u  (or h1 A_L u + h2 B u);
 //   CG: p <- dinv r + beta p (written back), w = A_L p (or Helmholtz), and
-//       sum_l p_l w_l reduced over the grid into alpha = rho / pw.
-template <int N, typename T, bool HELM, bool CG, typename DM>
+//       sum_l p_l w_l reduced over the grid into alpha = rho / pw;
+//   AFF (axis-aligned box elements): G is diagonal and factorises, G_rr =
+//       rho_i rho_j rho_k a_e etc.; G points at the [E][4] scalars (a, b, c, 0).
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM>
 __global__ void __launch_bounds__(ax_threads<N>())
     ax_kernel(const T *__restrict__ u, T *__restrict__ w, const T *__restrict__ G,
               const double *__restrict__ Bm, const DM Dm, const AxArgs args, const CgFuse<T> cg,
               int *__restrict__ err) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    constexpr int SB = ax_stage_bytes<N, T, HELM, CG>();
+    constexpr int SB = ax_stage_bytes<N, T, HELM, CG, AFF>();
+    // Vector r-line loads and D_kl as constant-bank operands cut the shared-
+    // memory instructions; measured faster for the FP32 plain and affine
+    // forms, slower for the general fused CG form and FP64, which keep
+    // scalar loads and D from shared memory.
+    constexpr bool kLineLoads = sizeof(T) == 4 && (AFF || !CG);
     constexpr int NIN = CG ? 3 : 1;  // input slabs
     extern __shared__ __align__(128) unsigned char smem[];
     if (CG && cg.scal->done) return;  // uniform: the solve has converged or paused
@@ -103,10 +140,20 @@ __global__ void __launch_bounds__(ax_threads<N>())
         rDtj[l] = active ? sD[l * N1 + j] : T(0);
     }
     const T beta = CG ? (T)cg.scal->beta : T(0);
+    T rij = T(0);  // rho_i rho_j (affine mode); unrolled selects keep the parameters in the constant bank
+    if (AFF && active) {
+        T ri = T(0), rj = T(0);
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+            ri = q == i ? (T)args.rho[q] : ri;
+            rj = q == j ? (T)args.rho[q] : rj;
+        }
+        rij = ri * rj;
+    }
 
     const int64_t E = args.E;
     const int64_t stride = gridDim.x;
-    const uint32_t ubytes = NPT * sizeof(T), gbytes = 6 * NPT * sizeof(T);
+    const uint32_t ubytes = NPT * sizeof(T), gbytes = AFF ? 16 : 6 * NPT * sizeof(T);
     const uint32_t bbytes = HELM ? NPT * sizeof(double) : 0;
 
     auto stage_ptr = [&](int s) { return smem + s * SB; };
@@ -120,7 +167,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
         } else {
             bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
         }
-        bulk_g2s(st + NIN * ubytes, G + e * 6 * NPT, gbytes, &bar[s]);
+        bulk_g2s(st + NIN * ubytes, AFF ? G + e * 4 : G + e * 6 * NPT, gbytes, &bar[s]);
         if (HELM) bulk_g2s(st + NIN * ubytes + gbytes, Bm + e * NPT, bbytes, &bar[s]);
     };
 
@@ -153,8 +200,8 @@ __global__ void __launch_bounds__(ax_threads<N>())
             } else {
                 for (int q = tid; q < NPT; q += blockDim.x) dst[q] = u[e * NPT + q];
             }
-            const T *gs = G + e * 6 * NPT;
-            for (int q = tid; q < 6 * NPT; q += blockDim.x) dst[NIN * NPT + q] = gs[q];
+            const T *gs = AFF ? G + e * 4 : G + e * 6 * NPT;
+            for (int q = tid; q < (AFF ? 4 : 6 * NPT); q += blockDim.x) dst[NIN * NPT + q] = gs[q];
             if (HELM) {
                 double *db = reinterpret_cast<double *>(st + NIN * ubytes + gbytes);
                 for (int q = tid; q < NPT; q += blockDim.x) db[q] = Bm[e * NPT + q];
@@ -188,18 +235,36 @@ __global__ void __launch_bounds__(ax_threads<N>())
 #pragma unroll
             for (int k = 0; k < N1; ++k) {
                 T ur = T(0), us = T(0), ut = T(0);
+                if constexpr (kLineLoads) {
+                    T line[N1];  // the r-line (., j, k): vector loads; D_kl from the constant bank
+                    smem_line<T, N1>(su + N1 * (j + N1 * k), line);
 #pragma unroll
-                for (int l = 0; l < N1; ++l) {
-                    ur = fma(rDi[l], su[l + N1 * (j + N1 * k)], ur);
-                    us = fma(rDj[l], su[i + N1 * (l + N1 * k)], us);
-                    ut = fma(sD[k * N1 + l], ru[l], ut);
+                    for (int l = 0; l < N1; ++l) {
+                        ur = fma(rDi[l], line[l], ur);
+                        us = fma(rDj[l], su[i + N1 * (l + N1 * k)], us);
+                        ut = fma((T)Dm.d[k * N1 + l], ru[l], ut);
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < N1; ++l) {
+                        ur = fma(rDi[l], su[l + N1 * (j + N1 * k)], ur);
+                        us = fma(rDj[l], su[i + N1 * (l + N1 * k)], us);
+                        ut = fma(sD[k * N1 + l], ru[l], ut);
+                    }
                 }
                 const int p = i + N1 * (j + N1 * k);
-                const T g0 = sg[p], g1 = sg[NPT + p], g2 = sg[2 * NPT + p];
-                const T g3 = sg[3 * NPT + p], g4 = sg[4 * NPT + p], g5 = sg[5 * NPT + p];
-                svr[p] = g0 * ur + g3 * us + g4 * ut;
-                svs[p] = g3 * ur + g1 * us + g5 * ut;
-                rvt[k] = g4 * ur + g5 * us + g2 * ut;
+                if (AFF) {
+                    const T wq = rij * (T)args.rho[k];
+                    svr[p] = (wq * sg[0]) * ur;
+                    svs[p] = (wq * sg[1]) * us;
+                    rvt[k] = (wq * sg[2]) * ut;
+                } else {
+                    const T g0 = sg[p], g1 = sg[NPT + p], g2 = sg[2 * NPT + p];
+                    const T g3 = sg[3 * NPT + p], g4 = sg[4 * NPT + p], g5 = sg[5 * NPT + p];
+                    svr[p] = g0 * ur + g3 * us + g4 * ut;
+                    svs[p] = g3 * ur + g1 * us + g5 * ut;
+                    rvt[k] = g4 * ur + g5 * us + g2 * ut;
+                }
             }
         }
         __syncthreads();
@@ -209,11 +274,22 @@ __global__ void __launch_bounds__(ax_threads<N>())
             for (int k = 0; k < N1; ++k) {
                 // three independent accumulation chains (one per direction)
                 T ar = T(0), as = T(0), at = T(0);
+                if constexpr (kLineLoads) {
+                    T line[N1];
+                    smem_line<T, N1>(svr + N1 * (j + N1 * k), line);
 #pragma unroll
-                for (int l = 0; l < N1; ++l) {
-                    ar = fma(rDti[l], svr[l + N1 * (j + N1 * k)], ar);
-                    as = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], as);
-                    at = fma(sD[l * N1 + k], rvt[l], at);
+                    for (int l = 0; l < N1; ++l) {
+                        ar = fma(rDti[l], line[l], ar);
+                        as = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], as);
+                        at = fma((T)Dm.d[l * N1 + k], rvt[l], at);
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < N1; ++l) {
+                        ar = fma(rDti[l], svr[l + N1 * (j + N1 * k)], ar);
+                        as = fma(rDtj[l], svs[i + N1 * (l + N1 * k)], as);
+                        at = fma(sD[l * N1 + k], rvt[l], at);
+                    }
                 }
                 T acc = (ar + as) + at;
                 const int p = i + N1 * (j + N1 * k);
@@ -280,18 +356,18 @@ __global__ void __launch_bounds__(ax_threads<N>())
 
 // ---------------------------------------------------------------- launch
 
-template <int N, typename T, bool HELM, bool CG, typename DM>
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM>
 static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
                        const DM &Dm, const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st) {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
     constexpr int threads = ax_threads<N>();
-    auto kern = ax_kernel<N, T, HELM, CG, DM>;
+    auto kern = ax_kernel<N, T, HELM, CG, AFF, DM>;
     int dev_max = 0;
     SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, N);
+    const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, AFF, N);
     int nst = tune.nst < 1 ? 1 : (tune.nst > 3 ? 3 : tune.nst);
-    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG>(nst) > dev_max) --nst;
-    const int smem = ax_smem_bytes<N, T, HELM, CG>(nst);
+    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG, AFF>(nst) > dev_max) --nst;
+    const int smem = ax_smem_bytes<N, T, HELM, CG, AFF>(nst);
     if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
     SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
@@ -308,6 +384,7 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
     a.h2 = h2;
     a.guard = guard;
     a.guard_value = gval;
+    for (int q = 0; q < kMaxN1; ++q) a.rho[q] = q <= m->N ? (float)m->rho[q] : 0.f;
     uintptr_t al = reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(m->B);
     if (CG)
         al |= reinterpret_cast<uintptr_t>(cg.r) | reinterpret_cast<uintptr_t>(cg.dinv) |
@@ -320,13 +397,13 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
     return SEM_OK;
 }
 
-template <typename T, bool HELM, bool CG, typename DM>
+template <typename T, bool HELM, bool CG, typename DM, bool AFF = false>
 static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
                        const DM &Dm, const CgFuse<T> &cg, cudaStream_t st, const int *guard = nullptr,
                        int gval = 0) {
     switch (m->N) {
 #define SEM_AX_CASE(n) \
-    case n: return launch_ax_n<n, T, HELM, CG, DM>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st);
+    case n: return launch_ax_n<n, T, HELM, CG, AFF, DM>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st);
         SEM_AX_CASE(1) SEM_AX_CASE(2) SEM_AX_CASE(3) SEM_AX_CASE(4) SEM_AX_CASE(5)
         SEM_AX_CASE(6) SEM_AX_CASE(7) SEM_AX_CASE(8) SEM_AX_CASE(9) SEM_AX_CASE(10) SEM_AX_CASE(11)
 #undef SEM_AX_CASE
@@ -345,6 +422,8 @@ int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, doub
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
     const CgFuse<float> none{};
+    if (m->aff32)
+        return dispatch_ax<float, false, false, DMatF, true>(m, u, w, m->aff32, 1.0, 0.0, m->Df, none, st);
     return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st);
 }
 
@@ -356,6 +435,8 @@ int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, dou
 
 int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st) {
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
+    if (m->aff32)
+        return dispatch_ax<float, false, true, DMatF, true>(m, nullptr, w, m->aff32, 1.0, 0.0, m->Df, cg, st);
     return dispatch_ax<float, false, true>(m, nullptr, w, m->G32, 1.0, 0.0, m->Df, cg, st);
 }
 
@@ -406,7 +487,13 @@ static int time_operator(const sem_mesh *m, const T *G, const DM &Dm, T *bufs, P
     const int64_t n = m->nloc;
     T *u = bufs, *w = bufs + n, *dinv = bufs + 2 * n, *pp = bufs + 3 * n;
     CgFuse<T> cg{u, dinv, pp, scal, partial};
-    auto once = [&]() { return dispatch_ax<T, false, CG>(m, u, w, G, 1.0, 0.0, Dm, cg, st); };
+    // the same dispatch as the solvers (FP32: the affine form on affine meshes)
+    auto once = [&]() {
+        if (sizeof(T) == 4)
+            return CG ? ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg), reinterpret_cast<float *>(w), st)
+                      : ax_launch_f32(m, reinterpret_cast<const float *>(u), reinterpret_cast<float *>(w), st);
+        return dispatch_ax<T, false, CG>(m, u, w, G, 1.0, 0.0, Dm, cg, st);
+    };
     for (int q = 0; q < 2; ++q) {
         int s = once();
         if (s != SEM_OK) return s;
@@ -454,7 +541,7 @@ int sem_autotune_operator(const sem_mesh *m, int dtype, int fused_cg, void *scra
     PcgScal *scal = reinterpret_cast<PcgScal *>(p + align_up(sizeof(double) * 4 * m->nloc));
     double *partial = reinterpret_cast<double *>(p + align_up(sizeof(double) * 4 * m->nloc) + align_up(sizeof(PcgScal)));
     const int dt = dtype == SEM_F64 ? 0 : 1, cg = fused_cg ? 1 : 0, N = m->N;
-    AxTune &slot = g_ax_tune[dt][0][cg][N];
+    AxTune &slot = g_ax_tune[dt][0][cg][dt == 1 && m->aff32 ? 1 : 0][N];
     const AxTune saved = slot;
     const int stages[3] = {1, 2, 3}, caps[4] = {0, 1, 2, 4};
     float best = 1e30f;
@@ -499,7 +586,8 @@ int sem_autotune_reset(void) {
     for (auto &a : g_ax_tune)
         for (auto &b : a)
             for (auto &c : b)
-                for (auto &d : c) d = AxTune{0, 0};
+                for (auto &d : c)
+                    for (auto &f : d) f = AxTune{0, 0};
     return SEM_OK;
 }
 

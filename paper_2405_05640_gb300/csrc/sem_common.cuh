@@ -65,6 +65,7 @@ struct sem_mesh {
     double *G;           // [E][6][npt]
     float *G32;          // [E][6][npt] FP32 geometric factors, or nullptr
     float2 *G2;          // [E][6][npt] FP32-pair (hi, lo) geometric factors, or nullptr
+    float *aff32;        // [E][4] affine elements: (a, b, c, 0), G_rr = rho_i rho_j rho_k a, ... or nullptr
     double *B;           // [E][npt]
     double *mult;        // [nloc]
     double *minv;        // [nloc] 1/mult
@@ -182,12 +183,12 @@ constexpr int kAxMaxGrid = 152 * 32;  // upper bound of the operator grid (parti
 int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, const int *guard = nullptr,
               int gval = 0);
 
-// Operator launch shape (see sem_ax.cu); g_ax_tune[dtype][helm][cg][N].
+// Operator launch shape (see sem_ax.cu); g_ax_tune[dtype][helm][cg][affine][N].
 struct AxTune {
     int nst;         // pipeline stages, 0 = default (2)
     int per_sm_cap;  // resident CTAs per SM cap, 0 = occupancy limit
 };
-extern AxTune g_ax_tune[2][2][2][kMaxN1];
+extern AxTune g_ax_tune[2][2][2][2][kMaxN1];
 int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);
 
 // Box topology for the arithmetic (index-free) gather-scatter of the CG loop:

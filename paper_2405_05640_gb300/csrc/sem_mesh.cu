@@ -226,13 +226,15 @@ static int validate(const sem_mesh_desc *d) {
     int64_t E = (int64_t)d->nel[0] * d->nel[1] * d->nel[2];
     int64_t nloc = E * (d->N + 1) * (d->N + 1) * (d->N + 1);
     if (nloc >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "E*(N+1)^3 must be < 2^31");
-    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX | SEM_GEOM_PAIR))
+    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX | SEM_GEOM_PAIR | SEM_GEOM_AFFINE))
         return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
+    if ((d->geom_flags & SEM_GEOM_AFFINE) && !(d->geom_flags & SEM_GEOM_F32))
+        return fail(SEM_ERR_INVALID_ARG, "SEM_GEOM_AFFINE needs SEM_GEOM_F32");
     return SEM_OK;
 }
 
 struct Layout {
-    size_t verts, G, G32, G2, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
+    size_t verts, G, G32, G2, aff, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -247,6 +249,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.G = take(sizeof(double) * E * 6 * npt);
     L.G32 = f32 ? take(sizeof(float) * E * 6 * npt) : 0;
     L.G2 = (d->geom_flags & SEM_GEOM_PAIR) ? take(sizeof(float2) * E * 6 * npt) : 0;
+    L.aff = (d->geom_flags & SEM_GEOM_AFFINE) ? take(sizeof(float) * 4 * E) : 0;
     L.B = take(sizeof(double) * nloc);
     L.mult = take(sizeof(double) * nloc);
     L.minv = take(sizeof(double) * nloc);
@@ -498,6 +501,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->G = reinterpret_cast<double *>(base + L.G);
     m->G32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.G32) : nullptr;
     m->G2 = (d->geom_flags & SEM_GEOM_PAIR) ? reinterpret_cast<float2 *>(base + L.G2) : nullptr;
+    m->aff32 = (d->geom_flags & SEM_GEOM_AFFINE) ? reinterpret_cast<float *>(base + L.aff) : nullptr;
     m->B = reinterpret_cast<double *>(base + L.B);
     m->mult = reinterpret_cast<double *>(base + L.mult);
     m->minv = reinterpret_cast<double *>(base + L.minv);
@@ -528,6 +532,34 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
         if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #call)); \
     } while (0)
     CK(cudaMemcpyAsync(m->verts, d->vertices, sizeof(double) * m->E * 24, cudaMemcpyHostToDevice, s));
+    std::vector<float> aff;
+    if (m->aff32) {
+        // axis-aligned boxes: vertex v = V0 + (vx hx, vy hy, vz hz); then J =
+        // diag(h)/2, det J = hx hy hz / 8 and G_rr = rho_i rho_j rho_k hy hz / (2 hx),
+        // G_ss = ... hx hz / (2 hy), G_tt = ... hx hy / (2 hz), cross terms 0
+        aff.resize(4 * m->E);
+        for (int64_t e = 0; e < m->E; ++e) {
+            const double *V = d->vertices + e * 24;
+            const double h[3] = {V[1 * 3 + 0] - V[0], V[2 * 3 + 1] - V[1], V[4 * 3 + 2] - V[2]};
+            const double tol = 1e-12 * (std::fabs(h[0]) + std::fabs(h[1]) + std::fabs(h[2]));
+            bool ok = h[0] > 0 && h[1] > 0 && h[2] > 0;
+            for (int v = 0; v < 8 && ok; ++v) {
+                const int b[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+                for (int a = 0; a < 3; ++a)
+                    if (std::fabs(V[v * 3 + a] - (V[a] + b[a] * h[a])) > tol) ok = false;
+            }
+            if (!ok) {
+                delete m;
+                return fail(SEM_ERR_MESH, "SEM_GEOM_AFFINE: element " + std::to_string(e) +
+                                              " is not an axis-aligned box");
+            }
+            aff[4 * e + 0] = (float)(h[1] * h[2] / (2.0 * h[0]));
+            aff[4 * e + 1] = (float)(h[0] * h[2] / (2.0 * h[1]));
+            aff[4 * e + 2] = (float)(h[0] * h[1] / (2.0 * h[2]));
+            aff[4 * e + 3] = 0.f;
+        }
+        CK(cudaMemcpyAsync(m->aff32, aff.data(), sizeof(float) * aff.size(), cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemcpyAsync(m->gs_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int) * 8, s));
     GllConst g{};
