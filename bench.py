@@ -244,6 +244,49 @@ def _solve_series(gm, b, scratch, steps, opts, profile=True):
                 last=stats)
 
 
+def perf_model_block(case, gm, scratch, ms_per_step, iters, cpu_gdofs, om):
+    """The paper's performance model (section 4.1) applied to this GPU and
+    its host: cost = element-iterations of one solve; P_opt(GPU) from the
+    timed chosen solves, P_opt(CPU) from the oracle's single-core rate times
+    the host's cores (linear scaling: as optimistic as the model); capacities
+    = device memory / bytes per element of each side."""
+    import numpy as np
+    import torch
+
+    from paper_2405_05640_gb300 import binding
+    E = case.E
+    C = E * iters
+    P_gpu = C / (ms_per_step / 1e3)
+    cores = os.cpu_count() or 1
+    P_cpu = cpu_gdofs * 1e9 / case.N ** 3 * cores
+    _, total = torch.cuda.mem_get_info()
+    # the chosen solver's footprint: mesh workspace without the FP32-pair
+    # factors this benchmark adds for its FP64-pair line (48 B per point), plus
+    # the solver scratch
+    gpu_bpe = (gm.info.workspace_bytes - 48 * case.nloc + scratch.numel()) / E
+    cpu_bpe = sum(v.nbytes for v in vars(om).values() if isinstance(v, np.ndarray)) / E
+    host = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    emax_gpu, emax_cpu = 0.95 * total / gpu_bpe, 0.8 * host / cpu_bpe
+    T, split = binding.perf_model([P_gpu, P_cpu], C, [emax_gpu * iters, emax_cpu * iters])
+    out = {"unit": "element-iterations/s", "P_opt_gpu": round(P_gpu, 1), "P_opt_cpu": round(P_cpu, 1),
+           "host_cores": cores, "cost": C, "T_gpu_alone_ms": round(ms_per_step, 3),
+           "T_min_gpu_plus_cpu_ms": round(T * 1e3, 3), "predicted_gain": round(ms_per_step / (T * 1e3) - 1.0, 5),
+           "elements_gpu_cpu": [round(split[0] / iters, 1), round(split[1] / iters, 1)],
+           "capacity_elements_gpu_cpu": [int(emax_gpu), int(emax_cpu)],
+           "bytes_per_element_gpu_cpu": [int(gpu_bpe), int(cpu_bpe)]}
+    # the capacity-bound regime: a problem larger than the GPU holds (half as
+    # much again, within what GPU + host hold together), same iterations
+    Eb = emax_gpu + 0.5 * min(emax_gpu, emax_cpu)
+    if Eb <= emax_gpu + emax_cpu:
+        Tb, sb = binding.perf_model([P_gpu, P_cpu], Eb * iters, [emax_gpu * iters, emax_cpu * iters])
+        Tc = Eb * iters / P_cpu if Eb <= emax_cpu else float("inf")
+        out["capacity_case"] = {"elements": int(Eb), "T_min_ms": round(Tb * 1e3, 1),
+                                "cpu_alone_ms": round(Tc * 1e3, 1) if Tc != float("inf") else None,
+                                "elements_gpu_cpu": [round(sb[0] / iters, 1), round(sb[1] / iters, 1)],
+                                "gpu_alone": "does not fit"}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -293,6 +336,16 @@ def run_ours(args):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1) / args.plain_steps
+
+    # the FP64 solver on the FP32-pair operator (FP64-accurate, FP32 pipes)
+    pair_opts = dict(base, precision=2)
+    gm.pcg(b, scratch=scratch, **pair_opts)
+    torch.cuda.synchronize()
+    p0.record(stream)
+    qser = _solve_series(gm, b, scratch, args.plain_steps, pair_opts)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    pair_solve_ms = p0.elapsed_time(p1) / args.plain_steps
 
     # end to end through the host-buffer entry point (chosen solver)
     e2e = None
@@ -385,6 +438,10 @@ def run_ours(args):
                 "chosen_inner_iters": ser["iters"] / args.steps,
                 "chosen_outer_iters": st["outer_iters"] if st else None,
                 "plain_iters": pser["iters"] / args.plain_steps,
+                "fp64_pair_time_to_1e-8_ms": round(pair_solve_ms, 3),
+                "fp64_pair_iters": qser["iters"] / args.plain_steps,
+                "fp64_pair_rel_res": qser["last"]["rel_res"] if qser["last"] else None,
+                "fp64_pair_speedup_vs_plain_fp64": round(plain_ms / pair_solve_ms, 3),
                 "chosen_rel_res_fp64": st["rel_res"] if st else None,
                 "status": st["status"] if st else None,
                 "outer_fp64_operator_ms": round(ser["outer_ms"] / max(ser["outer_n"], 1), 4)},
@@ -397,8 +454,9 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        g, dt, desc, _, _ = cpu_oracle_sample(case, args.cpu_iters, V)
+        g, dt, desc, om, _ = cpu_oracle_sample(case, args.cpu_iters, V)
         rec["cpu_baseline"] = {"value": round(g, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        rec["perf_model"] = perf_model_block(case, gm, scratch, ms_per_step, ser["iters"] / args.steps, g, om)
     if rank == 0:
         print(json.dumps(rec), flush=True)
 

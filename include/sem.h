@@ -203,9 +203,14 @@ int sem_glsc3_noalloc(const sem_mesh *mesh, const double *a, const double *b, do
  *   (FP32 operator and vectors, FP32 accumulation): every time the FP32
  *   residual has fallen by inner_tol, the FP32 increment is added to the FP64
  *   solution and the FP64 residual b - A x is recomputed; the outer dot
- *   products and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh. */
+ *   products and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh.
+ * precision = SEM_PCG_F64_PAIR: the FP64 solver (FP64 vectors, dot products
+ *   and updates) with the operator evaluated in FP32-pair arithmetic (as
+ *   sem_ax SEM_F64_PAIR; error ~2^-42 of the line-wise magnitudes).  Poisson
+ *   only (h1 = 1, h2 = 0); requires SEM_GEOM_PAIR in the mesh. */
 #define SEM_PCG_F64 0
 #define SEM_PCG_MIXED 1
+#define SEM_PCG_F64_PAIR 2
 typedef struct {
     double tol;            /* stopping tolerance */
     int tol_is_relative;   /* 1: relative to ||b||, 0: absolute */

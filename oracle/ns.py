@@ -21,19 +21,86 @@ dealiasing, on a fully periodic box:
 
 Derivatives along the reference directions are the contractions with D
 written out with numpy.einsum; the inverse Jacobian comes from the C oracle.
+
+Higher order and dealiasing (the splitting the paper cites is the high-order
+one of Karniadakis, Israeli & Orszag 1991: BDF_k / EXT_k up to k = 3):
+  BDF3: b0 = 11/6, b = (3, -3/2, 1/3);  EXT3: a = (3, -3, 1),
+ramping k = 1, 2, 3 over the first steps.  Dealiased advection (over-
+integration on M = 3(N+1)/2 Gauss-Legendre points per direction, the usual
+3/2 rule for SEM): the weak form
+  W_c[i] = int phi_i (u . grad) u_c dx
+         = sum_q w_q (sum_a [sum_m detJ dr_a/dx_m u_m] d u_c / d r_a) phi_i  at the Gauss points,
+with u and d u_c / d r_a interpolated from the GLL points and detJ dr_a/dx_m
+= cofactor C[m][a] of the trilinear Jacobian evaluated at the Gauss points;
+the advection term is then NL_c = -(Q Q^T W_c) / (Q Q^T B).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import Mesh, inverse_jacobian
+from . import Mesh, gll, inverse_jacobian
 
-BDF = {1: (1.0, (1.0,)), 2: (1.5, (2.0, -0.5))}
-EXT = {1: (1.0,), 2: (2.0, -1.0)}
+BDF = {1: (1.0, (1.0,)), 2: (1.5, (2.0, -0.5)), 3: (11.0 / 6.0, (3.0, -1.5, 1.0 / 3.0))}
+EXT = {1: (1.0,), 2: (2.0, -1.0), 3: (3.0, -3.0, 1.0)}
+
+
+def dealias_points(N: int) -> int:
+    """M = 3(N+1)/2 Gauss points per direction (rounded up)."""
+    return (3 * (N + 1) + 1) // 2
+
+
+def lagrange_matrix(xi: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """J[q, i] = l_i(z_q), the Lagrange basis on the nodes xi at the points z
+    (product formula)."""
+    J = np.ones((len(z), len(xi)))
+    for i in range(len(xi)):
+        for j in range(len(xi)):
+            if j != i:
+                J[:, i] *= (z - xi[j]) / (xi[i] - xi[j])
+    return J
+
+
+def fine_metric(verts: np.ndarray, z: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """W[e, m, a, q] = w_q detJ dr_a/dx_m at the tensor points q = (qi, qj, qk)
+    (qi fastest) of the 1-D points z with weights w: for the trilinear map
+    x(r,s,t) = sum_v V_v prod (1 +- r)/2, detJ dr_a/dx_m is the cofactor
+    C[m][a] of J_ab = dx_a/dr_b (computed from vertex offsets)."""
+    verts = np.asarray(verts, dtype=np.float64).reshape(-1, 8, 3)
+    M = len(z)
+    r = z[None, None, :]
+    s = z[None, :, None]
+    t = z[:, None, None]
+    lo = lambda x: 0.5 * (1.0 - x)
+    hi = lambda x: 0.5 * (1.0 + x)
+    f = [(lo, -0.5), (hi, 0.5)]
+    J = np.zeros((verts.shape[0], 3, 3, M, M, M))
+    for v in range(1, 8):
+        bx, by, bz = v & 1, (v >> 1) & 1, (v >> 2) & 1
+        gr = f[bx][1] * f[by][0](s) * f[bz][0](t) * np.ones_like(r)
+        gs = f[bx][0](r) * f[by][1] * f[bz][0](t) * np.ones_like(s)
+        gt = f[bx][0](r) * f[by][0](s) * f[bz][1] * np.ones_like(t)
+        X = verts[:, v, :] - verts[:, 0, :]
+        for a in range(3):
+            J[:, a, 0] += X[:, a, None, None, None] * gr
+            J[:, a, 1] += X[:, a, None, None, None] * gs
+            J[:, a, 2] += X[:, a, None, None, None] * gt
+    C = np.zeros_like(J)
+    for a in range(3):
+        for b in range(3):
+            a1, a2 = (a + 1) % 3, (a + 2) % 3
+            b1, b2 = (b + 1) % 3, (b + 2) % 3
+            C[:, a, b] = J[:, a1, b1] * J[:, a2, b2] - J[:, a1, b2] * J[:, a2, b1]
+    wq = (w[:, None, None] * w[None, :, None] * w[None, None, :])  # [qk, qj, qi]
+    Wm = np.zeros((verts.shape[0], 3, 3, M ** 3))
+    for m in range(3):
+        for a in range(3):
+            Wm[:, m, a] = (wq * C[:, m, a]).reshape(verts.shape[0], -1)
+    return Wm
 
 
 class NSOracle:
-    def __init__(self, N, nel, verts, Re, periodic=(1, 1, 1)):
+    def __init__(self, N, nel, verts, Re, periodic=(1, 1, 1), order=2, dealias=False, M=None):
+        self.order, self.dealias = order, dealias
         self.m = Mesh(N, nel, periodic, 0, verts)
         self.N, self.E, self.n1 = N, self.m.E, N + 1
         self.nu = 1.0 / Re
@@ -44,6 +111,10 @@ class NSOracle:
         self.nl_hist = []  # previous advection terms, most recent first
         self.p = np.zeros(self.m.nloc)
         self.steps = 0
+        self.verts = np.asarray(verts, dtype=np.float64).reshape(-1, 8, 3)
+        self.M = M if M is not None else dealias_points(N)
+        if dealias:
+            self.binv = 1.0 / self.m.dssum(self.m.B.reshape(-1))
 
     # ---- operators
     def _cube(self, f):
@@ -69,6 +140,37 @@ class NSOracle:
             g = self.grad(u[c])
             out.append(-(u[0] * g[0] + u[1] * g[1] + u[2] * g[2]))
         return out
+
+    def advect_weak(self, u, M=None):
+        """W_c = int phi_i (u . grad) u_c by Gauss quadrature with M points per
+        direction (local, not assembled)."""
+        M = self.M if M is None else M
+        N1, E = self.n1, self.E
+        z, w = np.polynomial.legendre.leggauss(M)
+        xi = gll(self.N)[0]
+        J = lagrange_matrix(xi, z)
+        JD = J @ self.m.D
+        Wm = fine_metric(self.verts, z, w)
+
+        def interp(f, Ji, Jj, Jk):
+            F = np.reshape(f, (E, N1, N1, N1))
+            return np.einsum("qi,rj,sk,ekji->esrq", Ji, Jj, Jk, F).reshape(E, -1)
+
+        uf = [interp(u[m], J, J, J) for m in range(3)]
+        ct = [sum(Wm[:, m, a] * uf[m] for m in range(3)) for a in range(3)]
+        out = []
+        for c in range(3):
+            dr = interp(u[c], JD, J, J)
+            ds = interp(u[c], J, JD, J)
+            dt = interp(u[c], J, J, JD)
+            fq = (ct[0] * dr + ct[1] * ds + ct[2] * dt).reshape(E, M, M, M)
+            out.append(np.einsum("qi,rj,sk,esrq->ekji", J, J, J, fq).reshape(-1))
+        return out
+
+    def advect_dealiased(self, u):
+        """NL_c = -(Q Q^T W_c) / (Q Q^T B)."""
+        W = self.advect_weak(u)
+        return [-self.binv * self.m.dssum(Wc) for Wc in W]
 
     def wdiv(self, F):
         """Local weak divergence: int grad(phi_i) . F by GLL quadrature,
@@ -103,10 +205,10 @@ class NSOracle:
         return p - self.unique_mean(p), it, st
 
     def step(self, dt, p_tol=1e-12, v_tol=1e-12):
-        k = min(self.steps + 1, 2)
+        k = min(self.steps + 1, self.order)
         b0, bj = BDF[k]
         aj = EXT[k]
-        nl = self.advect(self.u)
+        nl = self.advect_dealiased(self.u) if self.dealias else self.advect(self.u)
         us = [self.u] + self.u_hist
         nls = [nl] + self.nl_hist
         F = []
@@ -124,8 +226,9 @@ class NSOracle:
             unew.append(uc)
             vits.append(it)
         self.m.set_helmholtz(1.0, 0.0)
-        self.u_hist = [self.u] + self.u_hist[:0]
-        self.nl_hist = [nl] + self.nl_hist[:0]
+        keep = self.order - 1
+        self.u_hist = ([self.u] + self.u_hist)[:keep]
+        self.nl_hist = ([nl] + self.nl_hist)[:keep]
         self.u = unew
         self.steps += 1
         return {"p_iters": pit, "p_status": pst, "v_iters": vits, "p_rhs": bp}

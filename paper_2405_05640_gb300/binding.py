@@ -28,7 +28,7 @@ SEM_GEOM_F32 = 1
 SEM_GEOM_RX = 2
 SEM_GEOM_PAIR = 4
 SEM_GEOM_AFFINE = 8
-SEM_PCG_F64, SEM_PCG_MIXED = 0, 1
+SEM_PCG_F64, SEM_PCG_MIXED, SEM_PCG_F64_PAIR = 0, 1, 2
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
 

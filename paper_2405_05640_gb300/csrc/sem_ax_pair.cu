@@ -67,7 +67,8 @@ struct PairShape {
     static constexpr int PB = S * NL;                       // pairs in one padded field
     static constexpr int UPT = (NPT + T - 1) / T;           // u values per thread (prefetched)
     static constexpr int SB = NPT * 48;                     // one stage: the G pair slab
-    static constexpr int smem(int nst) { return nst * SB + 4 * PB * 8 + 64 + 16 * 4; }
+    // stages, 4 pair fields, 8 mbarriers, 16 ints and 16 doubles of reductions
+    static constexpr int smem(int nst) { return nst * SB + 4 * PB * 8 + 64 + 16 * 4 + 16 * 8; }
 };
 
 // ---------------------------------------------------------------- pair arithmetic
@@ -212,10 +213,12 @@ __device__ __forceinline__ void fwd_line(const float2 *src, float2 *dst, int bas
 }
 
 // Backward contraction of one line; mode 0: write into acc, 1: add into acc,
-// 2: add acc and store the FP64 result (scaled back by sc) to global.
+// 2: add acc and store the FP64 result (scaled back by sc) to global; with pe
+// (fused CG form) also pw += pe * w at the stored points.
 template <int N, int H, int MODE>
 __device__ __forceinline__ void bwd_line(const float2 *src, float2 *acc, int base, int step, const PairD<N + 1> &D,
-                                         double *__restrict__ we, int gbase, int gstep, int sc, bool nan) {
+                                         double *__restrict__ we, int gbase, int gstep, int sc, bool nan,
+                                         const double *pe = nullptr, double *pw = nullptr) {
     using P = PairShape<N>;
     constexpr int N1 = P::N1, I0 = H ? P::H0 : 0, I1 = H ? N1 : P::H0;
     float2 x[N1], y[I1 - I0];
@@ -231,15 +234,20 @@ __device__ __forceinline__ void bwd_line(const float2 *src, float2 *acc, int bas
             acc[q] = pair_add(acc[q], y[i - I0]);
         } else {
             const float2 v = pair_add(acc[q], y[i - I0]);
-            we[gbase + i * gstep] = nan ? __longlong_as_double(0x7ff8000000000000ll) : pair_to_f64(v, sc);
+            const double wv = nan ? __longlong_as_double(0x7ff8000000000000ll) : pair_to_f64(v, sc);
+            we[gbase + i * gstep] = wv;
+            if (pe) *pw = fma(pe[gbase + i * gstep], wv, *pw);
         }
     }
 }
 
-template <int N>
+// CG: the fused CG form of the FP64 solver: p <- dinv r + beta p (FP64,
+// written back), w = A_L p, and sum_l p_l w_l reduced over the grid into
+// alpha = rho / pw (per-CTA partials; the last CTA sums them in a fixed order).
+template <int N, bool CG>
 __global__ void __launch_bounds__(PairShape<N>::T)
     ax_pair_kernel(const double *__restrict__ u, double *__restrict__ w, const float2 *__restrict__ G2,
-                   const PairD<N + 1> D, const PairArgs a, int *__restrict__ err) {
+                   const PairD<N + 1> D, const PairArgs a, const CgFuse<double> cg, int *__restrict__ err) {
     using P = PairShape<N>;
     constexpr int N1 = P::N1, NPT = P::NPT, NL = P::NL, LP = P::LP, T = P::T, PB = P::PB;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -248,6 +256,8 @@ __global__ void __launch_bounds__(PairShape<N>::T)
     float2 *R = U + PB, *Sb = R + PB, *Tb = Sb + PB;             // u_r, u_s, u_t, later v_*
     uint64_t *bar = reinterpret_cast<uint64_t *>(Tb + PB);
     int *red = reinterpret_cast<int *>(bar + 8);
+    double *dred = reinterpret_cast<double *>(red + 16);
+    if (CG && cg.scal->done) return;  // uniform: the solve has converged
     const int tid = threadIdx.x;
     const int half = tid / LP, L = tid % LP;  // warp-uniform half
     const bool lact = L < NL;
@@ -269,13 +279,25 @@ __global__ void __launch_bounds__(PairShape<N>::T)
             const int64_t e = blockIdx.x + s * stride;
             if (e < E) issue(e, s);
         }
-    // u of the element being processed, prefetched into registers one element ahead
-    double ur[P::UPT];
+    // the operand of the element being processed (u; CG: r, dinv and the old
+    // p), prefetched into registers one element ahead.  In the CG form p of a
+    // later element is still the old one when prefetched: this CTA writes it
+    // only when it reaches that element.
+    double ur[P::UPT], rr[CG ? P::UPT : 1], dr[CG ? P::UPT : 1];
+    const double beta = CG ? cg.scal->beta : 0.0;
+    double pw_acc = 0.0;
     auto load_u = [&](int64_t e) {
 #pragma unroll
         for (int q = 0; q < P::UPT; ++q) {
             const int idx = tid + q * T;
-            ur[q] = (e < E && idx < NPT) ? __ldg(u + e * NPT + idx) : 0.0;
+            const bool in = e < E && idx < NPT;
+            if (CG) {
+                ur[q] = in ? cg.p[e * NPT + idx] : 0.0;
+                rr[q] = in ? __ldg(cg.r + e * NPT + idx) : 0.0;
+                dr[q] = in ? __ldg(cg.dinv + e * NPT + idx) : 0.0;
+            } else {
+                ur[q] = in ? __ldg(u + e * NPT + idx) : 0.0;
+            }
         }
     };
     load_u(blockIdx.x);
@@ -294,6 +316,15 @@ __global__ void __launch_bounds__(PairShape<N>::T)
             float2 *dg = reinterpret_cast<float2 *>(smem + s * P::SB);
             for (int q = tid; q < 6 * NPT; q += T) dg[q] = G2[e * 6 * NPT + q];
             __syncthreads();
+        }
+        if (CG) {
+            // p <- dinv r + beta p, the new search direction (FP64)
+#pragma unroll
+            for (int q = 0; q < P::UPT; ++q) {
+                const int idx = tid + q * T;
+                ur[q] = fma(beta, ur[q], dr[q] * rr[q]);
+                if (idx < NPT) cg.p[e * NPT + idx] = ur[q];
+            }
         }
         // element exponent: the largest biased FP64 exponent of u
         int exm = 0;
@@ -370,10 +401,11 @@ __global__ void __launch_bounds__(PairShape<N>::T)
             int base, step;
             line_at<N>(2, L, base, step);
             const int gbase = L, gstep = NL;  // (i, j, k): i + N1 j + N1^2 k, L = i + N1 j
+            const double *pe = CG ? cg.p + e * NPT : nullptr;  // written above, visible after the barriers
             if (half == 0)
-                bwd_line<N, 0, 2>(Tb, U, base, step, D, we, gbase, gstep, sc, nan);
+                bwd_line<N, 0, 2>(Tb, U, base, step, D, we, gbase, gstep, sc, nan, pe, &pw_acc);
             else
-                bwd_line<N, 1, 2>(Tb, U, base, step, D, we, gbase, gstep, sc, nan);
+                bwd_line<N, 1, 2>(Tb, U, base, step, D, we, gbase, gstep, sc, nan, pe, &pw_acc);
         }
         // the barrier at the top of the next element protects U, R, Sb, Tb
     }
@@ -385,14 +417,49 @@ __global__ void __launch_bounds__(PairShape<N>::T)
             if (en < E) mbar_wait_bounded(&bar[s], (itn / nst) & 1, err, kDevTimeoutTma);
         }
     }
+    if (CG) {
+        // grid reduction of p.w: per-CTA partials, the last CTA sums them with
+        // all its threads in a fixed order
+        __shared__ int s_last;
+        double v = pw_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) dred[wid] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < T / 32; ++q) t += dred[q];
+            cg.partial[blockIdx.x] = t;
+            __threadfence();
+            s_last = atomicAdd(&cg.scal->cnt[3], 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double t = 0.0;
+            for (int q = tid; q < (int)gridDim.x; q += T) t += __ldcg(cg.partial + q);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) dred[wid] = t;  // thread 0 read dred before the barrier above
+            __syncthreads();
+            if (tid == 0) {
+                double pw = 0.0;
+                for (int q = 0; q < T / 32; ++q) pw += dred[q];
+                cg.scal->pw = pw;
+                cg.scal->alpha = cg.scal->rho / pw;
+                cg.scal->cnt[3] = 0u;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- launch
 
 AxTune g_ax_pair_tune[kMaxN1] = {};
 
-template <int N>
-static int launch_pair_n(const sem_mesh *m, const double *u, double *w, cudaStream_t st) {
+template <int N, bool CG>
+static int launch_pair_n(const sem_mesh *m, const double *u, double *w, const CgFuse<double> &cg, cudaStream_t st) {
     using P = PairShape<N>;
     constexpr int N1 = P::N1;
     PairD<N1> D;
@@ -421,7 +488,7 @@ static int launch_pair_n(const sem_mesh *m, const double *u, double *w, cudaStre
     while (nst > 1 && P::smem(nst) > dev_max) --nst;
     const int smem = P::smem(nst);
     if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
-    auto kern = ax_pair_kernel<N>;
+    auto kern = ax_pair_kernel<N, CG>;
     SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P::T, smem));
@@ -429,25 +496,36 @@ static int launch_pair_n(const sem_mesh *m, const double *u, double *w, cudaStre
     if (tune.per_sm_cap > 0 && per_sm > tune.per_sm_cap) per_sm = tune.per_sm_cap;
     int64_t grid = (int64_t)m->num_sms * per_sm;
     if (grid > m->E) grid = m->E;
+    if (grid > kAxMaxGrid) grid = kAxMaxGrid;  // partials of the fused CG form
     PairArgs a;
     a.E = m->E;
     a.nst = nst;
     a.use_tma = reinterpret_cast<uintptr_t>(m->G2) % 16 == 0;
-    kern<<<(int)grid, P::T, smem, st>>>(u, w, m->G2, D, a, m->d_err);
+    kern<<<(int)grid, P::T, smem, st>>>(u, w, m->G2, D, a, cg, m->d_err);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
 
-int ax_launch_pair(const sem_mesh *m, const double *u, double *w, cudaStream_t st) {
+template <bool CG>
+static int dispatch_pair(const sem_mesh *m, const double *u, double *w, const CgFuse<double> &cg, cudaStream_t st) {
     if (!m->G2) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_PAIR");
     switch (m->N) {
 #define SEM_PAIR_CASE(n) \
-    case n: return launch_pair_n<n>(m, u, w, st);
+    case n: return launch_pair_n<n, CG>(m, u, w, cg, st);
         SEM_PAIR_CASE(1) SEM_PAIR_CASE(2) SEM_PAIR_CASE(3) SEM_PAIR_CASE(4) SEM_PAIR_CASE(5)
         SEM_PAIR_CASE(6) SEM_PAIR_CASE(7) SEM_PAIR_CASE(8) SEM_PAIR_CASE(9) SEM_PAIR_CASE(10) SEM_PAIR_CASE(11)
 #undef SEM_PAIR_CASE
         default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
     }
+}
+
+int ax_launch_pair(const sem_mesh *m, const double *u, double *w, cudaStream_t st) {
+    const CgFuse<double> none{};
+    return dispatch_pair<false>(m, u, w, none, st);
+}
+
+int ax_cg_launch_pair(const sem_mesh *m, const CgFuse<double> &cg, double *w, cudaStream_t st) {
+    return dispatch_pair<true>(m, nullptr, w, cg, st);
 }
 
 }  // namespace sem

@@ -179,6 +179,8 @@ int ax_launch_pair(const sem_mesh *m, const double *u, double *w, cudaStream_t s
 int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
                      cudaStream_t st);
 int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st);
+// Fused CG form of the FP32-pair FP64 operator (sem_ax_pair.cu).
+int ax_cg_launch_pair(const sem_mesh *m, const CgFuse<double> &cg, double *w, cudaStream_t st);
 constexpr int kAxMaxGrid = 152 * 32;  // upper bound of the operator grid (partials of the fused kernel)
 int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, const int *guard = nullptr,
               int gval = 0);

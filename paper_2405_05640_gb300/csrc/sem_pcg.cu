@@ -12,8 +12,9 @@
 //
 // GB300 design: per iteration three stream-ordered kernels -- the persistent
 // TMA operator kernel fused with the search-direction update p = z + beta p
-// and the <p, A p> reduction (alpha); the gather-scatter; and one fused
-// update kernel (x, r, z, both dot products, beta, convergence flag).  All
+// and the <p, A p> reduction (alpha); the y and z passes of the gather-
+// scatter; and one line-wise update kernel (the x pass of the gather-scatter,
+// the Dirichlet mask, x, r, z, both dot products, beta, convergence flag).  All
 // scalars stay on the device; the host reads a convergence flag every
 // `check_every` iterations, and kernels launched after convergence return at
 // once.  Reductions are two-level (block partials, summed in block order by
@@ -29,7 +30,6 @@ namespace sem {
 
 constexpr int kPThreads = 256;
 constexpr int kPBlocks = 1184;  // 152 SMs x 8 blocks: fixed so the reduction order is fixed
-constexpr int kUBlocks = 608;   // vectorised update (62 registers): 152 SMs x 4 resident blocks, one wave
 
 // Vectors of one CG iteration space in precision T.
 template <typename T>
@@ -190,62 +190,6 @@ __device__ __forceinline__ void update_point(T alpha, T p, T w, T mi, T di, T &x
     } else {
         f0 = fma(r * r, mi, f0);
         f1 = fma(r * (di * r), mi, f1);
-    }
-}
-
-// x += alpha p; r -= alpha w; z = dinv r; rr = <r,r>; rz = <r,z>;
-// last block: beta = rz/rho, rho = rz, iteration count and convergence flag.
-// VEC: every array 16-byte aligned; each thread step takes 16 bytes of every
-// array (4 FP32 / 2 FP64 points), the last n mod (16 / sizeof(T)) points
-// one by one.
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(kPThreads)
-    pcg_update_kernel(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
-                      PcgWork<T> W) {
-    if (W.scal->done) return;
-    const T alpha = (T)W.scal->alpha;
-    double v[2] = {0.0, 0.0};
-    T f0 = T(0), f1 = T(0);
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
-    constexpr int V = V16<T>::n;
-    const int64_t nv = VEC ? n / V : 0;
-    for (int64_t q = tid; q < nv; q += stride) {
-        const int64_t l = q * V;
-        const V16<T> p = ld16(W.p + l), w = ld16(W.w + l), mi = ld16(minv + l), di = ld16(dinv + l);
-        V16<T> xv = ld16(x + l), rv = ld16(W.r + l);
-#pragma unroll
-        for (int c = 0; c < V; ++c) update_point(alpha, p.a[c], w.a[c], mi.a[c], di.a[c], xv.a[c], rv.a[c], v, f0, f1);
-        st16(x + l, xv);
-        st16(W.r + l, rv);
-    }
-    for (int64_t l = nv * V + tid; l < n; l += stride) {
-        T xl = x[l], rl = W.r[l];
-        update_point(alpha, W.p[l], W.w[l], minv[l], dinv[l], xl, rl, v, f0, f1);
-        x[l] = xl;
-        W.r[l] = rl;
-    }
-    if (sizeof(T) == 4) {
-        v[0] = (double)f0;
-        v[1] = (double)f1;
-    }
-    double t[2];
-    if (grid_reduce<2>(v, W.partial + 2 * kPBlocks, &W.scal->cnt[2], t)) {
-        PcgScal *s = W.scal;
-        s->rr = t[0];
-        s->beta = t[1] / s->rho;
-        s->rho_prev = s->rho;
-        s->rho = t[1];
-        s->iter += 1;
-        if (!isfinite(t[0])) {
-            s->done = 1;
-            s->status = SEM_ERR_NAN;
-        } else if (t[0] <= s->tol2) {
-            s->done = 1;
-            s->status = SEM_OK;
-        } else if (s->iter >= s->max_iter) {
-            s->done = 1;
-            s->status = SEM_ERR_NOT_CONVERGED;
-        }
     }
 }
 
@@ -410,16 +354,6 @@ static int launch_update_box(const sem_mesh *m, T *x, const T *dinv, const PcgWo
 #undef SEM_UB_CASE
         default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
     }
-}
-
-template <typename T>
-static int launch_update(T *x, const T *dinv, const T *minv, int64_t n, const PcgWork<T> &W, cudaStream_t st) {
-    if (al16(x) && al16(dinv) && al16(minv) && al16(W.p) && al16(W.w) && al16(W.r))
-        pcg_update_kernel<T, true><<<kUBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
-    else
-        pcg_update_kernel<T, false><<<kPBlocks, kPThreads, 0, st>>>(x, dinv, minv, n, W);
-    SEM_CUDA_CHECK(cudaGetLastError());
-    return SEM_OK;
 }
 
 // ---- FP64 outer loop of the mixed solver ----
@@ -596,10 +530,12 @@ struct SolveCtx {
 // Assembled operator y = M Q Q^T (h1 A_L + h2 B) x in precision T, timed.
 template <typename T>
 static int apply_assembled_timed(const sem_mesh *m, const T *x, T *y, double h1, double h2, cudaStream_t st,
-                                 SolveCtx &c) {
+                                 SolveCtx &c, bool pair = false) {
     c.tax.start(st);
     int s;
-    if (sizeof(T) == 8)
+    if (sizeof(T) == 8 && pair)
+        s = ax_launch_pair(m, reinterpret_cast<const double *>(x), reinterpret_cast<double *>(y), st);
+    else if (sizeof(T) == 8)
         s = ax_launch_f64(m, reinterpret_cast<const double *>(x), reinterpret_cast<double *>(y), h1, h2, st);
     else
         s = ax_launch_f32(m, reinterpret_cast<const float *>(x), reinterpret_cast<float *>(y), st);
@@ -613,19 +549,13 @@ static int apply_assembled_timed(const sem_mesh *m, const T *x, T *y, double h1,
     return s;
 }
 
-template <typename T>
-static const T *minv_of(const sem_mesh *m);
-template <>
-const double *minv_of<double>(const sem_mesh *m) { return m->minv; }
-template <>
-const float *minv_of<float>(const sem_mesh *m) { return m->minv32; }
 
 // CG iterations after an init kernel: three kernels per iteration (fused
 // operator, gather-scatter, fused update), with a host check every `check`
 // iterations.  Leaves the final scalars in *h.
 template <typename T>
 static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max_iter, int check, double h1,
-                   double h2, cudaStream_t st, SolveCtx &c, PcgScal *h) {
+                   double h2, cudaStream_t st, SolveCtx &c, PcgScal *h, bool pair = false) {
     CgFuse<T> cg{W.r, dinv, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
     while (true) {
@@ -637,11 +567,13 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
         for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
             // p <- dinv r + beta p; w = A_L p; alpha = rho / <p, w>   (one kernel)
             c.tax.start(st);
-            int s = (sizeof(T) == 8)
-                        ? ax_cg_launch_f64(m, reinterpret_cast<const CgFuse<double> &>(cg),
-                                           reinterpret_cast<double *>(W.w), h1, h2, st)
-                        : ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg),
-                                           reinterpret_cast<float *>(W.w), st);
+            int s = (sizeof(T) == 4)
+                        ? ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg),
+                                           reinterpret_cast<float *>(W.w), st)
+                        : pair ? ax_cg_launch_pair(m, reinterpret_cast<const CgFuse<double> &>(cg),
+                                                   reinterpret_cast<double *>(W.w), st)
+                               : ax_cg_launch_f64(m, reinterpret_cast<const CgFuse<double> &>(cg),
+                                                  reinterpret_cast<double *>(W.w), h1, h2, st);
             c.tax.stop(st);
             if (s != SEM_OK) return s;
             // w <- M Q Q^T w, axis by axis: the y and z passes here, the x
@@ -682,9 +614,10 @@ static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_
     if (s0 == SEM_OK) s0 = c.tgs.init(o->profile != 0, check + 1);
     if (s0 != SEM_OK) return s0;
     SEM_CUDA_CHECK(cudaMemsetAsync(W.scal, 0, sizeof(PcgScal), st));
+    const bool pair = o->precision == SEM_PCG_F64_PAIR;
     const double *ax0 = nullptr;
     if (o->use_initial_guess) {
-        int s = apply_assembled_timed<double>(m, x, W.w, o->h1, o->h2, st, c);
+        int s = apply_assembled_timed<double>(m, x, W.w, o->h1, o->h2, st, c, pair);
         if (s != SEM_OK) return s;
         ax0 = W.w;
     } else {
@@ -696,7 +629,7 @@ static int pcg_f64(const sem_mesh *m, const double *b, double *x, const sem_pcg_
     SEM_CUDA_CHECK(cudaGetLastError());
     c.launches += 1;
     PcgScal h{};
-    int s = cg_loop<double>(m, W, x, dinv, o->max_iter, check, o->h1, o->h2, st, c, &h);
+    int s = cg_loop<double>(m, W, x, dinv, o->max_iter, check, o->h1, o->h2, st, c, &h, pair);
     if (s != SEM_OK) return s;
     stats->iters = h.iter;
     stats->outer_iters = 0;
@@ -796,8 +729,12 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
 }
 
 static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
-    if (o->precision != SEM_PCG_F64 && o->precision != SEM_PCG_MIXED)
+    if (o->precision != SEM_PCG_F64 && o->precision != SEM_PCG_MIXED && o->precision != SEM_PCG_F64_PAIR)
         return fail(SEM_ERR_UNSUPPORTED, "unknown precision mode");
+    if (o->precision == SEM_PCG_F64_PAIR && !m->G2)
+        return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_F64_PAIR needs a mesh built with SEM_GEOM_PAIR");
+    if (o->precision == SEM_PCG_F64_PAIR && (o->h2 != 0.0 || o->h1 != 1.0))
+        return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_F64_PAIR solves the Poisson operator (h1 = 1, h2 = 0)");
     if (o->precision == SEM_PCG_MIXED && !m->G32)
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_MIXED needs a mesh built with SEM_GEOM_F32");
     if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
@@ -958,9 +895,11 @@ static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
     for (int q = 0; q < K; ++q) {
         int s = ax_cg_launch_f32(m, cg, S.M.in.w, st);
         if (s != SEM_OK) return s;
-        s = gs_launch(m, S.M.in.w, SEM_F32, kGsSumMask, st, &S.M.in.scal->done, 0);
+        // axis-by-axis gather-scatter: y and z passes (guarded by the solve's
+        // done flag), the x pass and the mask inside the update
+        s = gs_yz_launch(m, S.M.in.w, SEM_F32, st, &S.M.in.scal->done, 0);
         if (s != SEM_OK) return s;
-        s = launch_update<float>(S.M.d32, m->dinv32, m->minv32, n, S.M.in, st);
+        s = launch_update_box<float>(m, S.M.d32, m->dinv32, S.M.in, st);
         if (s != SEM_OK) return s;
     }
     bt_pause_kernel<<<1, 32, 0, st>>>(S.M.in.scal, S.M.scal_out);

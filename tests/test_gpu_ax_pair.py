@@ -104,3 +104,57 @@ def test_full_size_ax_pair_sampled_elements():
     assert st == 0
     ref = oracle.ax_local(case.N, oracle.deriv(case.N), G, u.reshape(case.E, -1)[sel])
     assert _rel(w[sel], ref) <= AX_TOL
+
+
+# ------------------------------------------------------------------ the FP64 solver on the pair operator
+# Gate as for the other non-FP64 paths: the oracle's own residual of the
+# returned solution, the iteration count of the FP64 solver (same Krylov
+# process), and continuity (every copy of a node holds the same value).
+PCG_CASES = [inputs.channel(5, 7), inputs.deformed_cube(6, 5),
+             inputs.BoxCase("n9", 9, (3, 4, 3), (0, 0, 0), inputs.ALL_FACES, perturb_amp=0.05, seed=2)] + \
+            [c for c in CASES if c.name in ("n2_jitter", "n3_periodic1", "n11_deformed")]
+
+
+@pytest.mark.parametrize("case", PCG_CASES, ids=[c.name for c in PCG_CASES])
+def test_pcg_f64_pair_matches_oracle(case):
+    om, gm = _meshes(case)
+    b = om.scatter(case.rhs_global())
+    xg, st = gm.pcg(_dev(b), tol=1e-10, max_iter=20000, precision=binding.SEM_PCG_F64_PAIR)
+    _, s64 = gm.pcg(_dev(b), tol=1e-10, max_iter=20000)
+    assert st["status"] == 0, st
+    assert abs(st["iters"] - s64["iters"]) <= max(3, 0.02 * s64["iters"])
+    xh = _host(xg)
+    r = b - om.apply(xh)
+    assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 2e-10
+    xo, _, _, sto = om.pcg(b, tol=1e-12, max_iter=20000)
+    assert sto == 0 and _rel(xh, xo) <= 1e-6
+    one = np.zeros(om.nglob)
+    one[om.gid] = xh
+    np.testing.assert_array_equal(xh, one[om.gid])
+
+
+def test_pcg_f64_pair_needs_pair_geometry_and_poisson():
+    case = CASES[4]
+    om, gm = _meshes(case)
+    b = _dev(om.scatter(case.rhs_global()))
+    with pytest.raises(binding.SemError) as ei:
+        gm.pcg(b, precision=binding.SEM_PCG_F64_PAIR, h2=1.0)
+    assert ei.value.status == binding.SEM_ERR_UNSUPPORTED
+    g2 = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices())
+    with pytest.raises(binding.SemError) as ei:
+        g2.pcg(b, precision=binding.SEM_PCG_F64_PAIR)
+    assert ei.value.status == binding.SEM_ERR_INVALID_ARG
+
+
+@pytest.mark.slow
+def test_full_size_pcg_f64_pair_true_residual():
+    case = inputs.channel(32, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_pair=True)
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    xg, st = gm.pcg(_dev(b), tol=1e-8, max_iter=20000, precision=binding.SEM_PCG_F64_PAIR)
+    assert st["status"] == 0
+    x = _host(xg)
+    r = b - om.apply(x)
+    assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 1.05e-8
