@@ -153,8 +153,11 @@ class NSOracle:
         Wm = fine_metric(self.verts, z, w)
 
         def interp(f, Ji, Jj, Jk):
+            # one direction at a time (i, then j, then k)
             F = np.reshape(f, (E, N1, N1, N1))
-            return np.einsum("qi,rj,sk,ekji->esrq", Ji, Jj, Jk, F).reshape(E, -1)
+            F = np.einsum("qi,ekji->ekjq", Ji, F)
+            F = np.einsum("rj,ekjq->ekrq", Jj, F)
+            return np.einsum("sk,ekrq->esrq", Jk, F).reshape(E, -1)
 
         uf = [interp(u[m], J, J, J) for m in range(3)]
         ct = [sum(Wm[:, m, a] * uf[m] for m in range(3)) for a in range(3)]
@@ -164,7 +167,9 @@ class NSOracle:
             ds = interp(u[c], J, JD, J)
             dt = interp(u[c], J, J, JD)
             fq = (ct[0] * dr + ct[1] * ds + ct[2] * dt).reshape(E, M, M, M)
-            out.append(np.einsum("qi,rj,sk,esrq->ekji", J, J, J, fq).reshape(-1))
+            g = np.einsum("sk,esrq->ekrq", J, fq)
+            g = np.einsum("rj,ekrq->ekjq", J, g)
+            out.append(np.einsum("qi,ekjq->ekji", J, g).reshape(-1))
         return out
 
     def advect_dealiased(self, u):
