@@ -299,12 +299,28 @@ int sem_ns_set_velocity(sem_ns *ns, const double *u, void *stream);
 /* Copy a state field to dst (device, nloc): 0..2 velocity u^n, 3 pressure
  * p^n, 4 pressure p^{n-1}, 5 pressure p^{n-2}, 6 the last pressure right-
  * hand side (assembled, zero mean), 7..9 velocity u^{n-1}, 10..12 advection
- * term NL^{n-1}.  sem_ns_set writes the same slots (checkpoint restore);
- * with sem_ns_get_steps / sem_ns_set_steps they hold the whole state. */
+ * term NL^{n-1}, 13..15 velocity u^{n-2}, 16..18 NL^{n-2}.  sem_ns_set writes
+ * the same slots (checkpoint restore); with sem_ns_get_steps /
+ * sem_ns_set_steps they hold the whole state. */
 int sem_ns_get(const sem_ns *ns, int which, double *dst, void *stream);
 int sem_ns_set(sem_ns *ns, int which, const double *src, void *stream);
 int sem_ns_get_steps(const sem_ns *ns);
 int sem_ns_set_steps(sem_ns *ns, int steps);
+/* Time scheme and advection form (defaults: order 2, collocation).
+ * order 1..3: step n uses BDF_k / EXT_k with k = min(n+1, order); order 3 is
+ * the BDF3 / EXT3 pair of the high-order splitting the paper cites for Neko
+ * (section 3.1): b0 = 11/6, b = (3, -3/2, 1/3), a = (3, -3, 1).
+ * dealias != 0: the advection term is integrated exactly on M = 3(N+1)/2
+ * Gauss-Legendre points per direction (the 3/2 rule) in its weak form
+ * int phi_i (u.grad)u_c, then assembled and divided by the assembled mass;
+ * d_dealias (device, 256-byte aligned, >= sem_ns_dealias_bytes) receives the
+ * fine-point metric factors (9 doubles per Gauss point) and must stay alive
+ * while the state is used.  N <= 9.  Stream-ordered. */
+size_t sem_ns_dealias_bytes(const sem_mesh *mesh);
+int sem_ns_set_scheme(sem_ns *ns, int order, int dealias, void *d_dealias, size_t bytes, void *stream);
+/* The state's advection term of u (device, 3*nloc, continuous) into nl
+ * (device, 3*nloc): -(u.grad)u by collocation, or its dealiased form. */
+int sem_ns_advect(const sem_ns *ns, const double *u, double *nl, void *stream);
 /* Scratch for sem_ns_step with these solver options. */
 size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts);
 /* One time step.  popts / vopts: pressure / velocity solver options (the

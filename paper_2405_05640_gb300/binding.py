@@ -139,6 +139,9 @@ _SIGS = {
     "sem_ns_step": ([_VP, ctypes.c_double, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgOpts), _VP,
                      ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_ns_kinetic_energy": ([_VP, ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_ns_dealias_bytes": ([_VP], ctypes.c_size_t),
+    "sem_ns_set_scheme": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_ns_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
                        ctypes.c_int),
 }
@@ -403,6 +406,25 @@ class NSState:
     def set_velocity(self, u):
         check(lib().sem_ns_set_velocity(self.handle, _ptr(u), _stream()), "sem_ns_set_velocity")
 
+    def set_scheme(self, order: int = 2, dealias: bool = False):
+        """sem_ns_set_scheme; the dealiasing buffer is kept by this object."""
+        import torch
+        self._dealias = None
+        ptr, n = None, 0
+        if dealias:
+            n = lib().sem_ns_dealias_bytes(self.mesh.handle)
+            self._dealias = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+            ptr = _VP((self._dealias.data_ptr() + 255) // 256 * 256)
+        check(lib().sem_ns_set_scheme(self.handle, int(order), int(bool(dealias)), ptr, n, _stream()),
+              "sem_ns_set_scheme")
+
+    def advect(self, u):
+        """The state's advection term of u ([3, nloc] device tensor)."""
+        import torch
+        out = torch.empty_like(u)
+        check(lib().sem_ns_advect(self.handle, _ptr(u), _ptr(out), _stream()), "sem_ns_advect")
+        return out
+
     def get(self, which: int):
         import torch
         out = torch.empty(self.mesh.nloc, dtype=torch.float64, device="cuda")
@@ -440,7 +462,7 @@ class NSState:
                                        ctypes.byref(ps), vs, _VP(base), nbytes, _stream()), "sem_ns_step_finish")
         return ps.as_dict(), [v.as_dict() for v in vs]
 
-    SLOTS = 13
+    SLOTS = 19
 
     def checkpoint(self):
         """Device copies of every state field plus the step count."""

@@ -221,6 +221,14 @@ inline BoxTopo box_topo(const sem_mesh *m) {
 int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const int *guard = nullptr,
                  int gval = 0);
 
+// Dealiased advection (sem_dealias.cu): fine-point factors w_q det J dr_a/dx_m
+// ([E][9][M^3], M = 3(N+1)/2 Gauss points per direction) and the local weak
+// form W_c = int phi_i (u . grad) u_c.  N <= 9.
+size_t dealias_metric_bytes(const sem_mesh *m);
+int dealias_metric_launch(const sem_mesh *m, double *W, cudaStream_t st);
+int advect_weak_launch(const sem_mesh *m, const double *W, const double *const u[3], double *const out[3],
+                       cudaStream_t st);
+
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies
 constexpr int kGsSumMask = 1;   // sum copies, then zero Dirichlet nodes

@@ -6,7 +6,9 @@
 // (Karniadakis, Israeli & Orszag 1991), a Krylov method solves the pressure
 // system each step and CG the velocity systems.  The scheme written here is
 // BDF_k / EXT_k (k = min(step+1, 2)), P_N-P_N collocation without
-// dealiasing:
+// dealiasing by default; sem_ns_set_scheme raises the order to 3 (BDF3 /
+// EXT3, the high-order splitting the paper cites) and switches the advection
+// to its dealiased weak form (sem_dealias.cu):
 //   F   = sum_j (b_j/dt) u^{n+1-j} + sum_j a_j NL^{n+1-j},   NL = -(u.grad)u
 //   A p = Q Q^T wdiv(F) - mean  (singular periodic Poisson; p has zero mean)
 //   (nu A + (b0/dt) B) u_c = Q Q^T [B (F_c - dp/dx_c)]
@@ -26,8 +28,13 @@ struct sem_ns {
     const sem_mesh *m;
     double nu;
     int steps;
-    double *u[3], *uprev[3], *unew[3];
-    double *nl[3], *nlprev[3];
+    int order;      // highest BDF/EXT order (1..3); step n uses k = min(n+1, order)
+    int dealias;    // advection by the dealiased weak form
+    int k;          // order of the step begun
+    double *W;      // fine-point factors of the dealiased advection (caller buffer)
+    double *binv;   // 1 / (Q Q^T B)
+    double *u[3], *uprev[3], *uprev2[3], *unew[3];
+    double *nl[3], *nlprev[3], *nlprev2[3];
     double *F[3];
     double *ph[3];  // p^n, p^{n-1}, p^{n-2}
     double *bp;     // last pressure right-hand side (assembled, zero mean)
@@ -126,18 +133,19 @@ __global__ void __launch_bounds__(ns_threads<N>())
     }
 }
 
-// Forcing F_c = s1 u_c + s2 uprev_c + a1 nl_c + a2 nlprev_c (order 2 terms
-// skipped when k = 1), stored; then the local weak divergence
-// w = sum_a D_a^T [B sum_m rx[a][m] F_m].  With u == nullptr, F is an input.
+// Forcing F_c = sum_{j<k} (s_j u^{n-j}_c + a_j NL^{n-j}_c), stored; then the
+// local weak divergence w = sum_a D_a^T [B sum_m rx[a][m] F_m].  With k = 0,
+// F is an input.
+struct NsForce {
+    const double *u[3][3];   // [level j][component]
+    const double *nl[3][3];
+    double s[3], a[3];
+    int k;
+};
+
 template <int N>
 __global__ void __launch_bounds__(ns_threads<N>())
-    force_wdiv_kernel(const double *__restrict__ u0, const double *__restrict__ u1, const double *__restrict__ u2,
-                      const double *__restrict__ up0, const double *__restrict__ up1,
-                      const double *__restrict__ up2, const double *__restrict__ nl0,
-                      const double *__restrict__ nl1, const double *__restrict__ nl2,
-                      const double *__restrict__ np0, const double *__restrict__ np1,
-                      const double *__restrict__ np2, double s1, double s2, double a1, double a2, int order,
-                      double *__restrict__ F0, double *__restrict__ F1, double *__restrict__ F2,
+    force_wdiv_kernel(const NsForce H, double *__restrict__ F0, double *__restrict__ F1, double *__restrict__ F2,
                       const double *__restrict__ Bm, const double *__restrict__ rx, DMat Dm, int E,
                       double *__restrict__ w) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
@@ -149,14 +157,11 @@ __global__ void __launch_bounds__(ns_threads<N>())
         for (int p = threadIdx.x; p < NPT; p += blockDim.x) {
             const int64_t l = (int64_t)e * NPT + p;
             double f[3];
-            if (u0) {
-                f[0] = s1 * u0[l] + a1 * nl0[l];
-                f[1] = s1 * u1[l] + a1 * nl1[l];
-                f[2] = s1 * u2[l] + a1 * nl2[l];
-                if (order == 2) {
-                    f[0] += s2 * up0[l] + a2 * np0[l];
-                    f[1] += s2 * up1[l] + a2 * np1[l];
-                    f[2] += s2 * up2[l] + a2 * np2[l];
+            if (H.k > 0) {
+                for (int c = 0; c < 3; ++c) {
+                    double v = 0.0;
+                    for (int j = 0; j < H.k; ++j) v += H.s[j] * H.u[j][c][l] + H.a[j] * H.nl[j][c][l];
+                    f[c] = v;
                 }
                 F0[l] = f[0];
                 F1[l] = f[1];
@@ -184,6 +189,12 @@ __global__ void __launch_bounds__(ns_threads<N>())
             w[(int64_t)e * NPT + p] = s;
         }
     }
+}
+
+// nl <- -binv * nl (the assembled weak advection to its strong, continuous form)
+__global__ void scale_neg_kernel(double *__restrict__ a, const double *__restrict__ binv, int64_t n) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+        a[l] = -binv[l] * a[l];
 }
 
 // velocity right-hand sides vr_c = B (F_c - d p / d x_c) (local)
@@ -350,11 +361,8 @@ static int launch_advect(const sem_mesh *m, const double *const u[3], double *co
     return SEM_OK;
 }
 
-static int launch_force_wdiv(const sem_mesh *m, const double *const u[3], const double *const up[3],
-                             const double *const nl[3], const double *const np[3], double s1, double s2,
-                             double a1, double a2, int order, double *const F[3], double *w, cudaStream_t st) {
-    SEM_NS_DISPATCH(force_wdiv_kernel, u[0], u[1], u[2], up[0], up[1], up[2], nl[0], nl[1], nl[2], np[0], np[1],
-                    np[2], s1, s2, a1, a2, order, F[0], F[1], F[2], m->B, m->rx, m->D, (int)m->E, w)
+static int launch_force_wdiv(const sem_mesh *m, const NsForce &H, double *const F[3], double *w, cudaStream_t st) {
+    SEM_NS_DISPATCH(force_wdiv_kernel, H, F[0], F[1], F[2], m->B, m->rx, m->D, (int)m->E, w)
     return SEM_OK;
 }
 
@@ -386,6 +394,23 @@ static size_t ns_red_bytes() { return align_up(sizeof(double) * (2 * kNsRedBlock
 
 }  // namespace sem
 
+// The state's advection form on u (3 fields) into nl: collocation, or the
+// dealiased weak form assembled and divided by the assembled mass.
+static int ns_advect_into(const sem_ns *ns, const double *const u[3], double *const nl[3], cudaStream_t st) {
+    using namespace sem;
+    const sem_mesh *m = ns->m;
+    if (!ns->dealias) return launch_advect(m, u, nl, st);
+    int s = advect_weak_launch(m, ns->W, u, nl, st);
+    if (s != SEM_OK) return s;
+    for (int c = 0; c < 3; ++c) {
+        s = gs_launch(m, nl[c], SEM_F64, kGsSum, st);
+        if (s != SEM_OK) return s;
+        scale_neg_kernel<<<grid_pts(m), 256, 0, st>>>(nl[c], ns->binv, m->nloc);
+        SEM_CUDA_CHECK(cudaGetLastError());
+    }
+    return SEM_OK;
+}
+
 using namespace sem;
 
 static double *ns_slot(const sem_ns *ns, int which);
@@ -412,14 +437,16 @@ int sem_weak_div(const sem_mesh *m, const double *F, double *w, void *stream) {
     int s = need_rx(m);
     if (s != SEM_OK) return s;
     if (!F || !w) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
-    const double *none[3] = {nullptr, nullptr, nullptr};
+    NsForce H{};
+    H.k = 0;  // F is the input
     double *FF[3] = {const_cast<double *>(F), const_cast<double *>(F + m->nloc), const_cast<double *>(F + 2 * m->nloc)};
-    return launch_force_wdiv(m, none, none, none, none, 0, 0, 0, 0, 1, FF, w, as_stream(stream));
+    return launch_force_wdiv(m, H, FF, w, as_stream(stream));
 }
 
-// 27 fields: per component u, u^{n-1}, u^{n+1}, NL, NL^{n-1}, F, pressure
-// history slot, velocity right-hand side; plus bp, dA, dh; then reductions.
-constexpr int kNsFields = 27;
+// 34 fields: per component u, u^{n-1}, u^{n-2}, u^{n+1}, NL, NL^{n-1},
+// NL^{n-2}, F, pressure history slot, velocity right-hand side; plus bp, dA,
+// dh, binv; then reductions.
+constexpr int kNsFields = 34;
 
 size_t sem_ns_workspace_bytes(const sem_mesh *m) {
     if (!m) return 0;
@@ -446,9 +473,11 @@ int sem_ns_create(const sem_mesh *m, double Re, void *ws, size_t bytes, void *st
     for (int c = 0; c < 3; ++c) {
         ns->u[c] = take();
         ns->uprev[c] = take();
+        ns->uprev2[c] = take();
         ns->unew[c] = take();
         ns->nl[c] = take();
         ns->nlprev[c] = take();
+        ns->nlprev2[c] = take();
         ns->F[c] = take();
         ns->ph[c] = take();
         ns->vr[c] = take();
@@ -456,6 +485,11 @@ int sem_ns_create(const sem_mesh *m, double Re, void *ws, size_t bytes, void *st
     ns->bp = take();
     ns->dA = take();
     ns->dh = take();
+    ns->binv = take();
+    ns->order = 2;
+    ns->dealias = 0;
+    ns->k = 1;
+    ns->W = nullptr;
     ns->red = reinterpret_cast<double *>(p);  // after the kNsFields slots
     cudaStream_t st = as_stream(stream);
     s = jacobi_diag_launch(m, ns->dA, st);
@@ -472,6 +506,41 @@ int sem_ns_create(const sem_mesh *m, double Re, void *ws, size_t bytes, void *st
     }
     *out = ns;
     return SEM_OK;
+}
+
+size_t sem_ns_dealias_bytes(const sem_mesh *m) { return dealias_metric_bytes(m); }
+
+int sem_ns_set_scheme(sem_ns *ns, int order, int dealias, void *d_dealias, size_t bytes, void *stream) {
+    if (!ns || order < 1 || order > 3) return fail(SEM_ERR_INVALID_ARG, "NULL state or order outside 1..3");
+    const sem_mesh *m = ns->m;
+    cudaStream_t st = as_stream(stream);
+    if (dealias) {
+        if (!d_dealias || reinterpret_cast<uintptr_t>(d_dealias) % kAlign || bytes < dealias_metric_bytes(m))
+            return fail(SEM_ERR_WORKSPACE, "dealias buffer NULL, misaligned or smaller than sem_ns_dealias_bytes");
+        double *W = static_cast<double *>(d_dealias);
+        int s = dealias_metric_launch(m, W, st);
+        if (s != SEM_OK) return s;
+        // 1 / (Q Q^T B)
+        SEM_CUDA_CHECK(cudaMemcpyAsync(ns->binv, m->B, sizeof(double) * m->nloc, cudaMemcpyDeviceToDevice, st));
+        s = gs_launch(m, ns->binv, SEM_F64, kGsSum, st);
+        if (s != SEM_OK) return s;
+        invert_kernel_ns<<<grid_pts(m), 256, 0, st>>>(ns->binv, m->nloc);
+        SEM_CUDA_CHECK(cudaGetLastError());
+        ns->W = W;
+    } else {
+        ns->W = nullptr;
+    }
+    ns->order = order;
+    ns->dealias = dealias ? 1 : 0;
+    return SEM_OK;
+}
+
+int sem_ns_advect(const sem_ns *ns, const double *u, double *nl, void *stream) {
+    if (!ns || !u || !nl) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n = ns->m->nloc;
+    const double *uu[3] = {u, u + n, u + 2 * n};
+    double *nn[3] = {nl, nl + n, nl + 2 * n};
+    return ns_advect_into(ns, uu, nn, as_stream(stream));
 }
 
 int sem_ns_destroy(sem_ns *ns) {
@@ -511,14 +580,30 @@ int sem_ns_step_begin(sem_ns *ns, double dt, void *stream) {
     if (!ns || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "NULL state or dt <= 0");
     const sem_mesh *m = ns->m;
     cudaStream_t st = as_stream(stream);
-    const int k = ns->steps == 0 ? 1 : 2;
-    const double s1 = (k == 1 ? 1.0 : 2.0) / dt, s2 = (k == 1 ? 0.0 : -0.5) / dt;
-    const double a1 = k == 1 ? 1.0 : 2.0, a2 = k == 1 ? 0.0 : -1.0;
+    const int k = ns->steps + 1 < ns->order ? ns->steps + 1 : ns->order;
+    // BDF_k history weights b_j (b0 in step_finish) and EXT_k weights a_j
+    static const double kB[4][3] = {{0, 0, 0}, {1.0, 0, 0}, {2.0, -0.5, 0}, {3.0, -1.5, 1.0 / 3.0}};
+    static const double kA[4][3] = {{0, 0, 0}, {1.0, 0, 0}, {2.0, -1.0, 0}, {3.0, -3.0, 1.0}};
     // advection at t^n, forcing, weak divergence -> pressure right-hand side
-    int s = launch_advect(m, ns->u, ns->nl, st);
+    int s = ns_advect_into(ns, ns->u, ns->nl, st);
     if (s != SEM_OK) return s;
-    s = launch_force_wdiv(m, ns->u, ns->uprev, ns->nl, ns->nlprev, s1, s2, a1, a2, k, ns->F, ns->bp, st);
+    NsForce H{};
+    H.k = k;
+    for (int c = 0; c < 3; ++c) {
+        H.u[0][c] = ns->u[c];
+        H.u[1][c] = ns->uprev[c];
+        H.u[2][c] = ns->uprev2[c];
+        H.nl[0][c] = ns->nl[c];
+        H.nl[1][c] = ns->nlprev[c];
+        H.nl[2][c] = ns->nlprev2[c];
+    }
+    for (int j = 0; j < 3; ++j) {
+        H.s[j] = kB[k][j] / dt;
+        H.a[j] = kA[k][j];
+    }
+    s = launch_force_wdiv(m, H, ns->F, ns->bp, st);
     if (s != SEM_OK) return s;
+    ns->k = k;
     s = gs_launch(m, ns->bp, SEM_F64, kGsSum, st);
     if (s != SEM_OK) return s;
     s = remove_mean(m, ns->bp, ns->red, st);
@@ -536,7 +621,7 @@ int sem_ns_step_finish(sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts
     const sem_mesh *m = ns->m;
     cudaStream_t st = as_stream(stream);
     const double dt = ns->begun_dt;
-    const double b0 = ns->steps == 0 ? 1.0 : 1.5;
+    const double b0 = ns->k == 1 ? 1.0 : (ns->k == 2 ? 1.5 : 11.0 / 6.0);
     int s;
     // pressure: solve into the oldest history slot
     double *pn = ns->ph[2];
@@ -580,13 +665,15 @@ int sem_ns_step_finish(sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts
         s = sem_pcg_solve(m, ns->vr[c], ns->unew[c], &vo, &vstats[c], scratch, scratch_bytes, stream);
         if (s != SEM_OK) return s;
     }
-    // history: u^{n-1} <- u^n <- u^{n+1};  NL^{n-1} <- NL^n;  p ring
+    // history: u^{n-2} <- u^{n-1} <- u^n <- u^{n+1};  NL^{n-2} <- NL^{n-1} <- NL^n;  p ring
     for (int c = 0; c < 3; ++c) {
-        double *t = ns->uprev[c];
+        double *t = ns->uprev2[c];
+        ns->uprev2[c] = ns->uprev[c];
         ns->uprev[c] = ns->u[c];
         ns->u[c] = ns->unew[c];
         ns->unew[c] = t;
-        double *q = ns->nlprev[c];
+        double *q = ns->nlprev2[c];
+        ns->nlprev2[c] = ns->nlprev[c];
         ns->nlprev[c] = ns->nl[c];
         ns->nl[c] = q;
     }
@@ -615,6 +702,8 @@ static double *ns_slot(const sem_ns *ns, int which) {
     if (which == 6) return ns->bp;
     if (which >= 7 && which < 10) return ns->uprev[which - 7];
     if (which >= 10 && which < 13) return ns->nlprev[which - 10];
+    if (which >= 13 && which < 16) return ns->uprev2[which - 13];
+    if (which >= 16 && which < 19) return ns->nlprev2[which - 16];
     return nullptr;
 }
 
