@@ -47,6 +47,9 @@ template <int N1>
 struct PairD {
     float h[N1 * N1], l[N1 * N1];  // D = h + l, row-major D[i][l]
     float rf[N1], rb[N1];           // anchor factors: 2 sum_l |h[i][l]| and 2 sum_l |h[l][i]|, rounded up
+    // the same entries for two consecutive outputs i, i+1 side by side (packed
+    // FP32x2 operands): fh[i][l] = (h[i][l], h[i+1][l]), bh[i][l] = (h[l][i], h[l][i+1])
+    float2 fh[(N1 - 1) * N1], fl[(N1 - 1) * N1], bh[(N1 - 1) * N1], bl[(N1 - 1) * N1];
 };
 
 struct PairArgs {
@@ -153,8 +156,49 @@ __device__ __forceinline__ void line_dot(const float2 (&x)[N1], const PairD<N1> 
     float m = 0.f;
 #pragma unroll
     for (int l = 0; l < N1; ++l) m = fmaxf(m, fabsf(x[l].x));
+    // outputs in pairs (i, i+1): every FP32 operation below runs as one packed
+    // FP32x2 instruction for both (the same IEEE operations per lane as the
+    // scalar tail; -(s1 - s) is fma(s1, -1, s), exact)
+    constexpr int NP = (I1 - I0) / 2;
+    if constexpr (NP > 0) {
+        float2 xh[N1], xl[N1];
 #pragma unroll
-    for (int i = I0; i < I1; ++i) {
+        for (int l = 0; l < N1; ++l) {
+            xh[l] = make_float2(x[l].x, x[l].x);
+            xl[l] = make_float2(x[l].y, x[l].y);
+        }
+        const float2 minus1 = make_float2(-1.f, -1.f);
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+            const int i = I0 + 2 * pr;
+            float2 sig;
+            {
+                const float f0 = __fmul_rn(m, TR ? D.rb[i] : D.rf[i]);
+                const float f1 = __fmul_rn(m, TR ? D.rb[i + 1] : D.rf[i + 1]);
+                sig = make_float2(__int_as_float((__float_as_int(f0) + 0x007fffff) & 0x7f800000),
+                                  __int_as_float((__float_as_int(f1) + 0x007fffff) & 0x7f800000));
+            }
+            float2 s2 = sig, ce = make_float2(0.f, 0.f), cx = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                const float2 dh = TR ? D.bh[i * N1 + l] : D.fh[i * N1 + l];
+                const float2 dl = TR ? D.bl[i * N1 + l] : D.fl[i * N1 + l];
+                const float2 p = __fmul2_rn(dh, xh[l]);
+                const float2 s1 = __fadd2_rn(s2, p);
+                const float2 nd = __ffma2_rn(s1, minus1, s2);  // s - s1, exact: |s| >= |p|
+                ce = __fadd2_rn(ce, __ffma2_rn(dh, xh[l], nd)); // fl(dh*xh - (s1 - s))
+                s2 = s1;
+                cx = __ffma2_rn(dh, xl[l], cx);
+                cx = __ffma2_rn(dl, xh[l], cx);
+            }
+            const float2 hi = __fadd2_rn(s2, make_float2(-sig.x, -sig.y));  // exact (Sterbenz)
+            const float2 lo = __fadd2_rn(ce, cx);
+            y[i - I0] = TR ? make_float2(hi.x, lo.x) : pair_fast(hi.x, lo.x);
+            y[i + 1 - I0] = TR ? make_float2(hi.y, lo.y) : pair_fast(hi.y, lo.y);
+        }
+    }
+#pragma unroll
+    for (int i = I0 + 2 * NP; i < I1; ++i) {  // the odd output, scalar
         const float f = __fmul_rn(m, TR ? D.rb[i] : D.rf[i]);
         const float sig = __int_as_float((__float_as_int(f) + 0x007fffff) & 0x7f800000);
         float s = sig, ce = 0.f, cx = 0.f;
@@ -469,6 +513,13 @@ static int launch_pair_n(const sem_mesh *m, const double *u, double *w, const Cg
             const float h = (float)d;
             D.h[i * N1 + l] = h;
             D.l[i * N1 + l] = (float)(d - (double)h);
+        }
+    for (int i = 0; i + 1 < N1; ++i)
+        for (int l = 0; l < N1; ++l) {
+            D.fh[i * N1 + l] = make_float2(D.h[i * N1 + l], D.h[(i + 1) * N1 + l]);
+            D.fl[i * N1 + l] = make_float2(D.l[i * N1 + l], D.l[(i + 1) * N1 + l]);
+            D.bh[i * N1 + l] = make_float2(D.h[l * N1 + i], D.h[l * N1 + i + 1]);
+            D.bl[i * N1 + l] = make_float2(D.l[l * N1 + i], D.l[l * N1 + i + 1]);
         }
     for (int i = 0; i < N1; ++i) {
         double rs = 0.0, cs = 0.0;

@@ -221,8 +221,8 @@ int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const i
     const int64_t ntot = (nA + Gy * nKs) * nxl;
     if (ntot == 0) return SEM_OK;
     if (ntot >= (int64_t(1) << 32)) return fail(SEM_ERR_UNSUPPORTED, "gs_yz: too many node groups");
-    int64_t g = (ntot + 255) / 256;
-    if (g > (int64_t)m->num_sms * 16) g = (int64_t)m->num_sms * 16;
+    // one node group per thread: the loads of every group are in flight at once
+    const int64_t g = (ntot + 255) / 256;
     if (dtype == SEM_F64)
         gs_yz_kernel<double><<<(int)g, 256, 0, st>>>(static_cast<double *>(u), B, (unsigned)nA, (unsigned)ntot, nKs,
                                                      guard, gval);
