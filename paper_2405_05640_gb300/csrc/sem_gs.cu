@@ -156,58 +156,73 @@ __device__ __forceinline__ int axis_copies(int G, int nel, int per, int N, int &
     return 1;
 }
 
-// Thread t (32-bit: t < 2 nloc < 2^32) -> x position (ex, i) = t mod nxl and
-// group q = t / nxl: q < nA: J = the (q / Gz)-th shared y boundary, K = q mod
-// Gz; else J = any y node that is not shared (shared ones are skipped: they
-// belong to the first set), K = a shared z boundary.
-template <typename T>
+// Block row y = one (J, K) node group: y < nA: J = the (y / Gz)-th shared y
+// boundary, K = y mod Gz; else J = any y node that is not shared (shared ones
+// are skipped: they belong to the first set), K = a shared z boundary.
+// Threads along x run over the x positions (ex, i).  N is a template
+// parameter, so the index arithmetic per thread is a few multiplies.
+template <typename T, int N>
 __global__ void __launch_bounds__(256)
-    gs_yz_kernel(T *__restrict__ u, BoxTopo B, unsigned nA, unsigned ntot, int nKs, const int *__restrict__ guard,
-                 int gval) {
+    gs_yz_kernel(T *__restrict__ u, BoxTopo B, int nA, int nrows, int nKs, const int *__restrict__ guard, int gval) {
     if (guard && *guard != gval) return;
-    const unsigned nxl = (unsigned)(B.nel[0] * B.N1);  // x positions (ex, i)
-    const unsigned Gz = (unsigned)(B.nel[2] * B.N + (B.per[2] ? 0 : 1));
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += gridDim.x * blockDim.x) {
-        const unsigned q = t / nxl;
-        const int xi = (int)(t - q * nxl);
-        const int ex = xi / B.N1, i = xi - ex * B.N1;
+    constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
+    const int nxl = B.nel[0] * N1;  // x positions (ex, i)
+    const int Gz = B.nel[2] * N + (B.per[2] ? 0 : 1);
+    for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
         int J, K;
-        if (q < nA) {
-            const unsigned a = q / Gz;
-            K = (int)(q - a * Gz);
-            J = (int)(B.per[1] ? a : a + 1) * B.N;
+        if (row < nA) {
+            const int a = row / Gz;
+            K = row - a * Gz;
+            J = (B.per[1] ? a : a + 1) * N;
         } else {
-            const unsigned b = q - nA;
-            const unsigned jj = b / (unsigned)nKs;
-            const int c = (int)(b - jj * (unsigned)nKs);
-            J = (int)jj;
-            K = (B.per[2] ? c : c + 1) * B.N;
+            const int b = row - nA;
+            const int jj = b / nKs;
+            J = jj;
+            K = (B.per[2] ? b - jj * nKs : b - jj * nKs + 1) * N;
         }
         int ey[2], jy[1], ez[2], kz[1];
-        const int ny = axis_copies(J, B.nel[1], B.per[1], B.N, ey[0], jy[0], ey[1]);
-        if (q >= nA && ny == 2) continue;  // a shared y node: done in the first set
-        const int nz = axis_copies(K, B.nel[2], B.per[2], B.N, ez[0], kz[0], ez[1]);
+        const int ny = axis_copies(J, B.nel[1], B.per[1], N, ey[0], jy[0], ey[1]);
+        if (row >= nA && ny == 2) continue;  // a shared y node: done in the first set (uniform per block)
+        const int nz = axis_copies(K, B.nel[2], B.per[2], N, ez[0], kz[0], ez[1]);
         if (ny * nz < 2) continue;
-        auto at = [&](int ay, int bz, int jj, int kk) {
-            const int64_t e = ex + (int64_t)B.nel[0] * (ey[ay] + (int64_t)B.nel[1] * ez[bz]);
-            return e * B.NPT + i + B.N1 * (jj + B.N1 * kk);
-        };
-        // copies in the order (y0,z0), (y1,z0), (y0,z1), (y1,z1); y1 / z1 sit at j / k = 0
-        const int64_t i00 = at(0, 0, jy[0], kz[0]);
-        if (ny == 2 && nz == 2) {
-            const int64_t i10 = at(1, 0, 0, kz[0]), i01 = at(0, 1, jy[0], 0), i11 = at(1, 1, 0, 0);
-            const T s = ((u[i00] + u[i10]) + u[i01]) + u[i11];
-            u[i00] = s;
-            u[i10] = s;
-            u[i01] = s;
-            u[i11] = s;
-        } else {
-            const int64_t i1 = ny == 2 ? at(1, 0, 0, kz[0]) : at(0, 1, jy[0], 0);
-            const T s = u[i00] + u[i1];
-            u[i00] = s;
-            u[i1] = s;
+        for (int xi = blockIdx.x * blockDim.x + threadIdx.x; xi < nxl; xi += gridDim.x * blockDim.x) {
+            const int ex = xi / N1, i = xi - ex * N1;
+            auto at = [&](int ay, int bz, int jj2, int kk) {
+                const int64_t e = ex + (int64_t)B.nel[0] * (ey[ay] + (int64_t)B.nel[1] * ez[bz]);
+                return e * NPT + i + N1 * (jj2 + N1 * kk);
+            };
+            // copies in the order (y0,z0), (y1,z0), (y0,z1), (y1,z1); y1 / z1 sit at j / k = 0
+            const int64_t i00 = at(0, 0, jy[0], kz[0]);
+            if (ny == 2 && nz == 2) {
+                const int64_t i10 = at(1, 0, 0, kz[0]), i01 = at(0, 1, jy[0], 0), i11 = at(1, 1, 0, 0);
+                const T s = ((u[i00] + u[i10]) + u[i01]) + u[i11];
+                u[i00] = s;
+                u[i10] = s;
+                u[i01] = s;
+                u[i11] = s;
+            } else {
+                const int64_t i1 = ny == 2 ? at(1, 0, 0, kz[0]) : at(0, 1, jy[0], 0);
+                const T s = u[i00] + u[i1];
+                u[i00] = s;
+                u[i1] = s;
+            }
         }
     }
+}
+
+template <typename T>
+static int gs_yz_dispatch(const sem_mesh *m, T *u, const BoxTopo &B, int nA, int nrows, int nKs, dim3 grid,
+                          cudaStream_t st, const int *guard, int gval) {
+    switch (m->N) {
+#define SEM_GSYZ_CASE(n) \
+    case n: gs_yz_kernel<T, n><<<grid, 256, 0, st>>>(u, B, nA, nrows, nKs, guard, gval); break;
+        SEM_GSYZ_CASE(1) SEM_GSYZ_CASE(2) SEM_GSYZ_CASE(3) SEM_GSYZ_CASE(4) SEM_GSYZ_CASE(5)
+        SEM_GSYZ_CASE(6) SEM_GSYZ_CASE(7) SEM_GSYZ_CASE(8) SEM_GSYZ_CASE(9) SEM_GSYZ_CASE(10) SEM_GSYZ_CASE(11)
+#undef SEM_GSYZ_CASE
+        default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
+    }
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
 }
 
 int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const int *guard, int gval) {
@@ -218,21 +233,15 @@ int gs_yz_launch(const sem_mesh *m, void *u, int dtype, cudaStream_t st, const i
     const int nKs = B.per[2] ? B.nel[2] : B.nel[2] - 1;
     const int64_t nxl = (int64_t)B.nel[0] * B.N1;
     const int64_t nA = (int64_t)nJs * Gz;
-    const int64_t ntot = (nA + Gy * nKs) * nxl;
-    if (ntot == 0) return SEM_OK;
-    if (ntot >= (int64_t(1) << 32)) return fail(SEM_ERR_UNSUPPORTED, "gs_yz: too many node groups");
-    // one node group per thread: the loads of every group are in flight at once
-    const int64_t g = (ntot + 255) / 256;
+    const int64_t nrows = nA + Gy * nKs;
+    if (nrows == 0 || nxl == 0) return SEM_OK;
+    if (nrows >= (int64_t(1) << 31)) return fail(SEM_ERR_UNSUPPORTED, "gs_yz: too many node rows");
+    dim3 grid((unsigned)((nxl + 255) / 256), (unsigned)(nrows < 65535 ? nrows : 65535));
     if (dtype == SEM_F64)
-        gs_yz_kernel<double><<<(int)g, 256, 0, st>>>(static_cast<double *>(u), B, (unsigned)nA, (unsigned)ntot, nKs,
-                                                     guard, gval);
-    else if (dtype == SEM_F32)
-        gs_yz_kernel<float><<<(int)g, 256, 0, st>>>(static_cast<float *>(u), B, (unsigned)nA, (unsigned)ntot, nKs,
-                                                    guard, gval);
-    else
-        return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
-    SEM_CUDA_CHECK(cudaGetLastError());
-    return SEM_OK;
+        return gs_yz_dispatch<double>(m, static_cast<double *>(u), B, (int)nA, (int)nrows, nKs, grid, st, guard, gval);
+    if (dtype == SEM_F32)
+        return gs_yz_dispatch<float>(m, static_cast<float *>(u), B, (int)nA, (int)nrows, nKs, grid, st, guard, gval);
+    return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
 }
 
 __global__ void scatter_kernel(const double *__restrict__ ug, double *__restrict__ ul, int64_t E, int N,
