@@ -79,6 +79,8 @@ def parse_args(argv=None):
     p.add_argument("--eval-steps", type=int, default=100)
     p.add_argument("--epochs", type=int, default=30)
     p.add_argument("--variant", choices=["p1", "d3"], default="p1")
+    p.add_argument("--bf16", action="store_true",
+                   help="channel variant: the FP32 inner operator reads BF16 geometric factors (32 B/point)")
     p.add_argument("--affine", action="store_true",
                    help="channel variant: the affine-element FP32 operator (3 scalars per element, 20 B/point)")
     return p.parse_args(argv)
@@ -225,7 +227,9 @@ def cpu_oracle_sample(case, iters, verts=None):
 #   FP64 operator: reads u (8 B) and G (6 x 8 B), writes w (8 B) = 64 B.
 OP_BYTES = {"f32_cg": 44, "f64": 64, "f64_cg": 64 + 16 + 8,
             # affine-element form: r, dinv, p read, p, w written; 16 B of scalars per element
-            "f32_cg_aff": 20}
+            "f32_cg_aff": 20,
+            # BF16 factors: r, dinv, p read (4 B each), G (6 x 2 B), p, w written
+            "f32_cg_bf16": 32}
 CHOSEN = dict(precision=1, inner_tol=1e-2)   # FP64 refinement around FP32 Jacobi-PCG
 PLAIN = dict(precision=0)
 
@@ -301,7 +305,7 @@ def run_ours(args):
     case = inputs.channel(args.nel, args.order)
     V = case.vertices()
     gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True, geom_pair=True,
-                      geom_affine=args.affine)
+                      geom_affine=args.affine, geom_bf16=args.bf16)
     bg = torch.from_numpy(case.rhs_global()).cuda()
     b = gm.scatter(bg)
     base = dict(tol=TOL, max_iter=50000, check_every=32)
@@ -372,13 +376,16 @@ def run_ours(args):
 
     peaks = measured_peaks()
     ax_avg_ms = ser["ax_ms"] / max(ser["ax_n"], 1)
-    algo_bytes = (OP_BYTES["f32_cg_aff"] * case.nloc + 16 * case.E) if args.affine else OP_BYTES["f32_cg"] * case.nloc
+    algo_bytes = ((OP_BYTES["f32_cg_aff"] * case.nloc + 16 * case.E) if args.affine else
+                  OP_BYTES["f32_cg_bf16"] * case.nloc if args.bf16 else OP_BYTES["f32_cg"] * case.nloc)
     achieved = algo_bytes / (ax_avg_ms * 1e-3) / 1e9
     sha = _src_sha(os.path.join(ROOT, "paper_2405_05640_gb300", "csrc", "sem_ax.cu"))
     tr = NCU_TRAFFIC.get("ax_f32_cg")
-    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha and not args.affine else None
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha and not (args.affine or args.bf16) else None
     kname = ("ax_kernel<7,float,CG,AFF> (fused FP32 operator, affine elements: p update, A p, <p,Ap>)"
-             if args.affine else "ax_kernel<7,float,CG> (fused FP32 operator: p update, A p, <p,Ap>)")
+             if args.affine else
+             "ax_kernel<7,float,CG,G16> (fused FP32 operator, BF16 factors: p update, A p, <p,Ap>)"
+             if args.bf16 else "ax_kernel<7,float,CG> (fused FP32 operator: p update, A p, <p,Ap>)")
     roofline = {"kernel": kname,
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
@@ -430,7 +437,8 @@ def run_ours(args):
                    "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL,
                    "precision": "FP64 iterative refinement around FP32 Jacobi-PCG (inner tol 1e-2)",
                    "geometry": ("affine elements: G from 3 scalars per element (variant)" if args.affine
-                                else "general: 6 geometric factors per point"),
+                                else "general, 6 factors per point in BF16 for the inner operator (variant)"
+                                if args.bf16 else "general: 6 geometric factors per point"),
                    "l2": "inputs larger than L2 (FP32 G 403 MB, FP64 G 805 MB, pair G 805 MB)",
                    "parallelism": f"replicas x{world}"},
         "pcg": {"chosen_time_to_1e-8_ms": round(ms_per_step, 3),
@@ -619,7 +627,7 @@ def run_deformed(args):
     from paper_2405_05640_gb300 import build as _build
     _build.build()
     case = inputs.deformed_cube(args.nel, args.order)
-    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True, geom_bf16=args.bf16)
     b = gm.scatter(torch.from_numpy(case.rhs_global()).cuda())
     scratch = gm.pcg_scratch(gm.pcg_opts(precision=binding.SEM_PCG_MIXED))
     out = {}

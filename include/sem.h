@@ -72,6 +72,12 @@ extern "C" {
                                       6 factors per point (20 instead of 44 bytes
                                       per point in the fused CG operator); needs
                                       SEM_GEOM_F32 */
+#define SEM_GEOM_BF16 16           /* BF16 copy of the six factors (12 bytes per point):
+                                      the FP32 operator (sem_ax SEM_F32, the mixed
+                                      solver's inner loop) reads it instead of the
+                                      FP32 factors (32 instead of 44 bytes per point
+                                      in the fused CG operator; FP32 arithmetic, the
+                                      factors rounded to 8 bits); needs SEM_GEOM_F32 */
 
 typedef struct sem_mesh sem_mesh;  /* opaque; freed by sem_mesh_destroy */
 

@@ -28,6 +28,7 @@ SEM_GEOM_F32 = 1
 SEM_GEOM_RX = 2
 SEM_GEOM_PAIR = 4
 SEM_GEOM_AFFINE = 8
+SEM_GEOM_BF16 = 16
 SEM_PCG_F64, SEM_PCG_MIXED, SEM_PCG_F64_PAIR = 0, 1, 2
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
@@ -196,7 +197,7 @@ class Mesh:
     """A box mesh living in a caller-owned (PyTorch) device workspace."""
 
     def __init__(self, N, nel, periodic, faces, vertices, geom_f32: bool = False, geom_rx: bool = False,
-                 geom_pair: bool = False, geom_affine: bool = False):
+                 geom_pair: bool = False, geom_affine: bool = False, geom_bf16: bool = False):
         import numpy as np
         import torch
         self._verts = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 8, 3)
@@ -207,7 +208,8 @@ class Mesh:
         d.dirichlet_faces = int(faces)
         d.vertices = self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.geom_flags = ((SEM_GEOM_F32 if geom_f32 else 0) | (SEM_GEOM_RX if geom_rx else 0)
-                        | (SEM_GEOM_PAIR if geom_pair else 0) | (SEM_GEOM_AFFINE if geom_affine else 0))
+                        | (SEM_GEOM_PAIR if geom_pair else 0) | (SEM_GEOM_AFFINE if geom_affine else 0)
+                        | (SEM_GEOM_BF16 if geom_bf16 else 0))
         self.desc = d
         nbytes = lib().sem_mesh_workspace_bytes(ctypes.byref(d))
         if nbytes == 0:

@@ -17,6 +17,10 @@
 // Every mbarrier wait is bounded in time; on time-out the kernel records
 // kDevTimeoutTma in the mesh error word and all CTAs leave the loop.
 
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "sem_common.cuh"
 
 namespace sem {
@@ -24,17 +28,17 @@ namespace sem {
 // Slabs per stage: the input field (u; or r, dinv, p in the fused CG mode),
 // the six geometric factors (AFF: the element's 4 affine scalars instead),
 // and B (Helmholtz, FP64).
-template <int N, typename T, bool HELM, bool CG, bool AFF>
+template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false>
 __host__ __device__ constexpr int ax_stage_bytes() {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
-    return ((NPT * ((CG ? 3 : 1) + (AFF ? 0 : 6)) * (int)sizeof(T) + (AFF ? 16 : 0) + (HELM ? NPT * 8 : 0)) + 15) /
-           16 * 16;
+    constexpr int gsize = AFF ? 16 : 6 * NPT * (G16 ? 2 : (int)sizeof(T));
+    return ((NPT * (CG ? 3 : 1) * (int)sizeof(T) + gsize + (HELM ? NPT * 8 : 0)) + 15) / 16 * 16;
 }
 
-template <int N, typename T, bool HELM, bool CG, bool AFF>
+template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false>
 __host__ __device__ constexpr int ax_smem_bytes(int nst) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    return nst * ax_stage_bytes<N, T, HELM, CG, AFF>() + 2 * NPT * (int)sizeof(T) +
+    return nst * ax_stage_bytes<N, T, HELM, CG, AFF, G16>() + 2 * NPT * (int)sizeof(T) +
            ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4 + 64;
 }
 
@@ -96,14 +100,18 @@ static AxTune tune_for(int dt, bool helm, bool cg, bool aff, int N) {
 //   CG: p <- dinv r + beta p (written back), w = A_L p (or Helmholtz), and
 //       sum_l p_l w_l reduced over the grid into alpha = rho / pw;
 //   AFF (axis-aligned box elements): G is diagonal and factorises, G_rr =
-//       rho_i rho_j rho_k a_e etc.; G points at the [E][4] scalars (a, b, c, 0).
-template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM>
+//       rho_i rho_j rho_k a_e etc.; G points at the [E][4] scalars (a, b, c, 0);
+//   G16 (FP32 operator): the six factors are stored in BF16 ([E][6][npt],
+//       12 bytes per point) and widened to FP32 in shared memory reads.
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16 = false>
 __global__ void __launch_bounds__(ax_threads<N>())
-    ax_kernel(const T *__restrict__ u, T *__restrict__ w, const T *__restrict__ G,
+    ax_kernel(const T *__restrict__ u, T *__restrict__ w, const void *__restrict__ Gv,
               const double *__restrict__ Bm, const DM Dm, const AxArgs args, const CgFuse<T> cg,
               int *__restrict__ err) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    constexpr int SB = ax_stage_bytes<N, T, HELM, CG, AFF>();
+    constexpr int SB = ax_stage_bytes<N, T, HELM, CG, AFF, G16>();
+    using GT = typename std::conditional<G16, __nv_bfloat16, T>::type;
+    const GT *__restrict__ G = static_cast<const GT *>(Gv);
     // Vector r-line loads and D_kl as constant-bank operands cut the shared-
     // memory instructions; measured faster for the FP32 plain and affine
     // forms, slower for the general fused CG form and FP64, which keep
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
 
     const int64_t E = args.E;
     const int64_t stride = gridDim.x;
-    const uint32_t ubytes = NPT * sizeof(T), gbytes = AFF ? 16 : 6 * NPT * sizeof(T);
+    const uint32_t ubytes = NPT * sizeof(T), gbytes = AFF ? 16 : 6 * NPT * sizeof(GT);
     const uint32_t bbytes = HELM ? NPT * sizeof(double) : 0;
 
     auto stage_ptr = [&](int s) { return smem + s * SB; };
@@ -200,8 +208,9 @@ __global__ void __launch_bounds__(ax_threads<N>())
             } else {
                 for (int q = tid; q < NPT; q += blockDim.x) dst[q] = u[e * NPT + q];
             }
-            const T *gs = AFF ? G + e * 4 : G + e * 6 * NPT;
-            for (int q = tid; q < (AFF ? 4 : 6 * NPT); q += blockDim.x) dst[NIN * NPT + q] = gs[q];
+            const GT *gs = AFF ? G + e * 4 : G + e * 6 * NPT;
+            GT *gd = reinterpret_cast<GT *>(st + NIN * ubytes);
+            for (int q = tid; q < (AFF ? 4 : 6 * NPT); q += blockDim.x) gd[q] = gs[q];
             if (HELM) {
                 double *db = reinterpret_cast<double *>(st + NIN * ubytes + gbytes);
                 for (int q = tid; q < NPT; q += blockDim.x) db[q] = Bm[e * NPT + q];
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
         }
         // the operand: u, or the updated search direction p (CG)
         T *su = reinterpret_cast<T *>(st) + (CG ? 2 * NPT : 0);
-        const T *sg = reinterpret_cast<const T *>(st) + NIN * NPT;
+        const GT *sg = reinterpret_cast<const GT *>(st + NIN * ubytes);
         const double *sb = reinterpret_cast<const double *>(st + NIN * ubytes + gbytes);
         if (CG) {
             const T *sr = reinterpret_cast<const T *>(st);
@@ -255,12 +264,12 @@ __global__ void __launch_bounds__(ax_threads<N>())
                 const int p = i + N1 * (j + N1 * k);
                 if (AFF) {
                     const T wq = rij * (T)args.rho[k];
-                    svr[p] = (wq * sg[0]) * ur;
-                    svs[p] = (wq * sg[1]) * us;
-                    rvt[k] = (wq * sg[2]) * ut;
+                    svr[p] = (wq * (T)sg[0]) * ur;
+                    svs[p] = (wq * (T)sg[1]) * us;
+                    rvt[k] = (wq * (T)sg[2]) * ut;
                 } else {
-                    const T g0 = sg[p], g1 = sg[NPT + p], g2 = sg[2 * NPT + p];
-                    const T g3 = sg[3 * NPT + p], g4 = sg[4 * NPT + p], g5 = sg[5 * NPT + p];
+                    const T g0 = (T)sg[p], g1 = (T)sg[NPT + p], g2 = (T)sg[2 * NPT + p];
+                    const T g3 = (T)sg[3 * NPT + p], g4 = (T)sg[4 * NPT + p], g5 = (T)sg[5 * NPT + p];
                     svr[p] = g0 * ur + g3 * us + g4 * ut;
                     svs[p] = g3 * ur + g1 * us + g5 * ut;
                     rvt[k] = g4 * ur + g5 * us + g2 * ut;
@@ -356,18 +365,18 @@ __global__ void __launch_bounds__(ax_threads<N>())
 
 // ---------------------------------------------------------------- launch
 
-template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM>
-static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16>
+static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const void *G, double h1, double h2,
                        const DM &Dm, const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st) {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
     constexpr int threads = ax_threads<N>();
-    auto kern = ax_kernel<N, T, HELM, CG, AFF, DM>;
+    auto kern = ax_kernel<N, T, HELM, CG, AFF, DM, G16>;
     int dev_max = 0;
     SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
     const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, AFF, N);
     int nst = tune.nst < 1 ? 1 : (tune.nst > 3 ? 3 : tune.nst);
-    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG, AFF>(nst) > dev_max) --nst;
-    const int smem = ax_smem_bytes<N, T, HELM, CG, AFF>(nst);
+    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG, AFF, G16>(nst) > dev_max) --nst;
+    const int smem = ax_smem_bytes<N, T, HELM, CG, AFF, G16>(nst);
     if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
     SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
@@ -397,13 +406,13 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const T *G, double h
     return SEM_OK;
 }
 
-template <typename T, bool HELM, bool CG, typename DM, bool AFF = false>
-static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const T *G, double h1, double h2,
+template <typename T, bool HELM, bool CG, typename DM, bool AFF = false, bool G16 = false>
+static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const void *G, double h1, double h2,
                        const DM &Dm, const CgFuse<T> &cg, cudaStream_t st, const int *guard = nullptr,
                        int gval = 0) {
     switch (m->N) {
 #define SEM_AX_CASE(n) \
-    case n: return launch_ax_n<n, T, HELM, CG, AFF, DM>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st);
+    case n: return launch_ax_n<n, T, HELM, CG, AFF, DM, G16>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st);
         SEM_AX_CASE(1) SEM_AX_CASE(2) SEM_AX_CASE(3) SEM_AX_CASE(4) SEM_AX_CASE(5)
         SEM_AX_CASE(6) SEM_AX_CASE(7) SEM_AX_CASE(8) SEM_AX_CASE(9) SEM_AX_CASE(10) SEM_AX_CASE(11)
 #undef SEM_AX_CASE
@@ -424,6 +433,8 @@ int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) 
     const CgFuse<float> none{};
     if (m->aff32)
         return dispatch_ax<float, false, false, DMatF, true>(m, u, w, m->aff32, 1.0, 0.0, m->Df, none, st);
+    if (m->G16)
+        return dispatch_ax<float, false, false, DMatF, false, true>(m, u, w, m->G16, 1.0, 0.0, m->Df, none, st);
     return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st);
 }
 
@@ -437,6 +448,8 @@ int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaS
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
     if (m->aff32)
         return dispatch_ax<float, false, true, DMatF, true>(m, nullptr, w, m->aff32, 1.0, 0.0, m->Df, cg, st);
+    if (m->G16)
+        return dispatch_ax<float, false, true, DMatF, false, true>(m, nullptr, w, m->G16, 1.0, 0.0, m->Df, cg, st);
     return dispatch_ax<float, false, true>(m, nullptr, w, m->G32, 1.0, 0.0, m->Df, cg, st);
 }
 

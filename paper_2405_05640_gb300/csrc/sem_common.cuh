@@ -66,6 +66,7 @@ struct sem_mesh {
     float *G32;          // [E][6][npt] FP32 geometric factors, or nullptr
     float2 *G2;          // [E][6][npt] FP32-pair (hi, lo) geometric factors, or nullptr
     float *aff32;        // [E][4] affine elements: (a, b, c, 0), G_rr = rho_i rho_j rho_k a, ... or nullptr
+    void *G16;           // [E][6][npt] BF16 geometric factors for the FP32 operator, or nullptr
     double *B;           // [E][npt]
     double *mult;        // [nloc]
     double *minv;        // [nloc] 1/mult

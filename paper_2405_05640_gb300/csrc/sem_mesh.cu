@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "sem_common.cuh"
 
 namespace sem {
@@ -226,15 +228,17 @@ static int validate(const sem_mesh_desc *d) {
     int64_t E = (int64_t)d->nel[0] * d->nel[1] * d->nel[2];
     int64_t nloc = E * (d->N + 1) * (d->N + 1) * (d->N + 1);
     if (nloc >= (int64_t(1) << 31)) return fail(SEM_ERR_INVALID_ARG, "E*(N+1)^3 must be < 2^31");
-    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX | SEM_GEOM_PAIR | SEM_GEOM_AFFINE))
+    if (d->geom_flags & ~(SEM_GEOM_F32 | SEM_GEOM_RX | SEM_GEOM_PAIR | SEM_GEOM_AFFINE | SEM_GEOM_BF16))
         return fail(SEM_ERR_INVALID_ARG, "unknown geom_flags bit");
+    if ((d->geom_flags & SEM_GEOM_BF16) && !(d->geom_flags & SEM_GEOM_F32))
+        return fail(SEM_ERR_INVALID_ARG, "SEM_GEOM_BF16 needs SEM_GEOM_F32");
     if ((d->geom_flags & SEM_GEOM_AFFINE) && !(d->geom_flags & SEM_GEOM_F32))
         return fail(SEM_ERR_INVALID_ARG, "SEM_GEOM_AFFINE needs SEM_GEOM_F32");
     return SEM_OK;
 }
 
 struct Layout {
-    size_t verts, G, G32, G2, aff, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
+    size_t verts, G, G32, G2, aff, G16, B, mult, minv, dinv, dinv32, minv32, rx, idx, err, total;
 };
 
 static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
@@ -250,6 +254,7 @@ static Layout layout_for(const sem_mesh_desc *d, const GsCounts &c) {
     L.G32 = f32 ? take(sizeof(float) * E * 6 * npt) : 0;
     L.G2 = (d->geom_flags & SEM_GEOM_PAIR) ? take(sizeof(float2) * E * 6 * npt) : 0;
     L.aff = (d->geom_flags & SEM_GEOM_AFFINE) ? take(sizeof(float) * 4 * E) : 0;
+    L.G16 = (d->geom_flags & SEM_GEOM_BF16) ? take(sizeof(__nv_bfloat16) * E * 6 * npt) : 0;
     L.B = take(sizeof(double) * nloc);
     L.mult = take(sizeof(double) * nloc);
     L.minv = take(sizeof(double) * nloc);
@@ -401,6 +406,12 @@ __global__ void split_pair_kernel(const double *__restrict__ a, float2 *__restri
     }
 }
 
+// BF16 copy (round to nearest even) of the geometric factors.
+__global__ void to_bf16_kernel(const double *__restrict__ a, __nv_bfloat16 *__restrict__ b, int64_t n) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+        b[l] = __float2bfloat16_rn((float)a[l]);
+}
+
 __global__ void copy_f32_from_f64(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
         b[l] = (float)a[l];
@@ -502,6 +513,7 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     m->G32 = (d->geom_flags & SEM_GEOM_F32) ? reinterpret_cast<float *>(base + L.G32) : nullptr;
     m->G2 = (d->geom_flags & SEM_GEOM_PAIR) ? reinterpret_cast<float2 *>(base + L.G2) : nullptr;
     m->aff32 = (d->geom_flags & SEM_GEOM_AFFINE) ? reinterpret_cast<float *>(base + L.aff) : nullptr;
+    m->G16 = (d->geom_flags & SEM_GEOM_BF16) ? static_cast<void *>(base + L.G16) : nullptr;
     m->B = reinterpret_cast<double *>(base + L.B);
     m->mult = reinterpret_cast<double *>(base + L.mult);
     m->minv = reinterpret_cast<double *>(base + L.minv);
@@ -572,6 +584,11 @@ int sem_mesh_create(const sem_mesh_desc *d, void *ws, size_t bytes, void *stream
     CK(cudaGetLastError());
     if (m->G2) {
         split_pair_kernel<<<grid_for(m->E * 6 * m->npt), 256, 0, s>>>(m->G, m->G2, m->E * 6 * m->npt);
+        CK(cudaGetLastError());
+    }
+    if (m->G16) {
+        to_bf16_kernel<<<grid_for(m->E * 6 * m->npt), 256, 0, s>>>(m->G, static_cast<__nv_bfloat16 *>(m->G16),
+                                                                   m->E * 6 * m->npt);
         CK(cudaGetLastError());
     }
     // multiplicity = Q Q^T 1
