@@ -1,0 +1,97 @@
+"""Pins of the hybrid Schwarz oracle (oracle/schwarz.py): the fast-
+diagonalisation local solve against a dense solve of the SEM operator on the
+extended subdomain (exact on axis-aligned tensor-product meshes), symmetry and
+definiteness of the preconditioner, the coarse transfer pair, and the
+flexible PCG against the plain oracle solve."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import schwarz as sw
+from paper_2405_05640_gb300 import inputs
+
+
+def _dense(m):
+    """Assembled operator on the unique (global) nodes, by columns."""
+    n = m.nglob
+    first = np.zeros(n, dtype=np.int64)
+    first[m.gid[::-1]] = np.arange(m.nloc)[::-1]
+    A = np.zeros((n, n))
+    for c in range(n):
+        eg = np.zeros(n)
+        eg[c] = 1.0
+        A[:, c] = m.apply(eg[m.gid])[first]
+    return A
+
+
+STRETCH = inputs.BoxCase("stretch", 3, (3, 4, 3), (1, 0, 1), inputs.Y_FACES, lo=(0.0, -1.0, 0.0),
+                         hi=(2.0, 1.0, 1.5), tanh_beta=(0.0, 2.0, 0.0))
+
+
+def test_fdm_local_solve_equals_dense_subdomain_solve():
+    case = STRETCH
+    V = case.vertices()
+    S = sw.SchwarzFDM(case.N, case.nel, case.periodic, case.faces, V)
+    A = _dense(S.m)
+    rng = np.random.default_rng(3)
+    rg = rng.standard_normal(S.m.nglob)
+    for e in (0, 5, 17, S.m.E - 1):
+        g = S.gid_ext[e]
+        ok = g >= 0
+        ge = g[ok]
+        assert len(np.unique(ge)) == len(ge)
+        u_dense = np.linalg.solve(A[np.ix_(ge, ge)], rg[ge])
+        rext = np.where(ok, rg[np.where(ok, g, 0)], 0.0)
+        u = S.local_solve(e, rext)[ok]
+        assert np.abs(u - u_dense).max() <= 1e-11 * np.abs(u_dense).max()
+
+
+def test_preconditioner_symmetric_positive_definite():
+    case = inputs.deformed_cube(3, 4)
+    V = case.vertices()
+    H = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V)
+    m = H.m
+    rng = np.random.default_rng(5)
+    x = m.apply_mask(m.scatter(rng.standard_normal(m.nglob)))
+    y = m.apply_mask(m.scatter(rng.standard_normal(m.nglob)))
+    a, b = m.glsc3(x, H.apply(y)), m.glsc3(y, H.apply(x))
+    assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    assert m.glsc3(x, H.apply(x)) > 0 and m.glsc3(y, H.apply(y)) > 0
+
+
+def test_coarse_transfer_pair():
+    case = inputs.BoxCase("aff", 5, (2, 3, 2), (0, 0, 0), inputs.ALL_FACES, lo=(0.0, -1.0, 0.5), hi=(2.0, 1.0, 1.5))
+    V = case.vertices()
+    m = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    C = sw.CoarseLevel(case.N, case.nel, case.periodic, case.faces, V, m)
+    # prolongation reproduces trilinear (here: linear) functions exactly
+    xc_, yc_, zc_ = C.mc.xyz
+    f = lambda x, y, z: 0.7 * x - 1.3 * y + 0.4 * z + 2.0
+    pf = C.prolong(f(xc_, yc_, zc_).reshape(-1))
+    x, y, z = m.xyz
+    assert np.abs(pf - f(x, y, z).reshape(-1)).max() <= 1e-13
+    # restriction is its adjoint in the unique-node products
+    rng = np.random.default_rng(7)
+    r = m.scatter(rng.standard_normal(m.nglob))
+    xc = C.mc.scatter(rng.standard_normal(C.mc.nglob))
+    lhs = float(np.sum(C.prolong(xc) * r / m.mult))
+    rc = C.mc.dssum(np.einsum("ia,jb,kc,ekji->ecba", C.J1, C.J1, C.J1,
+                              (r / m.mult).reshape(m.E, case.N + 1, case.N + 1, case.N + 1)).reshape(-1))
+    rhs = float(np.sum(xc * rc / C.mc.mult))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("case", [inputs.channel(4, 5), inputs.deformed_cube(4, 5), STRETCH],
+                         ids=["channel4", "deformed4", "stretch"])
+def test_flexible_pcg_converges_faster_to_the_same_solution(case):
+    V = case.vertices()
+    H = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V)
+    m = H.m
+    b = m.scatter(case.rhs_global())
+    xo, itj, _, st = m.pcg(b, tol=1e-12, max_iter=20000)
+    x, its, rel = sw.fpcg(m, b, H.apply, tol=1e-12)
+    assert st == 0 and rel <= 1e-12
+    assert its <= 0.5 * itj, (its, itj)
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
