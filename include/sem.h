@@ -448,6 +448,36 @@ int sem_autotune_operator(const sem_mesh *mesh, int dtype, int fused_cg, void *d
 /* Back to the default launch shapes (2 stages, occupancy-limited). */
 int sem_autotune_reset(void);
 
+/* ---- Hybrid Schwarz preconditioner of the pressure solve ------------------
+ * Section 3.1: the pressure is solved with a Krylov method and a hybrid-
+ * Schwarz multigrid preconditioner (the SEM overlapping Schwarz / fast-
+ * diagonalisation method).  Two additive levels, symmetric, FP32:
+ *   z = sum_e R_e^T A_e^{-1} R_e r  +  P A_c^{-1} P^T r
+ * R_e: element e extended by one GLL point into each neighbour; A_e the
+ * separable operator of that subdomain (1-D stiffness and mass along each
+ * direction from the mean edge lengths of the element and its neighbours,
+ * homogeneous Dirichlet just beyond the overlap), inverted by fast
+ * diagonalisation (exact for axis-aligned tensor-product meshes); P the
+ * trilinear interpolation from the element vertices, A_c the N = 1 operator,
+ * solved by coarse_iters Jacobi-CG iterations to coarse_tol (0 iterations:
+ * no coarse level).
+ * mesh: 2 <= N <= 9, built with SEM_GEOM_F32; coarse: the N = 1 mesh of the
+ * same vertices and topology, built with SEM_GEOM_F32.  Set-up solves the
+ * 1-D eigenproblems on the host (cached by length and boundary type) and
+ * waits for `stream`.  The object keeps pointers to both meshes. */
+typedef struct sem_schwarz sem_schwarz;
+size_t sem_schwarz_workspace_bytes(const sem_mesh *mesh, const sem_mesh *coarse);
+int sem_schwarz_create(const sem_mesh *mesh, const sem_mesh *coarse, void *d_workspace, size_t bytes,
+                       void *stream, sem_schwarz **out);
+int sem_schwarz_destroy(sem_schwarz *sw);
+/* Number of distinct 1-D eigenproblems solved at set-up. */
+int sem_schwarz_problems(const sem_schwarz *sw);
+/* z = M r (device FP32 E-layout, r continuous and zero on Dirichlet nodes;
+ * z continuous, zero on Dirichlet nodes).  Stream-ordered, no host
+ * synchronisation (graph-capturable). */
+int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
+                      void *stream);
+
 /* ---- Performance model for splitting one problem over devices -----------
  * Section 4.1 (Eq. 2-7): a homogeneous cost C (here: element-iterations of a
  * solve) split over ndev devices; device i computes C_i at its best

@@ -143,6 +143,11 @@ _SIGS = {
     "sem_ns_dealias_bytes": ([_VP], ctypes.c_size_t),
     "sem_ns_set_scheme": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_ns_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_schwarz_workspace_bytes": ([_VP, _VP], ctypes.c_size_t),
+    "sem_schwarz_create": ([_VP, _VP, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "sem_schwarz_destroy": ([_VP], ctypes.c_int),
+    "sem_schwarz_problems": ([_VP], ctypes.c_int),
+    "sem_schwarz_apply": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP], ctypes.c_int),
     "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
                        ctypes.c_int),
 }
@@ -632,3 +637,34 @@ def perf_model(P_opt, C, C_max=None):
     check(lib().sem_perf_model(len(P), _VP(P.ctypes.data), None if cap is None else _VP(cap.ctypes.data),
                                float(C), ctypes.byref(t), _VP(out.ctypes.data)), "sem_perf_model")
     return t.value, out
+
+
+class Schwarz:
+    """sem_schwarz_*: the hybrid Schwarz preconditioner of `mesh` with the
+    N = 1 `coarse` mesh of the same vertices (both built with geom_f32)."""
+
+    def __init__(self, mesh: Mesh, coarse: Mesh):
+        import torch
+        self.mesh, self.coarse = mesh, coarse
+        n = lib().sem_schwarz_workspace_bytes(mesh.handle, coarse.handle)
+        self.workspace = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        check(lib().sem_schwarz_create(mesh.handle, coarse.handle, _VP(base), n, _stream(), ctypes.byref(h)),
+              "sem_schwarz_create")
+        self.handle = h
+        self.problems = lib().sem_schwarz_problems(h)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sem_schwarz_destroy(h)
+            self.handle = None
+
+    def apply(self, r, coarse_iters=0, coarse_tol=1e-3, z=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        check(lib().sem_schwarz_apply(self.handle, _ptr(r), _ptr(z), int(coarse_iters), float(coarse_tol), _stream()),
+              "sem_schwarz_apply")
+        return z
