@@ -234,6 +234,12 @@ typedef struct {
                               direction across FP64 refinements (the FP64 true
                               residual replaces the FP32 one, p is rescaled); 1
                               restarts the inner CG at every refinement */
+    const struct sem_schwarz *schwarz;  /* SEM_PCG_MIXED, Poisson: the inner FP32 solve
+                              is flexible CG preconditioned by this hybrid Schwarz
+                              object (see sem_schwarz_create; built on the same
+                              mesh), restarted at every refinement; NULL: Jacobi */
+    int coarse_iters;      /* Schwarz: coarse-level CG iterations per application */
+    double coarse_tol;     /* Schwarz: coarse-level relative tolerance (0 = 1e-2) */
 } sem_pcg_opts;
 
 typedef struct {

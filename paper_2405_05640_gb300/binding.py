@@ -51,7 +51,8 @@ class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_is_relative", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
-                ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int),
+                ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double)]
 
 
 class PcgStats(ctypes.Structure):
@@ -299,8 +300,12 @@ class Mesh:
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
-                 mixed_restart=False) -> PcgOpts:
+                 mixed_restart=False, schwarz=None, coarse_iters=20, coarse_tol=1e-2) -> PcgOpts:
+        """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
+        preconditioner of the mixed solver)."""
         o = PcgOpts()
+        o.schwarz = schwarz.handle.value if schwarz is not None else None
+        o.coarse_iters, o.coarse_tol = int(coarse_iters), float(coarse_tol)
         o.profile = int(bool(profile))
         o.mixed_restart = int(bool(mixed_restart))
         o.tol, o.tol_is_relative, o.max_iter, o.precision = float(tol), int(relative), int(max_iter), int(precision)

@@ -164,13 +164,16 @@ __global__ void __launch_bounds__(ax_threads<N>())
     const uint32_t ubytes = NPT * sizeof(T), gbytes = AFF ? 16 : 6 * NPT * sizeof(GT);
     const uint32_t bbytes = HELM ? NPT * sizeof(double) : 0;
 
+    // CG with dinv == nullptr: the preconditioned residual z comes in r and
+    // p <- z + beta p (general preconditioner); the dinv slab is not loaded
+    const bool jac = CG && cg.dinv != nullptr;
     auto stage_ptr = [&](int s) { return smem + s * SB; };
     auto issue = [&](int64_t e, int s) {
         unsigned char *st = stage_ptr(s);
-        mbar_arrive_expect_tx(&bar[s], NIN * ubytes + gbytes + bbytes);
+        mbar_arrive_expect_tx(&bar[s], NIN * ubytes + gbytes + bbytes - (CG && !jac ? ubytes : 0));
         if (CG) {
             bulk_g2s(st, cg.r + e * NPT, ubytes, &bar[s]);
-            bulk_g2s(st + ubytes, cg.dinv + e * NPT, ubytes, &bar[s]);
+            if (jac) bulk_g2s(st + ubytes, cg.dinv + e * NPT, ubytes, &bar[s]);
             bulk_g2s(st + 2 * ubytes, cg.p + e * NPT, ubytes, &bar[s]);
         } else {
             bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
             if (CG) {
                 for (int q = tid; q < NPT; q += blockDim.x) {
                     dst[q] = cg.r[e * NPT + q];
-                    dst[NPT + q] = cg.dinv[e * NPT + q];
+                    if (jac) dst[NPT + q] = cg.dinv[e * NPT + q];
                     dst[2 * NPT + q] = cg.p[e * NPT + q];
                 }
             } else {
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
 #pragma unroll
                 for (int k = 0; k < N1; ++k) {
                     const int q = i + N1 * (j + N1 * k);
-                    const T pn = fma(beta, su[q], sdi[q] * sr[q]);
+                    const T pn = fma(beta, su[q], jac ? sdi[q] * sr[q] : sr[q]);
                     su[q] = pn;
                     pe[q] = pn;
                 }

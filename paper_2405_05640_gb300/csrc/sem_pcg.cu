@@ -248,9 +248,13 @@ __device__ __forceinline__ void face_status(int e, int nel, int per, bool lo, in
 // then x += alpha p, r -= alpha w and the <r,r>, <r,z> partials with the
 // weight 1/mult computed from the point's position (a power of two, the same
 // value as the mesh's stored 1/mult).
-template <typename T, int N, bool VEC>
+// WRITEW: the assembled, masked w is also written to wout (the flexible CG of
+// a general preconditioner needs <z, A p> in the next iteration).  wout must
+// not be W.w: the x pass of this launch reads W.w's raw line ends.
+template <typename T, int N, bool VEC, bool WRITEW = false>
 __global__ void __launch_bounds__(kPThreads)
-    pcg_update_box_kernel(T *__restrict__ x, const T *__restrict__ dinv, BoxTopo B, PcgWork<T> W) {
+    pcg_update_box_kernel(T *__restrict__ x, const T *__restrict__ dinv, BoxTopo B, PcgWork<T> W,
+                          T *__restrict__ wout = nullptr) {
     if (W.scal->done) return;
     constexpr int N1 = N + 1, NL = N1 * N1, NPT = NL * N1;
     const T alpha = (T)W.scal->alpha;
@@ -296,10 +300,12 @@ __global__ void __launch_bounds__(kPThreads)
             const int sh = sx + sy + sz;
             const T mi = sh == 0 ? T(1) : (sh == 1 ? T(0.5) : (sh == 2 ? T(0.25) : T(0.125)));
             const T wt = dd ? T(0) : w[i];
+            if (WRITEW) w[i] = wt;
             update_point(alpha, p[i], wt, mi, di[i], xv[i], r[i], v, f0, f1);
         }
         store_line<T, N1, VEC>(x + base, xv);
         store_line<T, N1, VEC>(W.r + base, r);
+        if (WRITEW) store_line<T, N1, VEC>(wout + base, w);
     }
     if (sizeof(T) == 4) {
         v[0] = (double)f0;
@@ -327,28 +333,34 @@ __global__ void __launch_bounds__(kPThreads)
 }
 
 template <typename T, int N>
-static int launch_update_box_n(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st) {
+static int launch_update_box_n(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st,
+                               T *wout) {
+    const bool writew = wout != nullptr;
     constexpr int N1 = N + 1;
     const BoxTopo B = box_topo(m);
-    const bool vec = (N1 * sizeof(T)) % 16 == 0 && al16(x) && al16(dinv) && al16(W.p) && al16(W.w) && al16(W.r);
+    const bool vec = (N1 * sizeof(T)) % 16 == 0 && al16(x) && al16(dinv) && al16(W.p) && al16(W.w) && al16(W.r) &&
+                     (!writew || al16(wout));
     auto kv = pcg_update_box_kernel<T, N, ((N1 * sizeof(T)) % 16 == 0)>;
     auto ks = pcg_update_box_kernel<T, N, false>;
-    auto kern = vec ? kv : ks;
+    auto kvw = pcg_update_box_kernel<T, N, ((N1 * sizeof(T)) % 16 == 0), true>;
+    auto ksw = pcg_update_box_kernel<T, N, false, true>;
+    auto kern = writew ? (vec ? kvw : ksw) : (vec ? kv : ks);
     // one wave: every resident block takes an equal share of the lines
     int per_sm = 0;
     SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, 0));
     int grid = m->num_sms * (per_sm > 0 ? per_sm : 1);
     if (grid > kPBlocks) grid = kPBlocks;
-    kern<<<grid, kPThreads, 0, st>>>(x, dinv, B, W);
+    kern<<<grid, kPThreads, 0, st>>>(x, dinv, B, W, wout);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
 
 template <typename T>
-static int launch_update_box(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st) {
+static int launch_update_box(const sem_mesh *m, T *x, const T *dinv, const PcgWork<T> &W, cudaStream_t st,
+                             T *wout = nullptr) {
     switch (m->N) {
 #define SEM_UB_CASE(n) \
-    case n: return launch_update_box_n<T, n>(m, x, dinv, W, st);
+    case n: return launch_update_box_n<T, n>(m, x, dinv, W, st, wout);
         SEM_UB_CASE(1) SEM_UB_CASE(2) SEM_UB_CASE(3) SEM_UB_CASE(4) SEM_UB_CASE(5)
         SEM_UB_CASE(6) SEM_UB_CASE(7) SEM_UB_CASE(8) SEM_UB_CASE(9) SEM_UB_CASE(10) SEM_UB_CASE(11)
 #undef SEM_UB_CASE
@@ -441,7 +453,7 @@ static size_t pcg_scratch_f64(const sem_mesh *m) {
 
 // mixed: FP64 r, w; FP32 d, r, p, w; two partial blocks; two scalar blocks
 static size_t pcg_scratch_mixed(const sem_mesh *m) {
-    return align_up(sizeof(double) * m->nloc) * 2 + align_up(sizeof(float) * m->nloc) * 4 +
+    return align_up(sizeof(double) * m->nloc) * 2 + align_up(sizeof(float) * m->nloc) * 6 +
            2 * align_up(kPartialBytes) + 2 * align_up(sizeof(PcgScal));
 }
 
@@ -464,6 +476,8 @@ static PcgWork<double> carve_f64(const sem_mesh *m, void *scratch) {
 struct MixedWork {
     double *r64, *w64;
     float *d32;
+    float *z32;  // preconditioned residual (general preconditioner)
+    float *wa32; // assembled A p of the last iteration (general preconditioner)
     double *partial_out;
     PcgScal *scal_out;
     PcgWork<float> in;
@@ -481,7 +495,9 @@ static MixedWork carve_mixed(const sem_mesh *m, void *scratch) {
     M.in.r = reinterpret_cast<float *>(p + vf);
     M.in.p = reinterpret_cast<float *>(p + 2 * vf);
     M.in.w = reinterpret_cast<float *>(p + 3 * vf);
-    p += 4 * vf;
+    M.z32 = reinterpret_cast<float *>(p + 4 * vf);
+    M.wa32 = reinterpret_cast<float *>(p + 5 * vf);
+    p += 6 * vf;
     M.partial_out = reinterpret_cast<double *>(p);
     M.in.partial = reinterpret_cast<double *>(p + pb);
     p += 2 * pb;
@@ -586,6 +602,66 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
             s = launch_update_box<T>(m, x, dinv, W, st);
             if (s != SEM_OK) return s;
             c.launches += 3;
+            c.ax_launches += 1;
+        }
+    }
+    return SEM_OK;
+}
+
+// Flexible CG with a general preconditioner z = M r: rho = <r, z> and the
+// Polak-Ribiere beta = <z, r_new - r_old> / rho_old = -alpha <z, A p> / rho_old
+// (A p assembled in wa by the update; rho_old kept in rho_prev by the update).
+template <typename T>
+__global__ void __launch_bounds__(kPThreads)
+    fpcg_dots_kernel(const T *__restrict__ r, const T *__restrict__ z, const T *__restrict__ wa,
+                     const T *__restrict__ minv, int64_t n, PcgWork<T> W, int first) {
+    if (W.scal->done) return;
+    T f0 = T(0), f1 = T(0);
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const T mi = minv[l], zl = z[l];
+        f0 = fma(r[l] * zl, mi, f0);
+        if (!first) f1 = fma(wa[l] * zl, mi, f1);
+    }
+    double v[2] = {(double)f0, (double)f1}, t[2];
+    if (grid_reduce<2>(v, W.partial, &W.scal->cnt[0], t)) {
+        PcgScal *s = W.scal;
+        s->beta = first ? 0.0 : -s->alpha * t[1] / s->rho_prev;
+        s->rho = t[0];
+    }
+}
+
+// Inner FP32 flexible CG with the hybrid Schwarz preconditioner, after an
+// init kernel: per iteration z = M r, the dots, the fused operator with
+// p = z + beta p, the y/z gather-scatter, the update (x pass, mask; writes
+// the assembled A p); host check every `check` iterations.
+static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float *wa, float *x, const sem_schwarz *sw,
+                           int coarse_iters, double coarse_tol, int max_iter, int check, cudaStream_t st, SolveCtx &c,
+                           PcgScal *h) {
+    CgFuse<float> cg{z, nullptr, W.p, W.scal, W.partial + 4 * kPBlocks};
+    int launched = 0;
+    while (true) {
+        SEM_CUDA_CHECK(cudaMemcpyAsync(h, W.scal, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        c.tax.harvest();
+        c.tgs.harvest();
+        if (h->done || launched >= max_iter) break;
+        for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
+            int s = schwarz_apply_f32(sw, W.r, z, coarse_iters, coarse_tol, st);
+            if (s != SEM_OK) return s;
+            fpcg_dots_kernel<float><<<kPBlocks, kPThreads, 0, st>>>(W.r, z, wa, m->minv32, m->nloc, W,
+                                                                    launched == 0 ? 1 : 0);
+            SEM_CUDA_CHECK(cudaGetLastError());
+            c.tax.start(st);
+            s = ax_cg_launch_f32(m, cg, W.w, st);
+            c.tax.stop(st);
+            if (s != SEM_OK) return s;
+            c.tgs.start(st);
+            s = gs_yz_launch(m, W.w, SEM_F32, st);
+            c.tgs.stop(st);
+            if (s != SEM_OK) return s;
+            s = launch_update_box<float>(m, x, m->dinv32, W, st, wa);
+            if (s != SEM_OK) return s;
+            c.launches += 6;
             c.ax_launches += 1;
         }
     }
@@ -720,7 +796,8 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         // stagnation guard: the FP64 residual must keep falling
         if (prev_rr >= 0.0 && !(ho.rr < 0.25 * prev_rr)) break;
         prev_rr = ho.rr;
-        if (outer == 0 || o->mixed_restart) {
+        const sem_schwarz *sw = static_cast<const sem_schwarz *>(o->schwarz);
+        if (outer == 0 || o->mixed_restart || sw) {
             // inner FP32 solve of A d = r / ||r||, from d = 0
             SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
             pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
@@ -732,10 +809,15 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         }
         SEM_CUDA_CHECK(cudaGetLastError());
         cin.launches += 1;
-        int s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st,
-                               cin, &hi);
+        int s;
+        if (sw)
+            s = cg_loop_schwarz(m, M.in, M.z32, M.wa32, M.d32, sw, o->coarse_iters, o->coarse_tol > 0 ? o->coarse_tol : 1e-2,
+                                o->max_iter - inner_total, check, st, cin, &hi);
+        else
+            s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st, cin,
+                               &hi);
         if (s != SEM_OK) return s;
-        inner_total = o->mixed_restart ? inner_total + hi.iter : hi.iter;
+        inner_total = (o->mixed_restart || sw) ? inner_total + hi.iter : hi.iter;
         // x += ||r|| d; r = b - A x in FP64
         ir_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, M.d32, n, M.scal_out);
         s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
@@ -765,6 +847,10 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
 static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
     if (o->precision != SEM_PCG_F64 && o->precision != SEM_PCG_MIXED && o->precision != SEM_PCG_F64_PAIR)
         return fail(SEM_ERR_UNSUPPORTED, "unknown precision mode");
+    if (o->schwarz && o->precision != SEM_PCG_MIXED)
+        return fail(SEM_ERR_UNSUPPORTED, "the Schwarz preconditioner is used by SEM_PCG_MIXED");
+    if (o->schwarz && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
+        return fail(SEM_ERR_UNSUPPORTED, "the Schwarz preconditioner is built for the Poisson operator");
     if (o->precision == SEM_PCG_F64_PAIR && !m->G2)
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_F64_PAIR needs a mesh built with SEM_GEOM_PAIR");
     if (o->precision == SEM_PCG_F64_PAIR && (o->h2 != 0.0 || o->h1 != 1.0))
