@@ -230,14 +230,10 @@ int dealias_metric_launch(const sem_mesh *m, double *W, cudaStream_t st);
 int advect_weak_launch(const sem_mesh *m, const double *W, const double *const u[3], double *const out[3],
                        cudaStream_t st);
 
-// A fixed number of device-driven FP32 Jacobi-CG iterations from x = 0 (sem_pcg.cu).
-size_t fixed_cg_scratch_bytes(const sem_mesh *m);
-int fixed_cg_f32(const sem_mesh *m, const float *b, float *x, int iters, double rel_tol, void *scratch,
-                 cudaStream_t st);
-
-// Hybrid Schwarz preconditioner (sem_schwarz.cu): z = M r in FP32.
+// Hybrid Schwarz preconditioner (sem_schwarz.cu): z = M r in FP32; done
+// (optional device flag): set -> the kernels return at once.
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      cudaStream_t st);
+                      const int *done, cudaStream_t st);
 
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies

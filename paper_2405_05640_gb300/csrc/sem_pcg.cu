@@ -646,7 +646,7 @@ static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float 
         c.tgs.harvest();
         if (h->done || launched >= max_iter) break;
         for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
-            int s = schwarz_apply_f32(sw, W.r, z, coarse_iters, coarse_tol, st);
+            int s = schwarz_apply_f32(sw, W.r, z, coarse_iters, coarse_tol, &W.scal->done, st);
             if (s != SEM_OK) return s;
             fpcg_dots_kernel<float><<<kPBlocks, kPThreads, 0, st>>>(W.r, z, wa, m->minv32, m->nloc, W,
                                                                     launched == 0 ? 1 : 0);
@@ -664,40 +664,6 @@ static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float 
             c.launches += 6;
             c.ax_launches += 1;
         }
-    }
-    return SEM_OK;
-}
-
-// A fixed number of FP32 Jacobi-CG iterations on mesh m from x = 0 (device-
-// driven, no host synchronisation; iterations after convergence to rel_tol
-// return at once): the coarse solve of the Schwarz preconditioner.
-size_t fixed_cg_scratch_bytes(const sem_mesh *m) {
-    return align_up(sizeof(float) * m->nloc) * 3 + align_up(kPartialBytes) + align_up(sizeof(PcgScal));
-}
-
-int fixed_cg_f32(const sem_mesh *m, const float *b, float *x, int iters, double rel_tol, void *scratch,
-                 cudaStream_t st) {
-    char *q = static_cast<char *>(scratch);
-    const size_t vb = align_up(sizeof(float) * m->nloc);
-    PcgWork<float> W;
-    W.r = reinterpret_cast<float *>(q);
-    W.p = reinterpret_cast<float *>(q + vb);
-    W.w = reinterpret_cast<float *>(q + 2 * vb);
-    W.partial = reinterpret_cast<double *>(q + 3 * vb);
-    W.scal = reinterpret_cast<PcgScal *>(q + 3 * vb + align_up(kPartialBytes));
-    SEM_CUDA_CHECK(cudaMemsetAsync(W.scal, 0, sizeof(PcgScal), st));
-    SEM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(float) * m->nloc, st));
-    pcg_init_kernel<float, float><<<kPBlocks, kPThreads, 0, st>>>(b, nullptr, m->dinv32, m->minv32, m->nloc, W,
-                                                                  nullptr, rel_tol, 1, iters);
-    SEM_CUDA_CHECK(cudaGetLastError());
-    CgFuse<float> cg{W.r, m->dinv32, W.p, W.scal, W.partial + 4 * kPBlocks};
-    for (int q2 = 0; q2 < iters; ++q2) {
-        int s = ax_cg_launch_f32(m, cg, W.w, st);
-        if (s != SEM_OK) return s;
-        s = gs_yz_launch(m, W.w, SEM_F32, st);
-        if (s != SEM_OK) return s;
-        s = launch_update_box<float>(m, x, m->dinv32, W, st);
-        if (s != SEM_OK) return s;
     }
     return SEM_OK;
 }

@@ -20,12 +20,20 @@
 // GB300 design (FP32, the inner solver's precision): the 1-D eigenproblems
 // are solved once on the host (Cholesky + cyclic Jacobi) and cached by their
 // key (lengths and boundary flags: a tensor-product mesh has few distinct
-// ones); one CTA per element gathers the extended residual from its
-// neighbours with computed indices (box topology), applies the six 1-D
-// contractions through shared memory and writes the extended solution; a
-// second kernel assembles each point's value from the (up to 2 x 2 x 2)
-// overlapping subdomains in a fixed order (deterministic, copies identical,
-// no atomics).
+// ones).  One warp per element gathers the extended residual from its
+// neighbours with computed indices (box topology) into a padded shared block
+// (strides chosen so the lanes' line accesses meet few bank conflicts along
+// all three directions), each lane owning whole 1-D lines: a contraction
+// reads the lane's lines once and the table rows as broadcast 16-byte loads,
+// so shared traffic is ~1/3 of one load per multiply-add.  The same warp
+// restricts the residual to the element vertices.  The coarse problem is
+// assembled once into a 27-point stencil on the global vertex grid and solved
+// by one cooperative kernel (Jacobi-CG, two grid barriers per iteration, the
+// search direction double-buffered so the operator rebuilds it on the fly).
+// A last kernel, one CTA per element, sums each point's value over the (up
+// to 2 x 2 x 2) overlapping subdomains in a fixed order and adds the
+// trilinear prolongation of the coarse solution: deterministic, copies of a
+// node bit-identical, no atomics.
 
 #include <algorithm>
 #include <cmath>
@@ -38,18 +46,22 @@
 struct sem_schwarz {
     const sem_mesh *m, *mc;
     int N, ne, P;
+    int nv;        // coarse (global vertex) unknowns
     float *S;      // [P][ne][ne] eigenvectors S[l][a] (row l = point, column a = mode)
     float *L;      // [P][ne] eigenvalues
     int *prob;     // [E][3] problem id per element and axis
     float *uext;   // [E][ne^3] extended local solutions
-    float *rc, *xc;  // coarse right-hand side and solution (coarse E-layout)
-    void *cg_scratch;
+    float *rce;    // [E][8] element restrictions of r / mult to the vertices
+    float *sten;   // [27][nv] assembled coarse operator, offset (ox,oy,oz) -> (ox+1) + 3(oy+1) + 9(oz+1)
+    float *cdinv;  // [nv] inverse coarse diagonal (0 on Dirichlet vertices)
+    float *xc, *rcg, *pc0, *pc1, *wc;  // [nv] coarse CG vectors
+    double *partial;  // [2][kCgMaxGrid]
+    unsigned *bar;    // grid barrier counter
+    float *J1;        // [2][kMaxN1] J1[a][i] = (1 -+ xi_i) / 2
     size_t ws_bytes;
 };
 
 namespace sem {
-
-constexpr int kMaxNe = kMaxN1 + 2;
 
 // ---------------------------------------------------------------- host set-up
 
@@ -144,13 +156,52 @@ static long long qlen(double h) { return std::llround(std::log2(h) * 1024.0); }
 
 // ---------------------------------------------------------------- kernels
 
+constexpr int kSwWarps = 4;       // elements (one per warp) per CTA of the local solve
+constexpr int kCgThreads = 512;   // coarse CG CTA
+constexpr int kCgMaxGrid = 1024;  // coarse CG CTAs at most (one per SM)
+
 struct SwArgs {
-    int64_t E;
+    int E;
     int nel[3], per[3], faces;
 };
 
-// Along one axis: the (element offset, local index) of extended point I of an
-// element at coordinate c of n (valid = false outside the domain).
+// Global vertex grid of the box: nv[a] = nel[a] (periodic) or nel[a] + 1.
+struct CoarseTopo {
+    int nel[3], per[3], nv[3], faces;
+    int nvt;
+};
+
+// Extended-block geometry of order N: NE = N + 3 points per direction, LPT
+// lines per lane (NE^2 lines over 32 lanes), table rows padded to NEP, block
+// strides PJ (J) and PK (K) in floats.  The strides minimise the bank
+// conflicts of the lanes' line accesses summed over the three directions
+// (exhaustive search over PJ in [NE, NE+12), PK in [NE PJ, NE PJ + 40) with
+// at most 20% padding).
+template <int N>
+struct SwShape {
+    static constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
+    static constexpr int NE = N + 3, NE2 = NE * NE, NE3 = NE2 * NE;
+    static constexpr int LPT = (NE2 + 31) / 32;
+    static constexpr int NEP = (NE + 3) / 4 * 4;
+    static constexpr int PJ = N == 5 ? 9 : N == 9 ? 13 : NE;
+    static constexpr int PK = N == 2   ? 25
+                              : N == 3 ? 36
+                              : N == 4 ? 52
+                              : N == 5 ? 72
+                              : N == 6 ? 81
+                              : N == 7 ? 101
+                              : N == 8 ? 121
+                                       : 156;
+    static constexpr int TAB = 3 * NE * NEP;                 // one table set (3 axes)
+    static constexpr int LAM = (3 * NE + 3) / 4 * 4;
+    static constexpr int BUF = (PK * NE + 3) / 4 * 4;
+    static constexpr int OFF = (6 * NE + 3) / 4 * 4;           // 3 NE source offsets (int64)
+    static constexpr int WARP_FLOATS = 2 * TAB + LAM + BUF + OFF;  // per warp: S rows, S^T rows, eigenvalues, block, offsets
+    static_assert(PJ >= NE && PK >= PJ * NE, "block strides");
+};
+
+// Along one axis: the (element-coordinate offset, local index) of extended
+// point I of an element at coordinate c of n (false outside the domain).
 __device__ __forceinline__ bool ext_move(int I, int N, int c, int n, int per, int &dc, int &li) {
     if (I == 0) {
         if (c == 0 && !per) return false;
@@ -167,203 +218,713 @@ __device__ __forceinline__ bool ext_move(int I, int N, int c, int n, int per, in
     return true;
 }
 
+// 1/mult factor along one axis of local index i: 1/2 on a face shared with a
+// neighbour (or with itself across a periodic direction of one element).
+__device__ __forceinline__ float mult_fac(int i, int N, int c, int n, int per) {
+    return ((i == 0 && (c > 0 || per)) || (i == N && (c < n - 1 || per))) ? 0.5f : 1.f;
+}
+
+__device__ __forceinline__ float f4c(const float4 &v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float2 f4p(const float4 &v, int h) {
+    return h == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+}
+
+// acc[q][.] += row (NE entries, rw) * x[q] for the lane's LPT lines, outputs
+// in packed pairs (FP32x2 multiply-adds; a scalar tail when NE is odd).
+template <int NE, int NEP, int LPT>
+__device__ __forceinline__ void row_fma(float2 (&acc)[LPT][NE / 2], float (&tail)[LPT], const float4 (&rw)[NEP / 4],
+                                        const float (&x)[LPT]) {
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        const float2 xx = make_float2(x[q], x[q]);
+#pragma unroll
+        for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = __ffma2_rn(f4p(rw[a2 / 2], a2 & 1), xx, acc[q][a2]);
+        if (NE & 1) tail[q] = fmaf(f4c(rw[(NE - 1) / 4], (NE - 1) & 3), x[q], tail[q]);
+    }
+}
+
+template <int NE, int LPT>
+__device__ __forceinline__ float acc_at(const float2 (&acc)[LPT][NE / 2], const float (&tail)[LPT], int q, int a) {
+    return (NE & 1) && a == NE - 1 ? tail[q] : ((a & 1) ? acc[q][a / 2].y : acc[q][a / 2].x);
+}
+
+// The lane's lines of the warp's block along axis AX: (c1, c2) =
+// (L mod NE, L / NE), L = lane + 32 q; offsets into the block.
+template <int N, int AX>
+__device__ __forceinline__ void line_offsets(int lane, int (&off)[SwShape<N>::LPT], int (&c1)[SwShape<N>::LPT],
+                                             int (&c2)[SwShape<N>::LPT]) {
+    using S = SwShape<N>;
+#pragma unroll
+    for (int q = 0; q < S::LPT; ++q) {
+        const int L = lane + 32 * q;
+        c1[q] = L < S::NE2 ? L % S::NE : 0;
+        c2[q] = L < S::NE2 ? L / S::NE : 0;
+        off[q] = AX == 0 ? S::PJ * c1[q] + S::PK * c2[q] : AX == 1 ? c1[q] + S::PK * c2[q] : c1[q] + S::PJ * c2[q];
+    }
+}
+
+// One 1-D contraction of the warp's block along axis AX, each lane on its
+// lines: out[a] = sum_l tab[AX][l][a] in[l] (in place), tab the S rows
+// (forward: S^T along the line) or the S^T rows (backward: S).
+template <int N, int AX>
+__device__ __forceinline__ void sw_lines(float *buf, const float *tab, int lane) {
+    using S = SwShape<N>;
+    constexpr int NE = S::NE, LPT = S::LPT, NEP = S::NEP;
+    constexpr int ST = AX == 0 ? 1 : AX == 1 ? S::PJ : S::PK;
+    int off[LPT], c1[LPT], c2[LPT];
+    line_offsets<N, AX>(lane, off, c1, c2);
+    float2 acc[LPT][NE / 2];
+    float tail[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        tail[q] = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = make_float2(0.f, 0.f);
+    }
+    const float *t = tab + AX * NE * NEP;
+#pragma unroll
+    for (int l = 0; l < NE; ++l) {
+        float x[LPT];
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) x[q] = buf[off[q] + l * ST];
+        float4 rw[NEP / 4];
+#pragma unroll
+        for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(t + l * NEP)[c4];
+        row_fma<NE, NEP, LPT>(acc, tail, rw, x);
+    }
+#pragma unroll
+    for (int q = 0; q < LPT; ++q)
+        if (lane + 32 * q < S::NE2) {
+#pragma unroll
+            for (int a = 0; a < NE; ++a) buf[off[q] + a * ST] = acc_at<NE, LPT>(acc, tail, q, a);
+        }
+}
+
+// The K direction: forward (S_z^T), division by lx[c1] + ly[c2] + lz[c] (the
+// lines then indexed by modes), backward (S_z), all in registers.
 template <int N>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const float *tabT, const float *lam,
+                                         int lane) {
+    using S = SwShape<N>;
+    constexpr int NE = S::NE, LPT = S::LPT, NEP = S::NEP, ST = S::PK;
+    int off[LPT], c1[LPT], c2[LPT];
+    line_offsets<N, 2>(lane, off, c1, c2);
+    float2 acc[LPT][NE / 2];
+    float tail[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        tail[q] = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = make_float2(0.f, 0.f);
+    }
+    const float *tS = tabS + 2 * NE * NEP, *tT = tabT + 2 * NE * NEP;
+#pragma unroll
+    for (int l = 0; l < NE; ++l) {
+        float x[LPT];
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) x[q] = buf[off[q] + l * ST];
+        float4 rw[NEP / 4];
+#pragma unroll
+        for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(tS + l * NEP)[c4];
+        row_fma<NE, NEP, LPT>(acc, tail, rw, x);
+    }
+    float lq[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) lq[q] = lam[c1[q]] + lam[NE + c2[q]];
+    float2 out[LPT][NE / 2];
+    float otail[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        otail[q] = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < NE / 2; ++a2) out[q][a2] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < NE; ++c) {
+        const float lz = lam[2 * NE + c];
+        float x[LPT];
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) x[q] = __fdividef(acc_at<NE, LPT>(acc, tail, q, c), lq[q] + lz);
+        float4 rw[NEP / 4];
+#pragma unroll
+        for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(tT + c * NEP)[c4];
+        row_fma<NE, NEP, LPT>(out, otail, rw, x);
+    }
+#pragma unroll
+    for (int q = 0; q < LPT; ++q)
+        if (lane + 32 * q < S::NE2) {
+#pragma unroll
+            for (int a = 0; a < NE; ++a) buf[off[q] + a * ST] = acc_at<NE, LPT>(out, otail, q, a);
+        }
+}
+
+// Local solves: one warp per element.  uext[e] = A_e^{-1} R_e r on the
+// extended points ([K][J][I], NE^3); with rce, also the restriction
+// rce[e][a + 2b + 4c] = sum_ijk J1[a][i] J1[b][j] J1[c][k] r(i,j,k) / mult.
+// done (optional): a device flag; set -> return at once.
+template <int N>
+__global__ void __launch_bounds__(kSwWarps * 32, N <= 6 ? 5 : 4)
     schwarz_local_kernel(const float *__restrict__ r, const float *__restrict__ Stab, const float *__restrict__ Ltab,
-                         const int *__restrict__ prob, SwArgs A, float *__restrict__ uext) {
-    constexpr int N1 = N + 1, NE = N + 3, NE2 = NE * NE, NE3 = NE2 * NE, NPT = N1 * N1 * N1;
-    __shared__ float sS[3][NE * NE], sL[3][NE], sa[NE3], sb[NE3];
-    for (int64_t e = blockIdx.x; e < A.E; e += gridDim.x) {
-        __syncthreads();
-        const int ex = (int)(e % A.nel[0]), ey = (int)((e / A.nel[0]) % A.nel[1]),
-                  ez = (int)(e / ((int64_t)A.nel[0] * A.nel[1]));
-        for (int t = threadIdx.x; t < 3 * NE2; t += blockDim.x) {
-            const int a = t / NE2;
-            sS[a][t - a * NE2] = Stab[(int64_t)prob[e * 3 + a] * NE2 + (t - a * NE2)];
+                         const int *__restrict__ prob, const float *__restrict__ J1, SwArgs A,
+                         const int *__restrict__ done, float *__restrict__ uext, float *__restrict__ rce) {
+    using S = SwShape<N>;
+    constexpr int NE = S::NE, NE2 = S::NE2, NE3 = S::NE3, N1 = S::N1, NPT = S::NPT, NEP = S::NEP;
+    if (done && *done) return;
+    extern __shared__ float4 sw_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sS = reinterpret_cast<float *>(sw_smem) + warp * S::WARP_FLOATS;
+    float *sT = sS + S::TAB, *sL = sT + S::TAB, *buf = sL + S::LAM;
+    int64_t *sOff = reinterpret_cast<int64_t *>(buf + S::BUF);
+    constexpr int64_t kOut = INT64_MIN;  // source outside the domain
+    const int sy = A.nel[0], sz = A.nel[0] * A.nel[1];
+    for (int e = blockIdx.x * kSwWarps + warp; e < A.E; e += gridDim.x * kSwWarps) {
+        __syncwarp();
+        const int ex = e % A.nel[0], ey = (e / A.nel[0]) % A.nel[1], ez = e / sz;
+        const int pid[3] = {__ldg(prob + 3 * (int64_t)e), __ldg(prob + 3 * (int64_t)e + 1),
+                            __ldg(prob + 3 * (int64_t)e + 2)};
+        // per axis, the offset of each extended point's source in r (element
+        // offset x points per element + local stride), or kOut outside the domain
+        for (int t = lane; t < 3 * NE; t += 32) {
+            const int ax = t / NE, I = t - ax * NE;
+            const int c = ax == 0 ? ex : ax == 1 ? ey : ez;
+            const int n = ax == 0 ? A.nel[0] : ax == 1 ? A.nel[1] : A.nel[2];
+            const int per = ax == 0 ? A.per[0] : ax == 1 ? A.per[1] : A.per[2];
+            const int64_t es = ax == 0 ? 1 : ax == 1 ? sy : sz;
+            const int ls = ax == 0 ? 1 : ax == 1 ? N1 : N1 * N1;
+            int dc, li;
+            sOff[t] = ext_move(I, N, c, n, per, dc, li) ? (dc * es) * NPT + (int64_t)li * ls : kOut;
         }
-        for (int t = threadIdx.x; t < 3 * NE; t += blockDim.x) {
-            const int a = t / NE;
-            sL[a][t - a * NE] = Ltab[(int64_t)prob[e * 3 + a] * NE + (t - a * NE)];
-        }
-        // gather the extended residual
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int I = t % NE, J = (t / NE) % NE, K = t / NE2;
-            int dx, dy, dz, i, j, k;
-            float v = 0.f;
-            if (ext_move(I, N, ex, A.nel[0], A.per[0], dx, i) && ext_move(J, N, ey, A.nel[1], A.per[1], dy, j) &&
-                ext_move(K, N, ez, A.nel[2], A.per[2], dz, k)) {
-                const int64_t e2 = (ex + dx) + (int64_t)A.nel[0] * ((ey + dy) + (int64_t)A.nel[1] * (ez + dz));
-                v = r[e2 * NPT + i + N1 * (j + N1 * k)];
+        __syncwarp();
+        // the extended residual, kGB loads in flight per lane
+        constexpr int kIt = (NE3 + 31) / 32, kGB = 8;
+        const float *re = r + (int64_t)e * NPT;
+#pragma unroll 1
+        for (int t0 = 0; t0 < kIt; t0 += kGB) {
+            float v[kGB];
+#pragma unroll
+            for (int u = 0; u < kGB; ++u) {
+                const int t = lane + 32 * (t0 + u);
+                v[u] = 0.f;
+                if (t < NE3) {
+                    const int I = t % NE, J = (t / NE) % NE, K = t / NE2;
+                    const int64_t ox = sOff[I], oy = sOff[NE + J], oz = sOff[2 * NE + K];
+                    if (ox != kOut && oy != kOut && oz != kOut) v[u] = __ldg(re + (ox + oy + oz));
+                }
             }
-            sa[t] = v;
-        }
-        __syncthreads();
-        // forward: along I with Sx^T, J with Sy^T, K with Sz^T
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int a = t % NE, r0 = t - a;
-            float s = 0.f;
 #pragma unroll
-            for (int l = 0; l < NE; ++l) s = fmaf(sS[0][l * NE + a], sa[r0 + l], s);
-            sb[t] = s;
+            for (int u = 0; u < kGB; ++u) {
+                const int t = lane + 32 * (t0 + u);
+                if (t < NE3) buf[t % NE + S::PJ * ((t / NE) % NE) + S::PK * (t / NE2)] = v[u];
+            }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int I = t % NE, b = (t / NE) % NE, K = t / NE2;
-            float s = 0.f;
+        constexpr int kTt = (3 * NE2 + 31) / 32;
+        float tv[kTt];
 #pragma unroll
-            for (int l = 0; l < NE; ++l) s = fmaf(sS[1][l * NE + b], sb[K * NE2 + l * NE + I], s);
-            sa[t] = s;
+        for (int u = 0; u < kTt; ++u) {
+            const int t = lane + 32 * u;
+            if (t < 3 * NE2) {
+                const int a = t / NE2;
+                tv[u] = __ldg(Stab + (int64_t)(a == 0 ? pid[0] : a == 1 ? pid[1] : pid[2]) * NE2 + (t - a * NE2));
+            }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int IJ = t % NE2, c = t / NE2;
-            float s = 0.f;
+        constexpr int kLt = (3 * NE + 31) / 32;
+        float lv[kLt];
 #pragma unroll
-            for (int l = 0; l < NE; ++l) s = fmaf(sS[2][l * NE + c], sa[l * NE2 + IJ], s);
-            const int a = IJ % NE, b = IJ / NE;
-            sb[t] = s / (sL[0][a] + sL[1][b] + sL[2][c]);
+        for (int u = 0; u < kLt; ++u) {
+            const int t = lane + 32 * u;
+            if (t < 3 * NE) {
+                const int a = t / NE;
+                lv[u] = __ldg(Ltab + (int64_t)(a == 0 ? pid[0] : a == 1 ? pid[1] : pid[2]) * NE + (t - a * NE));
+            }
         }
-        __syncthreads();
-        // backward: along K with Sz, J with Sy, I with Sx
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int IJ = t % NE2, K = t / NE2;
-            float s = 0.f;
 #pragma unroll
-            for (int c = 0; c < NE; ++c) s = fmaf(sS[2][K * NE + c], sb[c * NE2 + IJ], s);
-            sa[t] = s;
+        for (int u = 0; u < kTt; ++u) {
+            const int t = lane + 32 * u;
+            if (t < 3 * NE2) {
+                const int a = t / NE2, q = t - a * NE2, l = q / NE, c = q - l * NE;
+                sS[(a * NE + l) * NEP + c] = tv[u];
+                sT[(a * NE + c) * NEP + l] = tv[u];
+            }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < kLt; ++u)
+            if (lane + 32 * u < 3 * NE) sL[lane + 32 * u] = lv[u];
+        __syncwarp();
+        if (rce) {
+            float c8[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) c8[v] = 0.f;
+            for (int jk = lane; jk < N1 * N1; jk += 32) {
+                const int j = jk % N1, k = jk / N1;
+                const float *row = buf + 1 + S::PJ * (j + 1) + S::PK * (k + 1);
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int i = 0; i < N1; ++i) {
+                    const float v = row[i] * mult_fac(i, N, ex, A.nel[0], A.per[0]);
+                    s0 = fmaf(__ldg(J1 + i), v, s0);
+                    s1 = fmaf(__ldg(J1 + kMaxN1 + i), v, s1);
+                }
+                const float wy = mult_fac(j, N, ey, A.nel[1], A.per[1]), wz = mult_fac(k, N, ez, A.nel[2], A.per[2]);
+                const float y0 = __ldg(J1 + j) * wy, y1 = __ldg(J1 + kMaxN1 + j) * wy;
+                const float z0 = __ldg(J1 + k) * wz, z1 = __ldg(J1 + kMaxN1 + k) * wz;
+                c8[0] = fmaf(s0, y0 * z0, c8[0]);
+                c8[1] = fmaf(s1, y0 * z0, c8[1]);
+                c8[2] = fmaf(s0, y1 * z0, c8[2]);
+                c8[3] = fmaf(s1, y1 * z0, c8[3]);
+                c8[4] = fmaf(s0, y0 * z1, c8[4]);
+                c8[5] = fmaf(s1, y0 * z1, c8[5]);
+                c8[6] = fmaf(s0, y1 * z1, c8[6]);
+                c8[7] = fmaf(s1, y1 * z1, c8[7]);
+            }
+            float mine = 0.f;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                float t = c8[v];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == v) mine = t;
+            }
+            if (lane < 8) rce[(int64_t)e * 8 + lane] = mine;
+            __syncwarp();
+        }
+        sw_lines<N, 0>(buf, sS, lane);
+        __syncwarp();
+        sw_lines<N, 1>(buf, sS, lane);
+        __syncwarp();
+        sw_kpass<N>(buf, sS, sT, sL, lane);
+        __syncwarp();
+        sw_lines<N, 1>(buf, sT, lane);
+        __syncwarp();
+        sw_lines<N, 0>(buf, sT, lane);
+        __syncwarp();
+        float *ue = uext + (int64_t)e * NE3;
+        for (int t = lane; t < NE3; t += 32) {
             const int I = t % NE, J = (t / NE) % NE, K = t / NE2;
-            float s = 0.f;
-#pragma unroll
-            for (int b = 0; b < NE; ++b) s = fmaf(sS[1][J * NE + b], sa[K * NE2 + b * NE + I], s);
-            sb[t] = s;
-        }
-        __syncthreads();
-        float *ue = uext + e * NE3;
-        for (int t = threadIdx.x; t < NE3; t += blockDim.x) {
-            const int I = t % NE, r0 = t - I;
-            float s = 0.f;
-#pragma unroll
-            for (int a = 0; a < NE; ++a) s = fmaf(sS[0][I * NE + a], sb[r0 + a], s);
-            ue[t] = s;
+            ue[t] = buf[I + S::PJ * J + S::PK * K];
         }
     }
 }
 
 // Along one axis: the subdomains covering local index i of an element at
-// coordinate c of n: (element offset, extended index), left to right.
-// (N = 2: the middle point is covered by all three.)
-__device__ __forceinline__ int cover(int i, int N, int c, int n, int per, int (&dc)[3], int (&I)[3]) {
-    int m = 0;
-    if (i <= 1 && (c > 0 || per)) {  // the left neighbour (its own point N, or its right extension)
-        dc[m] = c == 0 ? n - 1 : -1;
-        I[m++] = i + N + 1;
-    }
-    dc[m] = 0;
-    I[m++] = i + 1;
-    if (i >= N - 1 && (c < n - 1 || per)) {  // the right neighbour (its own point 0, or its left extension)
-        dc[m] = c == n - 1 ? -(n - 1) : 1;
-        I[m++] = i - N + 1;
-    }
-    return m;
+// coordinate c of n, in three slots left to right: the left neighbour (its
+// own point N, or its right extension), the element itself, the right
+// neighbour (its own point 0, or its left extension); each with its
+// element-coordinate offset and extended index.  (N = 2: the middle point is
+// covered by all three.)
+struct Cover {
+    bool l, r;
+    int dl, dr, Il, I0, Ir;
+};
+__device__ __forceinline__ Cover cover(int i, int N, int c, int n, int per) {
+    Cover v;
+    v.l = i <= 1 && (c > 0 || per);
+    v.dl = c == 0 ? n - 1 : -1;
+    v.Il = i + N + 1;
+    v.I0 = i + 1;
+    v.r = i >= N - 1 && (c < n - 1 || per);
+    v.dr = c == n - 1 ? -(n - 1) : 1;
+    v.Ir = i - N + 1;
+    return v;
+}
+__device__ __forceinline__ bool cov_ok(const Cover &v, int slot) { return slot == 0 ? v.l : slot == 1 ? true : v.r; }
+__device__ __forceinline__ int cov_d(const Cover &v, int slot) { return slot == 0 ? v.dl : slot == 1 ? 0 : v.dr; }
+__device__ __forceinline__ int cov_I(const Cover &v, int slot) { return slot == 0 ? v.Il : slot == 1 ? v.I0 : v.Ir; }
+
+__device__ __forceinline__ bool dirichlet_at(int i, int N, int c, int n, int per, int faces, int axis) {
+    return !per && ((i == 0 && c == 0 && ((faces >> (2 * axis)) & 1)) ||
+                    (i == N && c == n - 1 && ((faces >> (2 * axis + 1)) & 1)));
+}
+
+// Global vertex index of vertex (vx, vy, vz) in [0, nel] (periodic: nel wraps to 0).
+__device__ __forceinline__ int vertex_id(const CoarseTopo &C, int vx, int vy, int vz) {
+    if (C.per[0] && vx == C.nel[0]) vx = 0;
+    if (C.per[1] && vy == C.nel[1]) vy = 0;
+    if (C.per[2] && vz == C.nel[2]) vz = 0;
+    return vx + C.nv[0] * (vy + C.nv[1] * vz);
 }
 
 // z(e, i, j, k) = sum over the covering subdomains (z, then y, then x from
-// low to high position) of their extended solutions; 0 on Dirichlet nodes
-// (dinv = 0 there).  With add, z += that sum.
+// low to high position) of their extended solutions, plus (xc non-NULL) the
+// trilinear interpolation of the coarse solution (x, then y, then z: exact at
+// element faces, so copies stay identical); 0 on Dirichlet nodes.  One thread
+// per (i, j) column of an element, k unrolled: the x/y covers, their offsets
+// and the x/y interpolation are formed once per column.
 template <int N>
-__global__ void __launch_bounds__(256)
-    schwarz_sum_kernel(const float *__restrict__ uext, const float *__restrict__ dinv, SwArgs A,
-                       float *__restrict__ z) {
-    constexpr int N1 = N + 1, NE = N + 3, NE2 = NE * NE, NE3 = NE2 * NE, NPT = N1 * N1 * N1;
-    const int64_t n = A.E * NPT;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = l / NPT;
-        const int p = (int)(l - e * NPT);
-        const int i = p % N1, j = (p / N1) % N1, k = p / (N1 * N1);
-        const int ex = (int)(e % A.nel[0]), ey = (int)((e / A.nel[0]) % A.nel[1]),
-                  ez = (int)(e / ((int64_t)A.nel[0] * A.nel[1]));
-        int dx[3], Ix[3], dy[3], Iy[3], dz[3], Iz[3];
-        const int mx = cover(i, N, ex, A.nel[0], A.per[0], dx, Ix);
-        const int my = cover(j, N, ey, A.nel[1], A.per[1], dy, Iy);
-        const int mz = cover(k, N, ez, A.nel[2], A.per[2], dz, Iz);
-        float s = 0.f;
-        for (int c = 0; c < mz; ++c)
-            for (int b = 0; b < my; ++b)
-                for (int a = 0; a < mx; ++a) {
-                    const int64_t e2 = (ex + dx[a]) + (int64_t)A.nel[0] * ((ey + dy[b]) + (int64_t)A.nel[1] * (ez + dz[c]));
-                    s += uext[e2 * NE3 + Ix[a] + NE * (Iy[b] + NE * Iz[c])];
+constexpr int sum_epb() {  // elements per 256-thread CTA
+    return 256 / ((N + 1) * (N + 1));
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 3)
+    schwarz_sum_kernel(const float *__restrict__ uext, const float *__restrict__ xc, const float *__restrict__ J1,
+                       SwArgs A, CoarseTopo C, const int *__restrict__ done, float *__restrict__ z) {
+    constexpr int N1 = N + 1, NE = N + 3, NE3 = NE * NE * NE, NPT = N1 * N1 * N1, COLS = N1 * N1;
+    constexpr int EPB = sum_epb<N>();
+    if (done && *done) return;
+    __shared__ float sx[EPB][8];
+    const int sy = A.nel[0], sz = A.nel[0] * A.nel[1];
+    const int el = threadIdx.x / COLS, col = threadIdx.x - el * COLS;
+    const int i = col % N1, j = col / N1;
+    for (int e0 = blockIdx.x * EPB; e0 < A.E; e0 += gridDim.x * EPB) {
+        const int e = e0 + el;
+        const bool live = el < EPB && e < A.E;
+        const int ex = e % A.nel[0], ey = (e / A.nel[0]) % A.nel[1], ez = e / sz;
+        if (xc) {
+            __syncthreads();
+            if (live && col < 8)
+                sx[el][col] = __ldcg(xc + vertex_id(C, ex + (col & 1), ey + ((col >> 1) & 1), ez + (col >> 2)));
+            __syncthreads();
+        }
+        if (!live) continue;
+        const bool dxy = dirichlet_at(i, N, ex, A.nel[0], A.per[0], A.faces, 0) ||
+                         dirichlet_at(j, N, ey, A.nel[1], A.per[1], A.faces, 1);
+        const Cover cx = cover(i, N, ex, A.nel[0], A.per[0]);
+        const Cover cy = cover(j, N, ey, A.nel[1], A.per[1]);
+        // x/y slot pairs (b outer, a inner): validity and offset
+        bool okxy[9];
+        int64_t oxy[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                okxy[3 * b + a] = cov_ok(cy, b) && cov_ok(cx, a);
+                oxy[3 * b + a] = (int64_t)(cov_d(cx, a) + sy * cov_d(cy, b)) * NE3 + cov_I(cx, a) + NE * cov_I(cy, b);
+            }
+        float u0 = 0.f, u1 = 0.f;
+        if (xc) {
+            const float jx0 = __ldg(J1 + i), jx1 = __ldg(J1 + kMaxN1 + i);
+            const float jy0 = __ldg(J1 + j), jy1 = __ldg(J1 + kMaxN1 + j);
+            const float *v = sx[el];
+            const float t00 = fmaf(jx0, v[0], jx1 * v[1]), t10 = fmaf(jx0, v[2], jx1 * v[3]);
+            const float t01 = fmaf(jx0, v[4], jx1 * v[5]), t11 = fmaf(jx0, v[6], jx1 * v[7]);
+            u0 = fmaf(jy0, t00, jy1 * t10);
+            u1 = fmaf(jy0, t01, jy1 * t11);
+        }
+        const float *ue = uext + (int64_t)e * NE3;
+        float *ze = z + (int64_t)e * NPT + col;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const Cover cz = cover(k, N, ez, A.nel[2], A.per[2]);
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (cov_ok(cz, c)) {
+                    const int64_t oz = (int64_t)(sz * cov_d(cz, c)) * NE3 + NE * NE * cov_I(cz, c);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        if (okxy[q]) s += __ldg(ue + oz + oxy[q]);
                 }
-        z[l] = dinv[l] != 0.f ? s : 0.f;
+            if (xc) s += fmaf(__ldg(J1 + k), u0, __ldg(J1 + kMaxN1 + k) * u1);
+            const bool dz = dirichlet_at(k, N, ez, A.nel[2], A.per[2], A.faces, 2);
+            ze[k * COLS] = (dxy || dz) ? 0.f : s;
+        }
     }
 }
 
-// Coarse restriction rc[e][c][b][a] = sum_ijk J1[i][a] J1[j][b] J1[k][c] r(i,j,k) / mult,
-// J1[i] = ((1 - xi_i)/2, (1 + xi_i)/2); one thread per (element, vertex).
-struct J1Tab {
-    float j[kMaxN1][2];
+// ---------------------------------------------------------------- coarse level
+
+// Element matrices of the N = 1 operator from its FP64 geometric factors
+// G[e][6][8] (rr, ss, tt, rs, rt, st at the 8 vertices, quadrature weights
+// included): Ae[e][p][j] = sum_q grad phi_p(q) . G(q) grad phi_j(q), with
+// d phi_j / dr at vertex q = +-1/2 where q agrees with j off that axis.
+__global__ void coarse_elem_kernel(const double *__restrict__ G, int E, float *__restrict__ Ae) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)E * 8;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / 8;
+        const int j = (int)(t - e * 8);
+        const double *Ge = G + e * 48;
+        double col[8] = {};
+        for (int q = 0; q < 8; ++q) {
+            double gj[3];
+            for (int a = 0; a < 3; ++a) {
+                const int mask = 7 & ~(1 << a);
+                gj[a] = ((q ^ j) & mask) ? 0.0 : (((j >> a) & 1) ? 0.5 : -0.5);
+            }
+            const double grr = Ge[q], gss = Ge[8 + q], gtt = Ge[16 + q], grs = Ge[24 + q], grt = Ge[32 + q],
+                         gst = Ge[40 + q];
+            const double v0 = grr * gj[0] + grs * gj[1] + grt * gj[2];
+            const double v1 = grs * gj[0] + gss * gj[1] + gst * gj[2];
+            const double v2 = grt * gj[0] + gst * gj[1] + gtt * gj[2];
+            for (int p = 0; p < 8; ++p) {
+                double gp[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int mask = 7 & ~(1 << a);
+                    gp[a] = ((q ^ p) & mask) ? 0.0 : (((p >> a) & 1) ? 0.5 : -0.5);
+                }
+                col[p] += gp[0] * v0 + gp[1] * v1 + gp[2] * v2;
+            }
+        }
+        for (int p = 0; p < 8; ++p) Ae[e * 64 + p * 8 + j] = (float)col[p];
+    }
+}
+
+__device__ __forceinline__ bool vertex_masked(const CoarseTopo &C, int v, int a) {
+    return !C.per[a] && ((v == 0 && ((C.faces >> (2 * a)) & 1)) || (v == C.nv[a] - 1 && ((C.faces >> (2 * a + 1)) & 1)));
+}
+
+// Neighbour coordinate v + o along an axis (periodic wrap); -1 outside.
+__device__ __forceinline__ int nb_coord(int v, int o, int nv, int per) {
+    int w = v + o;
+    if (per) w = (w + nv) % nv;
+    return (w < 0 || w >= nv) ? -1 : w;
+}
+
+// Element coordinate of the element holding vertex coordinate v at local
+// vertex s (0 or 1); -1 if none.
+__device__ __forceinline__ int elem_coord(int v, int s, int nel, int per) {
+    int c = v - s;
+    if (per) c = (c + nel) % nel;
+    return (c < 0 || c >= nel) ? -1 : c;
+}
+
+// The assembled coarse operator as a 27-point stencil per vertex:
+// sten[o][v] = sum over the (up to 8) elements e holding v at local vertex s
+// (s in a fixed order) of Ae[e][s][s + o] for s + o in {0,1}^3 (periodic
+// aliases included); rows and columns of Dirichlet vertices zeroed; cdinv the
+// inverse of the assembled diagonal (0 on Dirichlet vertices).
+__global__ void coarse_stencil_kernel(const float *__restrict__ Ae, CoarseTopo C, float *__restrict__ sten,
+                                      float *__restrict__ cdinv) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < C.nvt; v += gridDim.x * blockDim.x) {
+        const int vc[3] = {v % C.nv[0], (v / C.nv[0]) % C.nv[1], v / (C.nv[0] * C.nv[1])};
+        const bool mv = vertex_masked(C, vc[0], 0) || vertex_masked(C, vc[1], 1) || vertex_masked(C, vc[2], 2);
+        double diag = 0.0;
+        for (int o = 0; o < 27; ++o) {
+            const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+            int nc[3];
+            bool ok = true, mn = false;
+            for (int a = 0; a < 3; ++a) {
+                nc[a] = nb_coord(vc[a], od[a], C.nv[a], C.per[a]);
+                ok = ok && nc[a] >= 0;
+            }
+            double sum = 0.0;
+            if (ok) {
+                for (int a = 0; a < 3; ++a) mn = mn || vertex_masked(C, nc[a], a);
+                for (int s = 0; s < 8; ++s) {
+                    const int sd[3] = {s & 1, (s >> 1) & 1, s >> 2};
+                    int ec[3], td = 0;
+                    bool in = true;
+                    for (int a = 0; a < 3; ++a) {
+                        ec[a] = elem_coord(vc[a], sd[a], C.nel[a], C.per[a]);
+                        const int ta = sd[a] + od[a];
+                        in = in && ec[a] >= 0 && ta >= 0 && ta <= 1;
+                        td |= (ta & 1) << a;
+                    }
+                    if (!in) continue;
+                    const int64_t e = ec[0] + (int64_t)C.nel[0] * (ec[1] + (int64_t)C.nel[1] * ec[2]);
+                    sum += Ae[e * 64 + s * 8 + td];
+                }
+                const int nbv = nc[0] + C.nv[0] * (nc[1] + C.nv[1] * nc[2]);
+                if (nbv == v) diag += sum;
+            }
+            sten[(int64_t)o * C.nvt + v] = (ok && !mv && !mn) ? (float)sum : 0.f;
+        }
+        cdinv[v] = (mv || !(diag > 0.0)) ? 0.f : (float)(1.0 / diag);
+    }
+}
+
+struct CoarseArgs {
+    const float *sten, *cdinv, *rce;
+    float *x, *r, *p0, *p1, *w;
+    double *partial;  // [2][kCgMaxGrid]
+    unsigned *bar;
+    int *err;
+    const int *done;
+    CoarseTopo C;
+    int iters;
+    double tol2;
 };
 
-template <int N>
-__global__ void restrict_kernel(const float *__restrict__ r, const float *__restrict__ minv, J1Tab J, int64_t E,
-                                float *__restrict__ rc) {
-    constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < E * 8; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = t / 8;
-        const int v = (int)(t - e * 8), a = v & 1, b = (v >> 1) & 1, c = v >> 2;
-        const float *re = r + e * NPT, *me = minv + e * NPT;
-        float s = 0.f;
-        for (int k = 0; k < N1; ++k)
-            for (int j = 0; j < N1; ++j) {
-                const float wjk = J.j[j][b] * J.j[k][c];
-                float si = 0.f;
-#pragma unroll
-                for (int i = 0; i < N1; ++i) {
-                    const int q = i + N1 * (j + N1 * k);
-                    si = fmaf(J.j[i][a], re[q] * me[q], si);
-                }
-                s = fmaf(wjk, si, s);
+// Grid barrier of the cooperative coarse kernel: arrival counter, bounded
+// wait (1 s of global time; another CTA's give-up ends it at once).  Returns
+// false when the wait gave up (error word set).
+__device__ __forceinline__ bool cg_grid_sync(unsigned *bar, unsigned target, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        uint64_t t0 = 0;
+        while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (*reinterpret_cast<volatile int *>(err) != 0) {
+                good = 0;
+                break;
             }
-        rc[t] = s;
+            const uint64_t t = global_timer_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > 1000000000ull) {
+                atomicCAS(err, 0, kDevTimeoutFlag);
+                good = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok = good;
     }
+    __syncthreads();
+    return ok != 0;
 }
 
-// z += P xc (trilinear interpolation of the element's vertex values)
-template <int N>
-__global__ void prolong_add_kernel(const float *__restrict__ xc, J1Tab J, int64_t E, float *__restrict__ z) {
-    constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < E * NPT; l += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = l / NPT;
-        const int p = (int)(l - e * NPT);
-        const int i = p % N1, j = (p / N1) % N1, k = p / (N1 * N1);
-        const float *x = xc + e * 8;
-        float s = 0.f;
+// Block sum of v into partial[blockIdx.x]; after the barrier every CTA sums
+// the partials in the same fixed order (identical totals everywhere).
+__device__ __forceinline__ void cg_block_partial(double v, double *partial) {
+    __shared__ double sh[kCgThreads / 32];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) s = fmaf(J.j[i][v & 1] * J.j[j][(v >> 1) & 1] * J.j[k][v >> 2], x[v], s);
-        z[l] += s;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kCgThreads / 32; ++k) t += sh[k];
+        __stcg(partial + blockIdx.x, t);
     }
 }
 
-static size_t sw_layout(const sem_mesh *m, const sem_mesh *mc, size_t *off) {
+__device__ __forceinline__ double cg_total(const double *partial) {
+    __shared__ double tot;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) t += __ldcg(partial + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) tot = t;
+    }
+    __syncthreads();
+    const double v = tot;
+    __syncthreads();
+    return v;
+}
+
+// The coarse solve A_c x = b, b assembled from the element restrictions,
+// x0 = 0, up to `iters` Jacobi-CG iterations or rz <= tol2 rz0.  Per
+// iteration: (1) p_new = cdinv r + beta p_old for the owned vertices and
+// w = A_c p_new, the neighbours' p_new rebuilt from their r and p_old (no
+// barrier between the two), <p, w>; (2) x, r update, <r, cdinv r>.  Two grid
+// barriers per iteration.  Cooperative launch, grid <= one CTA per SM.
+__global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
+    if (P.done && *P.done) return;
+    const CoarseTopo &C = P.C;
+    const int nvt = C.nvt;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned nbar = 0;
+    // b = sum over the elements holding v (fixed order) of their restriction
+    double part = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvt; v += stride) {
+        const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
+        float b = 0.f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int ex = elem_coord(vx, s & 1, C.nel[0], C.per[0]);
+            const int ey = elem_coord(vy, (s >> 1) & 1, C.nel[1], C.per[1]);
+            const int ez = elem_coord(vz, s >> 2, C.nel[2], C.per[2]);
+            if (ex < 0 || ey < 0 || ez < 0) continue;
+            b += __ldg(P.rce + (ex + (int64_t)C.nel[0] * (ey + (int64_t)C.nel[1] * ez)) * 8 + s);
+        }
+        const float di = __ldg(P.cdinv + v);
+        if (di == 0.f) b = 0.f;
+        __stcg(P.r + v, b);
+        __stcg(P.x + v, 0.f);
+        __stcg(P.p0 + v, 0.f);
+        part += (double)b * (double)(di * b);
+    }
+    cg_block_partial(part, P.partial);
+    if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+    double rz = cg_total(P.partial);
+    const double rz0 = rz;
+    float beta = 0.f;
+    float *pold = P.p0, *pnew = P.p1;
+    for (int it = 0; it < P.iters; ++it) {
+        if (!(rz > P.tol2 * rz0)) break;
+        part = 0.0;
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvt; v += stride) {
+            const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
+            int nx[3], ny[3], nz[3];
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                nx[o] = nb_coord(vx, o - 1, C.nv[0], C.per[0]);
+                ny[o] = nb_coord(vy, o - 1, C.nv[1], C.per[1]);
+                nz[o] = nb_coord(vz, o - 1, C.nv[2], C.per[2]);
+            }
+            float w = 0.f;
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                const int a = nx[o % 3], b = ny[(o / 3) % 3], c = nz[o / 9];
+                if (a < 0 || b < 0 || c < 0) continue;
+                const int q = a + C.nv[0] * (b + C.nv[1] * c);
+                const float pq = fmaf(beta, __ldcg(pold + q), __ldg(P.cdinv + q) * __ldcg(P.r + q));
+                w = fmaf(__ldg(P.sten + (int64_t)o * nvt + v), pq, w);
+            }
+            const float pv = fmaf(beta, __ldcg(pold + v), __ldg(P.cdinv + v) * __ldcg(P.r + v));
+            __stcg(pnew + v, pv);
+            __stcg(P.w + v, w);
+            part += (double)pv * (double)w;
+        }
+        cg_block_partial(part, P.partial);
+        if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+        const double pw = cg_total(P.partial);
+        const float alpha = pw != 0.0 ? (float)(rz / pw) : 0.f;
+        part = 0.0;
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvt; v += stride) {
+            const float pv = __ldcg(pnew + v), wv = __ldcg(P.w + v);
+            __stcg(P.x + v, fmaf(alpha, pv, __ldcg(P.x + v)));
+            const float rv = fmaf(-alpha, wv, __ldcg(P.r + v));
+            __stcg(P.r + v, rv);
+            part += (double)rv * (double)(__ldg(P.cdinv + v) * rv);
+        }
+        cg_block_partial(part, P.partial + kCgMaxGrid);
+        if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+        const double rzn = cg_total(P.partial + kCgMaxGrid);
+        beta = rz != 0.0 ? (float)(rzn / rz) : 0.f;
+        rz = rzn;
+        float *t = pold;
+        pold = pnew;
+        pnew = t;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+static CoarseTopo coarse_topo(const sem_mesh *m) {
+    CoarseTopo C;
+    C.nvt = 1;
+    for (int a = 0; a < 3; ++a) {
+        C.nel[a] = m->nel[a];
+        C.per[a] = m->periodic[a];
+        C.nv[a] = m->nel[a] + (m->periodic[a] ? 0 : 1);
+        C.nvt *= C.nv[a];
+    }
+    C.faces = m->faces;
+    return C;
+}
+
+static size_t sw_layout(const sem_mesh *m, size_t *off) {
     const int ne = m->N + 3;
     const size_t P = 3 * (size_t)m->E;  // upper bound: every element and axis distinct
+    const size_t nv = (size_t)coarse_topo(m).nvt;
     size_t o = 0;
     auto take = [&](size_t b) { size_t at = o; o = align_up(o + b); return at; };
     off[0] = take(sizeof(float) * P * ne * ne);
     off[1] = take(sizeof(float) * P * ne);
     off[2] = take(sizeof(int) * 3 * m->E);
-    off[3] = take(sizeof(float) * (size_t)m->E * ne * ne * ne);
-    off[4] = take(sizeof(float) * mc->nloc);
-    off[5] = take(sizeof(float) * mc->nloc);
-    off[6] = take(fixed_cg_scratch_bytes(mc));
+    off[3] = take(sizeof(float) * (size_t)m->E * ne * ne * ne);  // also the element matrices at set-up
+    off[4] = take(sizeof(float) * 8 * (size_t)m->E);
+    off[5] = take(sizeof(float) * 27 * nv);
+    for (int q = 6; q < 12; ++q) off[q] = take(sizeof(float) * nv);
+    off[12] = take(sizeof(double) * 2 * kCgMaxGrid);
+    off[13] = take(sizeof(unsigned) * 4);
+    off[14] = take(sizeof(float) * 2 * kMaxN1);
     return o;
 }
 
 static SwArgs sw_args(const sem_mesh *m) {
     SwArgs A;
-    A.E = m->E;
+    A.E = (int)m->E;
     for (int a = 0; a < 3; ++a) {
         A.nel[a] = m->nel[a];
         A.per[a] = m->periodic[a];
@@ -374,41 +935,66 @@ static SwArgs sw_args(const sem_mesh *m) {
 
 template <int N>
 static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      cudaStream_t st) {
+                      const int *done, cudaStream_t st) {
+    using S = SwShape<N>;
     const sem_mesh *m = sw->m;
     const SwArgs A = sw_args(m);
-    int64_t g = m->E;
-    if (g > (int64_t)m->num_sms * 8) g = (int64_t)m->num_sms * 8;
-    schwarz_local_kernel<N><<<(int)g, 256, 0, st>>>(r, sw->S, sw->L, sw->prob, A, sw->uext);
-    SEM_CUDA_CHECK(cudaGetLastError());
-    int64_t gp = (m->nloc + 255) / 256;
-    if (gp > (int64_t)m->num_sms * 32) gp = (int64_t)m->num_sms * 32;
-    schwarz_sum_kernel<N><<<(int)gp, 256, 0, st>>>(sw->uext, m->dinv32, A, z);
-    SEM_CUDA_CHECK(cudaGetLastError());
-    if (coarse_iters > 0) {
-        J1Tab J{};
-        for (int i = 0; i <= m->N; ++i) {
-            J.j[i][0] = (float)(0.5 * (1.0 - m->xi[i]));
-            J.j[i][1] = (float)(0.5 * (1.0 + m->xi[i]));
-        }
-        int64_t gc = (m->E * 8 + 255) / 256;
-        restrict_kernel<N><<<(int)gc, 256, 0, st>>>(r, m->minv32, J, m->E, sw->rc);
-        SEM_CUDA_CHECK(cudaGetLastError());
-        int s = gs_launch(sw->mc, sw->rc, SEM_F32, kGsSumMask, st);
-        if (s != SEM_OK) return s;
-        s = fixed_cg_f32(sw->mc, sw->rc, sw->xc, coarse_iters, coarse_tol, sw->cg_scratch, st);
-        if (s != SEM_OK) return s;
-        prolong_add_kernel<N><<<(int)gp, 256, 0, st>>>(sw->xc, J, m->E, z);
-        SEM_CUDA_CHECK(cudaGetLastError());
+    const bool coarse = coarse_iters > 0;
+    const size_t smem = sizeof(float) * kSwWarps * S::WARP_FLOATS;
+    static int per_sm = 0;  // resident CTAs per SM of this instantiation (device-independent shape)
+    if (per_sm == 0) {
+        SEM_CUDA_CHECK(cudaFuncSetAttribute(schwarz_local_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_local_kernel<N>,
+                                                                     kSwWarps * 32, smem));
+        if (per_sm < 1) per_sm = 1;
     }
+    int64_t g = (m->E + kSwWarps - 1) / kSwWarps;
+    if (g > (int64_t)m->num_sms * per_sm) g = (int64_t)m->num_sms * per_sm;
+    schwarz_local_kernel<N><<<(int)g, kSwWarps * 32, smem, st>>>(r, sw->S, sw->L, sw->prob, sw->J1, A, done,
+                                                                  sw->uext, coarse ? sw->rce : nullptr);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    const CoarseTopo C = coarse_topo(m);
+    if (coarse) {
+        SEM_CUDA_CHECK(cudaMemsetAsync(sw->bar, 0, sizeof(unsigned), st));
+        CoarseArgs P;
+        P.sten = sw->sten;
+        P.cdinv = sw->cdinv;
+        P.rce = sw->rce;
+        P.x = sw->xc;
+        P.r = sw->rcg;
+        P.p0 = sw->pc0;
+        P.p1 = sw->pc1;
+        P.w = sw->wc;
+        P.partial = sw->partial;
+        P.bar = sw->bar;
+        P.err = m->d_err;
+        P.done = done;
+        P.C = C;
+        P.iters = coarse_iters;
+        P.tol2 = coarse_tol * coarse_tol;
+        static int cg_per_sm = 0;
+        if (cg_per_sm == 0)
+            SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cg_per_sm, coarse_cg_kernel, kCgThreads, 0));
+        int gc = (C.nvt + kCgThreads - 1) / kCgThreads;
+        gc = std::min(gc, std::min(m->num_sms * std::max(cg_per_sm, 1), kCgMaxGrid));
+        gc = std::min(gc, m->num_sms);
+        void *args[] = {&P};
+        SEM_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(coarse_cg_kernel), dim3(gc),
+                                                   dim3(kCgThreads), args, 0, st));
+    }
+    int64_t gp = (m->E + sum_epb<N>() - 1) / sum_epb<N>();
+    if (gp > (int64_t)m->num_sms * 16) gp = (int64_t)m->num_sms * 16;
+    schwarz_sum_kernel<N><<<(int)gp, 256, 0, st>>>(sw->uext, coarse ? sw->xc : nullptr, sw->J1, A, C, done, z);
+    SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
 
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      cudaStream_t st) {
+                      const int *done, cudaStream_t st) {
     switch (sw->N) {
 #define SEM_SW_CASE(n) \
-    case n: return sw_apply_n<n>(sw, r, z, coarse_iters, coarse_tol, st);
+    case n: return sw_apply_n<n>(sw, r, z, coarse_iters, coarse_tol, done, st);
         SEM_SW_CASE(2) SEM_SW_CASE(3) SEM_SW_CASE(4) SEM_SW_CASE(5) SEM_SW_CASE(6) SEM_SW_CASE(7)
         SEM_SW_CASE(8) SEM_SW_CASE(9)
 #undef SEM_SW_CASE
@@ -424,8 +1010,8 @@ extern "C" {
 
 size_t sem_schwarz_workspace_bytes(const sem_mesh *m, const sem_mesh *mc) {
     if (!m || !mc) return 0;
-    size_t off[7];
-    return sw_layout(m, mc, off);
+    size_t off[15];
+    return sw_layout(m, off);
 }
 
 int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t bytes, void *stream,
@@ -433,14 +1019,14 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
     if (!m || !mc || !out) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (m->N < 2 || m->N > 9) return fail(SEM_ERR_UNSUPPORTED, "Schwarz preconditioner built for 2 <= N <= 9");
-    if (!m->G32 || !mc->G32) return fail(SEM_ERR_INVALID_ARG, "both meshes need SEM_GEOM_F32");
+    if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "the mesh needs SEM_GEOM_F32");
     if (mc->N != 1 || mc->E != m->E)
         return fail(SEM_ERR_INVALID_ARG, "the coarse mesh must be the N = 1 mesh of the same elements");
     for (int a = 0; a < 3; ++a)
         if (mc->nel[a] != m->nel[a] || mc->periodic[a] != m->periodic[a])
             return fail(SEM_ERR_INVALID_ARG, "the coarse mesh must have the same topology");
-    size_t off[7];
-    const size_t need = sw_layout(m, mc, off);
+    size_t off[15];
+    const size_t need = sw_layout(m, off);
     if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign || bytes < need)
         return fail(SEM_ERR_WORKSPACE, "Schwarz workspace NULL, misaligned or smaller than sem_schwarz_workspace_bytes");
     cudaStream_t st = as_stream(stream);
@@ -542,15 +1128,45 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
     sw->L = reinterpret_cast<float *>(base + off[1]);
     sw->prob = reinterpret_cast<int *>(base + off[2]);
     sw->uext = reinterpret_cast<float *>(base + off[3]);
-    sw->rc = reinterpret_cast<float *>(base + off[4]);
-    sw->xc = reinterpret_cast<float *>(base + off[5]);
-    sw->cg_scratch = base + off[6];
+    sw->rce = reinterpret_cast<float *>(base + off[4]);
+    sw->sten = reinterpret_cast<float *>(base + off[5]);
+    float *cv[6];
+    for (int q = 0; q < 6; ++q) cv[q] = reinterpret_cast<float *>(base + off[6 + q]);
+    sw->cdinv = cv[0];
+    sw->xc = cv[1];
+    sw->rcg = cv[2];
+    sw->pc0 = cv[3];
+    sw->pc1 = cv[4];
+    sw->wc = cv[5];
+    sw->partial = reinterpret_cast<double *>(base + off[12]);
+    sw->bar = reinterpret_cast<unsigned *>(base + off[13]);
+    sw->J1 = reinterpret_cast<float *>(base + off[14]);
+    const CoarseTopo C = coarse_topo(m);
+    sw->nv = C.nvt;
     sw->ws_bytes = need;
+    std::vector<float> J1(2 * kMaxN1, 0.f);
+    for (int i = 0; i <= N; ++i) {
+        J1[i] = (float)(0.5 * (1.0 - m->xi[i]));
+        J1[kMaxN1 + i] = (float)(0.5 * (1.0 + m->xi[i]));
+    }
     cudaError_t ce = cudaMemcpyAsync(sw->S, Stab.data(), sizeof(float) * Stab.size(), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(sw->L, Ltab.data(), sizeof(float) * Ltab.size(), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(sw->prob, prob.data(), sizeof(int) * prob.size(), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(sw->J1, J1.data(), sizeof(float) * J1.size(), cudaMemcpyHostToDevice, st);
+    // the coarse operator: N = 1 element matrices (in the extended-solution
+    // buffer, free until the first application), then the vertex stencil
+    if (ce == cudaSuccess) {
+        const int64_t tE = 8 * E;
+        coarse_elem_kernel<<<(int)std::min<int64_t>((tE + 255) / 256, 4096), 256, 0, st>>>(mc->G, (int)E, sw->uext);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        coarse_stencil_kernel<<<std::min((C.nvt + 255) / 256, 4096), 256, 0, st>>>(sw->uext, C, sw->sten, sw->cdinv);
+        ce = cudaGetLastError();
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
         delete sw;
@@ -572,7 +1188,7 @@ int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coars
     if (!sw || !r || !z) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (r == z) return fail(SEM_ERR_INVALID_ARG, "r and z must not overlap");
     if (coarse_iters < 0) return fail(SEM_ERR_INVALID_ARG, "coarse_iters < 0");
-    return schwarz_apply_f32(sw, r, z, coarse_iters, coarse_tol, as_stream(stream));
+    return schwarz_apply_f32(sw, r, z, coarse_iters, coarse_tol, nullptr, as_stream(stream));
 }
 
 }  // extern "C"
