@@ -237,8 +237,10 @@ typedef struct {
     const struct sem_schwarz *schwarz;  /* SEM_PCG_MIXED, Poisson: the inner FP32 solve
                               is flexible CG preconditioned by this hybrid Schwarz
                               object (see sem_schwarz_create; built on the same
-                              mesh), restarted at every refinement; NULL: Jacobi */
-    int coarse_iters;      /* Schwarz: coarse-level CG iterations per application */
+                              mesh, else SEM_ERR_INVALID_ARG), restarted at every
+                              refinement; NULL: Jacobi */
+    int coarse_iters;      /* Schwarz: coarse-level CG iterations per application
+                              (0: one-level Schwarz; 3 suffice on the channel) */
     double coarse_tol;     /* Schwarz: coarse-level relative tolerance (0 = 1e-2) */
 } sem_pcg_opts;
 
@@ -464,13 +466,19 @@ int sem_autotune_reset(void);
  * direction from the mean edge lengths of the element and its neighbours,
  * homogeneous Dirichlet just beyond the overlap), inverted by fast
  * diagonalisation (exact for axis-aligned tensor-product meshes); P the
- * trilinear interpolation from the element vertices, A_c the N = 1 operator,
- * solved by coarse_iters Jacobi-CG iterations to coarse_tol (0 iterations:
- * no coarse level).
+ * trilinear interpolation from the element vertices, A_c the N = 1 operator
+ * (assembled at set-up into a 27-point stencil on the global vertices),
+ * solved by up to coarse_iters Jacobi-CG iterations from 0, stopping early
+ * when <r, D^-1 r> falls by coarse_tol^2 (0 iterations: no coarse level).
  * mesh: 2 <= N <= 9, built with SEM_GEOM_F32; coarse: the N = 1 mesh of the
- * same vertices and topology, built with SEM_GEOM_F32.  Set-up solves the
- * 1-D eigenproblems on the host (cached by length and boundary type) and
- * waits for `stream`.  The object keeps pointers to both meshes. */
+ * same vertices and topology (its FP64 geometric factors give A_c).  Set-up
+ * solves the 1-D eigenproblems on the host (cached by length and boundary
+ * type), assembles A_c on the device and waits for `stream`.  The object
+ * keeps pointers to both meshes; the workspace (sem_schwarz_workspace_bytes)
+ * holds the tables, the extended local solutions (4 (N+3)^3 B per element)
+ * and the coarse vectors.  Errors: SEM_ERR_INVALID_ARG (NULL, wrong coarse
+ * mesh, mesh without FP32 factors), SEM_ERR_UNSUPPORTED (N outside 2..9),
+ * SEM_ERR_WORKSPACE. */
 typedef struct sem_schwarz sem_schwarz;
 size_t sem_schwarz_workspace_bytes(const sem_mesh *mesh, const sem_mesh *coarse);
 int sem_schwarz_create(const sem_mesh *mesh, const sem_mesh *coarse, void *d_workspace, size_t bytes,
@@ -479,8 +487,11 @@ int sem_schwarz_destroy(sem_schwarz *sw);
 /* Number of distinct 1-D eigenproblems solved at set-up. */
 int sem_schwarz_problems(const sem_schwarz *sw);
 /* z = M r (device FP32 E-layout, r continuous and zero on Dirichlet nodes;
- * z continuous, zero on Dirichlet nodes).  Stream-ordered, no host
- * synchronisation (graph-capturable). */
+ * z continuous, every copy of a node bit-identical, zero on Dirichlet
+ * nodes).  Stream-ordered, no host synchronisation; three kernels (local
+ * solves, the cooperative coarse CG when coarse_iters > 0, overlap sums).
+ * The coarse CG's grid barriers wait at most 1 s; a timeout is recorded in
+ * the mesh's error word (reported as SEM_ERR_TIMEOUT by the solver). */
 int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
                       void *stream);
 

@@ -300,9 +300,11 @@ class Mesh:
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
-                 mixed_restart=False, schwarz=None, coarse_iters=20, coarse_tol=1e-2) -> PcgOpts:
+                 mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2) -> PcgOpts:
         """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
-        preconditioner of the mixed solver)."""
+        preconditioner of the mixed solver), its coarse level solved by
+        coarse_iters Jacobi-CG iterations (3: on the 32^3 channel, N = 7, more
+        do not lower the outer iteration count) to coarse_tol."""
         o = PcgOpts()
         o.schwarz = schwarz.handle.value if schwarz is not None else None
         o.coarse_iters, o.coarse_tol = int(coarse_iters), float(coarse_tol)

@@ -234,6 +234,8 @@ int advect_weak_launch(const sem_mesh *m, const double *W, const double *const u
 // (optional device flag): set -> the kernels return at once.
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
                       const int *done, cudaStream_t st);
+// The (fine) mesh a Schwarz object was built on.
+const sem_mesh *schwarz_mesh(const sem_schwarz *sw);
 
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies

@@ -661,7 +661,7 @@ static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float 
             if (s != SEM_OK) return s;
             s = launch_update_box<float>(m, x, m->dinv32, W, st, wa);
             if (s != SEM_OK) return s;
-            c.launches += 6;
+            c.launches += coarse_iters > 0 ? 7 : 6;
             c.ax_launches += 1;
         }
     }
@@ -815,6 +815,8 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_UNSUPPORTED, "unknown precision mode");
     if (o->schwarz && o->precision != SEM_PCG_MIXED)
         return fail(SEM_ERR_UNSUPPORTED, "the Schwarz preconditioner is used by SEM_PCG_MIXED");
+    if (o->schwarz && schwarz_mesh(o->schwarz) != m)
+        return fail(SEM_ERR_INVALID_ARG, "the Schwarz preconditioner was built on another mesh");
     if (o->schwarz && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
         return fail(SEM_ERR_UNSUPPORTED, "the Schwarz preconditioner is built for the Poisson operator");
     if (o->precision == SEM_PCG_F64_PAIR && !m->G2)

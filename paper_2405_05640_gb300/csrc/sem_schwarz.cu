@@ -1002,6 +1002,8 @@ int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coars
     }
 }
 
+const sem_mesh *schwarz_mesh(const sem_schwarz *sw) { return sw ? sw->m : nullptr; }
+
 }  // namespace sem
 
 using namespace sem;
