@@ -58,6 +58,7 @@ struct sem_schwarz {
     double *partial;  // [2][kCgMaxGrid]
     unsigned *bar;    // grid barrier counter
     float *J1;        // [2][kMaxN1] J1[a][i] = (1 -+ xi_i) / 2
+    short *lines;     // [3][32 LPT] line dealt to each (group, lane) slot of a pass, or -1
     size_t ws_bytes;
 };
 
@@ -173,10 +174,13 @@ struct CoarseTopo {
 
 // Extended-block geometry of order N: NE = N + 3 points per direction, LPT
 // lines per lane (NE^2 lines over 32 lanes), table rows padded to NEP, block
-// strides PJ (J) and PK (K) in floats.  The strides minimise the bank
-// conflicts of the lanes' line accesses summed over the three directions
-// (exhaustive search over PJ in [NE, NE+12), PK in [NE PJ, NE PJ + 40) with
-// at most 20% padding).
+// strides PJ (J) and PK (K) in floats.  Within a pass all of a lane's
+// accesses move by the same stride, so a group of 32 lines (one per lane) is
+// conflict-free when its start addresses fall in distinct banks: the strides
+// are chosen (exhaustive search) so that at most LPT line starts share a bank
+// in every direction where that is possible with little padding (N = 3, 4,
+// 6, 7), and the lines are dealt to the lanes by a per-pass table (see
+// line_table) that keeps equal banks in different groups.
 template <int N>
 struct SwShape {
     static constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
@@ -185,13 +189,14 @@ struct SwShape {
     static constexpr int NEP = (NE + 3) / 4 * 4;
     static constexpr int PJ = N == 5 ? 9 : N == 9 ? 13 : NE;
     static constexpr int PK = N == 2   ? 25
-                              : N == 3 ? 36
+                              : N == 3 ? 37
                               : N == 4 ? 52
                               : N == 5 ? 72
-                              : N == 6 ? 81
-                              : N == 7 ? 101
+                              : N == 6 ? 93
+                              : N == 7 ? 103
                               : N == 8 ? 121
                                        : 156;
+    static constexpr int SLOTS = 32 * LPT;  // line slots of a pass (line id or -1)
     static constexpr int TAB = 3 * NE * NEP;                 // one table set (3 axes)
     static constexpr int LAM = (3 * NE + 3) / 4 * 4;
     static constexpr int BUF = (PK * NE + 3) / 4 * 4;
@@ -250,17 +255,21 @@ __device__ __forceinline__ float acc_at(const float2 (&acc)[LPT][NE / 2], const 
     return (NE & 1) && a == NE - 1 ? tail[q] : ((a & 1) ? acc[q][a / 2].y : acc[q][a / 2].x);
 }
 
-// The lane's lines of the warp's block along axis AX: (c1, c2) =
-// (L mod NE, L / NE), L = lane + 32 q; offsets into the block.
+// The lane's lines of the warp's block along axis AX from the pass's line
+// table (line id c1 + NE c2, or -1): (c1, c2) = (J, K), (I, K) or (I, J);
+// offsets into the block.
 template <int N, int AX>
-__device__ __forceinline__ void line_offsets(int lane, int (&off)[SwShape<N>::LPT], int (&c1)[SwShape<N>::LPT],
-                                             int (&c2)[SwShape<N>::LPT]) {
+__device__ __forceinline__ void line_offsets(const short *lines, int lane, int (&off)[SwShape<N>::LPT],
+                                             int (&c1)[SwShape<N>::LPT], int (&c2)[SwShape<N>::LPT],
+                                             bool (&ok)[SwShape<N>::LPT]) {
     using S = SwShape<N>;
 #pragma unroll
     for (int q = 0; q < S::LPT; ++q) {
-        const int L = lane + 32 * q;
-        c1[q] = L < S::NE2 ? L % S::NE : 0;
-        c2[q] = L < S::NE2 ? L / S::NE : 0;
+        int id = lines[AX * S::SLOTS + 32 * q + lane];
+        ok[q] = id >= 0;
+        id = ok[q] ? id : 0;
+        c1[q] = id % S::NE;
+        c2[q] = id / S::NE;
         off[q] = AX == 0 ? S::PJ * c1[q] + S::PK * c2[q] : AX == 1 ? c1[q] + S::PK * c2[q] : c1[q] + S::PJ * c2[q];
     }
 }
@@ -269,12 +278,13 @@ __device__ __forceinline__ void line_offsets(int lane, int (&off)[SwShape<N>::LP
 // lines: out[a] = sum_l tab[AX][l][a] in[l] (in place), tab the S rows
 // (forward: S^T along the line) or the S^T rows (backward: S).
 template <int N, int AX>
-__device__ __forceinline__ void sw_lines(float *buf, const float *tab, int lane) {
+__device__ __forceinline__ void sw_lines(float *buf, const float *tab, const short *lines, int lane) {
     using S = SwShape<N>;
     constexpr int NE = S::NE, LPT = S::LPT, NEP = S::NEP;
     constexpr int ST = AX == 0 ? 1 : AX == 1 ? S::PJ : S::PK;
     int off[LPT], c1[LPT], c2[LPT];
-    line_offsets<N, AX>(lane, off, c1, c2);
+    bool ok[LPT];
+    line_offsets<N, AX>(lines, lane, off, c1, c2, ok);
     float2 acc[LPT][NE / 2];
     float tail[LPT];
 #pragma unroll
@@ -296,21 +306,25 @@ __device__ __forceinline__ void sw_lines(float *buf, const float *tab, int lane)
     }
 #pragma unroll
     for (int q = 0; q < LPT; ++q)
-        if (lane + 32 * q < S::NE2) {
+        if (ok[q]) {
 #pragma unroll
             for (int a = 0; a < NE; ++a) buf[off[q] + a * ST] = acc_at<NE, LPT>(acc, tail, q, a);
         }
 }
 
-// The K direction: forward (S_z^T), division by lx[c1] + ly[c2] + lz[c] (the
-// lines then indexed by modes), backward (S_z), all in registers.
-template <int N>
-__device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const float *tabT, const float *lam,
-                                         int lane) {
+// One direction done whole in registers: forward (S^T of axis AX), division
+// by lambda_AX[a] + the lines' two other eigenvalues (the lines are indexed
+// by modes then), backward (S).  Lines from the pass's line table.
+template <int N, int AX>
+__device__ __forceinline__ void sw_fused(float *buf, const float *tabS, const float *tabT, const float *lam,
+                                         const short *lines, int lane) {
     using S = SwShape<N>;
-    constexpr int NE = S::NE, LPT = S::LPT, NEP = S::NEP, ST = S::PK;
+    constexpr int NE = S::NE, LPT = S::LPT, NEP = S::NEP;
+    constexpr int ST = AX == 0 ? 1 : AX == 1 ? S::PJ : S::PK;
+    constexpr int L1 = AX == 0 ? 1 : 0, L2 = AX == 2 ? 1 : 2;  // axes of c1, c2
     int off[LPT], c1[LPT], c2[LPT];
-    line_offsets<N, 2>(lane, off, c1, c2);
+    bool ok[LPT];
+    line_offsets<N, AX>(lines, lane, off, c1, c2, ok);
     float2 acc[LPT][NE / 2];
     float tail[LPT];
 #pragma unroll
@@ -319,7 +333,7 @@ __device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const fl
 #pragma unroll
         for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = make_float2(0.f, 0.f);
     }
-    const float *tS = tabS + 2 * NE * NEP, *tT = tabT + 2 * NE * NEP;
+    const float *tS = tabS + AX * NE * NEP, *tT = tabT + AX * NE * NEP;
 #pragma unroll
     for (int l = 0; l < NE; ++l) {
         float x[LPT];
@@ -332,7 +346,7 @@ __device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const fl
     }
     float lq[LPT];
 #pragma unroll
-    for (int q = 0; q < LPT; ++q) lq[q] = lam[c1[q]] + lam[NE + c2[q]];
+    for (int q = 0; q < LPT; ++q) lq[q] = lam[L1 * NE + c1[q]] + lam[L2 * NE + c2[q]];
     float2 out[LPT][NE / 2];
     float otail[LPT];
 #pragma unroll
@@ -343,10 +357,10 @@ __device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const fl
     }
 #pragma unroll
     for (int c = 0; c < NE; ++c) {
-        const float lz = lam[2 * NE + c];
+        const float la = lam[AX * NE + c];
         float x[LPT];
 #pragma unroll
-        for (int q = 0; q < LPT; ++q) x[q] = __fdividef(acc_at<NE, LPT>(acc, tail, q, c), lq[q] + lz);
+        for (int q = 0; q < LPT; ++q) x[q] = __fdividef(acc_at<NE, LPT>(acc, tail, q, c), lq[q] + la);
         float4 rw[NEP / 4];
 #pragma unroll
         for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(tT + c * NEP)[c4];
@@ -354,7 +368,7 @@ __device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const fl
     }
 #pragma unroll
     for (int q = 0; q < LPT; ++q)
-        if (lane + 32 * q < S::NE2) {
+        if (ok[q]) {
 #pragma unroll
             for (int a = 0; a < NE; ++a) buf[off[q] + a * ST] = acc_at<NE, LPT>(out, otail, q, a);
         }
@@ -363,14 +377,19 @@ __device__ __forceinline__ void sw_kpass(float *buf, const float *tabS, const fl
 // Local solves: one warp per element.  uext[e] = A_e^{-1} R_e r on the
 // extended points ([K][J][I], NE^3); with rce, also the restriction
 // rce[e][a + 2b + 4c] = sum_ijk J1[a][i] J1[b][j] J1[c][k] r(i,j,k) / mult.
+// Passes: K forward straight from global memory (lanes on (I, J) lines in
+// natural order; the restriction from the same registers), J forward, I
+// forward + division + I backward, J backward, K backward straight to
+// global memory (for each K the warp stores 32 consecutive points).
 // done (optional): a device flag; set -> return at once.
 template <int N>
 __global__ void __launch_bounds__(kSwWarps * 32, N <= 6 ? 5 : 4)
     schwarz_local_kernel(const float *__restrict__ r, const float *__restrict__ Stab, const float *__restrict__ Ltab,
-                         const int *__restrict__ prob, const float *__restrict__ J1, SwArgs A,
-                         const int *__restrict__ done, float *__restrict__ uext, float *__restrict__ rce) {
+                         const int *__restrict__ prob, const float *__restrict__ J1, const short *__restrict__ ltab,
+                         SwArgs A, const int *__restrict__ done, float *__restrict__ uext,
+                         float *__restrict__ rce) {
     using S = SwShape<N>;
-    constexpr int NE = S::NE, NE2 = S::NE2, NE3 = S::NE3, N1 = S::N1, NPT = S::NPT, NEP = S::NEP;
+    constexpr int NE = S::NE, NE2 = S::NE2, NE3 = S::NE3, N1 = S::N1, NPT = S::NPT, NEP = S::NEP, LPT = S::LPT;
     if (done && *done) return;
     extern __shared__ float4 sw_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -378,47 +397,25 @@ __global__ void __launch_bounds__(kSwWarps * 32, N <= 6 ? 5 : 4)
     float *sT = sS + S::TAB, *sL = sT + S::TAB, *buf = sL + S::LAM;
     int64_t *sOff = reinterpret_cast<int64_t *>(buf + S::BUF);
     constexpr int64_t kOut = INT64_MIN;  // source outside the domain
+    short *lines = reinterpret_cast<short *>(reinterpret_cast<float *>(sw_smem) + kSwWarps * S::WARP_FLOATS);
+    for (int t = threadIdx.x; t < 3 * S::SLOTS; t += blockDim.x) lines[t] = ltab[t];
+    __syncthreads();
     const int sy = A.nel[0], sz = A.nel[0] * A.nel[1];
+    // the lane's K lines (I, J), natural order
+    int kI[LPT], kJ[LPT];
+    bool kok[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        const int L = lane + 32 * q;
+        kok[q] = L < NE2;
+        kI[q] = kok[q] ? L % NE : 0;
+        kJ[q] = kok[q] ? L / NE : 0;
+    }
     for (int e = blockIdx.x * kSwWarps + warp; e < A.E; e += gridDim.x * kSwWarps) {
         __syncwarp();
         const int ex = e % A.nel[0], ey = (e / A.nel[0]) % A.nel[1], ez = e / sz;
         const int pid[3] = {__ldg(prob + 3 * (int64_t)e), __ldg(prob + 3 * (int64_t)e + 1),
                             __ldg(prob + 3 * (int64_t)e + 2)};
-        // per axis, the offset of each extended point's source in r (element
-        // offset x points per element + local stride), or kOut outside the domain
-        for (int t = lane; t < 3 * NE; t += 32) {
-            const int ax = t / NE, I = t - ax * NE;
-            const int c = ax == 0 ? ex : ax == 1 ? ey : ez;
-            const int n = ax == 0 ? A.nel[0] : ax == 1 ? A.nel[1] : A.nel[2];
-            const int per = ax == 0 ? A.per[0] : ax == 1 ? A.per[1] : A.per[2];
-            const int64_t es = ax == 0 ? 1 : ax == 1 ? sy : sz;
-            const int ls = ax == 0 ? 1 : ax == 1 ? N1 : N1 * N1;
-            int dc, li;
-            sOff[t] = ext_move(I, N, c, n, per, dc, li) ? (dc * es) * NPT + (int64_t)li * ls : kOut;
-        }
-        __syncwarp();
-        // the extended residual, kGB loads in flight per lane
-        constexpr int kIt = (NE3 + 31) / 32, kGB = 8;
-        const float *re = r + (int64_t)e * NPT;
-#pragma unroll 1
-        for (int t0 = 0; t0 < kIt; t0 += kGB) {
-            float v[kGB];
-#pragma unroll
-            for (int u = 0; u < kGB; ++u) {
-                const int t = lane + 32 * (t0 + u);
-                v[u] = 0.f;
-                if (t < NE3) {
-                    const int I = t % NE, J = (t / NE) % NE, K = t / NE2;
-                    const int64_t ox = sOff[I], oy = sOff[NE + J], oz = sOff[2 * NE + K];
-                    if (ox != kOut && oy != kOut && oz != kOut) v[u] = __ldg(re + (ox + oy + oz));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kGB; ++u) {
-                const int t = lane + 32 * (t0 + u);
-                if (t < NE3) buf[t % NE + S::PJ * ((t / NE) % NE) + S::PK * (t / NE2)] = v[u];
-            }
-        }
         constexpr int kTt = (3 * NE2 + 31) / 32;
         float tv[kTt];
 #pragma unroll
@@ -439,6 +436,18 @@ __global__ void __launch_bounds__(kSwWarps * 32, N <= 6 ? 5 : 4)
                 lv[u] = __ldg(Ltab + (int64_t)(a == 0 ? pid[0] : a == 1 ? pid[1] : pid[2]) * NE + (t - a * NE));
             }
         }
+        // per axis, the offset of each extended point's source in r (element
+        // offset x points per element + local stride), or kOut outside the domain
+        for (int t = lane; t < 3 * NE; t += 32) {
+            const int ax = t / NE, I = t - ax * NE;
+            const int c = ax == 0 ? ex : ax == 1 ? ey : ez;
+            const int n = ax == 0 ? A.nel[0] : ax == 1 ? A.nel[1] : A.nel[2];
+            const int per = ax == 0 ? A.per[0] : ax == 1 ? A.per[1] : A.per[2];
+            const int64_t es = ax == 0 ? 1 : ax == 1 ? sy : sz;
+            const int ls = ax == 0 ? 1 : ax == 1 ? N1 : N1 * N1;
+            int dc, li;
+            sOff[t] = ext_move(I, N, c, n, per, dc, li) ? (dc * es) * NPT + (int64_t)li * ls : kOut;
+        }
 #pragma unroll
         for (int u = 0; u < kTt; ++u) {
             const int t = lane + 32 * u;
@@ -452,57 +461,121 @@ __global__ void __launch_bounds__(kSwWarps * 32, N <= 6 ? 5 : 4)
         for (int u = 0; u < kLt; ++u)
             if (lane + 32 * u < 3 * NE) sL[lane + 32 * u] = lv[u];
         __syncwarp();
-        if (rce) {
-            float c8[8];
+        // ---- K forward from global memory (+ restriction)
+        {
+            const float *re = r + (int64_t)e * NPT;
+            int64_t oxy[LPT];
+            bool vxy[LPT];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) c8[v] = 0.f;
-            for (int jk = lane; jk < N1 * N1; jk += 32) {
-                const int j = jk % N1, k = jk / N1;
-                const float *row = buf + 1 + S::PJ * (j + 1) + S::PK * (k + 1);
-                float s0 = 0.f, s1 = 0.f;
+            for (int q = 0; q < LPT; ++q) {
+                const int64_t ox = sOff[kI[q]], oy = sOff[NE + kJ[q]];
+                vxy[q] = kok[q] && ox != kOut && oy != kOut;
+                oxy[q] = vxy[q] ? ox + oy : 0;
+            }
+            float2 acc[LPT][NE / 2];
+            float tail[LPT], rs0[LPT], rs1[LPT];
 #pragma unroll
-                for (int i = 0; i < N1; ++i) {
-                    const float v = row[i] * mult_fac(i, N, ex, A.nel[0], A.per[0]);
-                    s0 = fmaf(__ldg(J1 + i), v, s0);
-                    s1 = fmaf(__ldg(J1 + kMaxN1 + i), v, s1);
+            for (int q = 0; q < LPT; ++q) {
+                tail[q] = rs0[q] = rs1[q] = 0.f;
+#pragma unroll
+                for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = make_float2(0.f, 0.f);
+            }
+            const float *tS = sS + 2 * NE * NEP;
+#pragma unroll
+            for (int K = 0; K < NE; ++K) {
+                const int64_t oz = sOff[2 * NE + K];
+                float x[LPT];
+#pragma unroll
+                for (int q = 0; q < LPT; ++q) x[q] = (vxy[q] && oz != kOut) ? __ldg(re + (oxy[q] + oz)) : 0.f;
+                if (rce && K >= 1 && K <= N + 1) {
+                    const float wz = mult_fac(K - 1, N, ez, A.nel[2], A.per[2]);
+                    const float jz0 = __ldg(J1 + K - 1) * wz, jz1 = __ldg(J1 + kMaxN1 + K - 1) * wz;
+#pragma unroll
+                    for (int q = 0; q < LPT; ++q) {
+                        rs0[q] = fmaf(jz0, x[q], rs0[q]);
+                        rs1[q] = fmaf(jz1, x[q], rs1[q]);
+                    }
                 }
-                const float wy = mult_fac(j, N, ey, A.nel[1], A.per[1]), wz = mult_fac(k, N, ez, A.nel[2], A.per[2]);
-                const float y0 = __ldg(J1 + j) * wy, y1 = __ldg(J1 + kMaxN1 + j) * wy;
-                const float z0 = __ldg(J1 + k) * wz, z1 = __ldg(J1 + kMaxN1 + k) * wz;
-                c8[0] = fmaf(s0, y0 * z0, c8[0]);
-                c8[1] = fmaf(s1, y0 * z0, c8[1]);
-                c8[2] = fmaf(s0, y1 * z0, c8[2]);
-                c8[3] = fmaf(s1, y1 * z0, c8[3]);
-                c8[4] = fmaf(s0, y0 * z1, c8[4]);
-                c8[5] = fmaf(s1, y0 * z1, c8[5]);
-                c8[6] = fmaf(s0, y1 * z1, c8[6]);
-                c8[7] = fmaf(s1, y1 * z1, c8[7]);
-            }
-            float mine = 0.f;
+                float4 rw[NEP / 4];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                float t = c8[v];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == v) mine = t;
+                for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(tS + K * NEP)[c4];
+                row_fma<NE, NEP, LPT>(acc, tail, rw, x);
             }
-            if (lane < 8) rce[(int64_t)e * 8 + lane] = mine;
-            __syncwarp();
+            if (rce) {
+                float c8[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) c8[v] = 0.f;
+#pragma unroll
+                for (int q = 0; q < LPT; ++q) {
+                    const int i = kI[q] - 1, j = kJ[q] - 1;
+                    if (kok[q] && i >= 0 && i <= N && j >= 0 && j <= N) {
+                        const float wx = mult_fac(i, N, ex, A.nel[0], A.per[0]);
+                        const float wy = mult_fac(j, N, ey, A.nel[1], A.per[1]);
+                        const float x0 = __ldg(J1 + i) * wx, x1 = __ldg(J1 + kMaxN1 + i) * wx;
+                        const float y0 = __ldg(J1 + j) * wy, y1 = __ldg(J1 + kMaxN1 + j) * wy;
+                        c8[0] = fmaf(x0 * y0, rs0[q], c8[0]);
+                        c8[1] = fmaf(x1 * y0, rs0[q], c8[1]);
+                        c8[2] = fmaf(x0 * y1, rs0[q], c8[2]);
+                        c8[3] = fmaf(x1 * y1, rs0[q], c8[3]);
+                        c8[4] = fmaf(x0 * y0, rs1[q], c8[4]);
+                        c8[5] = fmaf(x1 * y0, rs1[q], c8[5]);
+                        c8[6] = fmaf(x0 * y1, rs1[q], c8[6]);
+                        c8[7] = fmaf(x1 * y1, rs1[q], c8[7]);
+                    }
+                }
+                float mine = 0.f;
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    float t = c8[v];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                    if (lane == v) mine = t;
+                }
+                if (lane < 8) rce[(int64_t)e * 8 + lane] = mine;
+            }
+#pragma unroll
+            for (int q = 0; q < LPT; ++q)
+                if (kok[q]) {
+#pragma unroll
+                    for (int c = 0; c < NE; ++c)
+                        buf[kI[q] + S::PJ * kJ[q] + S::PK * c] = acc_at<NE, LPT>(acc, tail, q, c);
+                }
         }
-        sw_lines<N, 0>(buf, sS, lane);
         __syncwarp();
-        sw_lines<N, 1>(buf, sS, lane);
+        sw_lines<N, 1>(buf, sS, lines, lane);
         __syncwarp();
-        sw_kpass<N>(buf, sS, sT, sL, lane);
+        sw_fused<N, 0>(buf, sS, sT, sL, lines, lane);
         __syncwarp();
-        sw_lines<N, 1>(buf, sT, lane);
+        sw_lines<N, 1>(buf, sT, lines, lane);
         __syncwarp();
-        sw_lines<N, 0>(buf, sT, lane);
-        __syncwarp();
-        float *ue = uext + (int64_t)e * NE3;
-        for (int t = lane; t < NE3; t += 32) {
-            const int I = t % NE, J = (t / NE) % NE, K = t / NE2;
-            ue[t] = buf[I + S::PJ * J + S::PK * K];
+        // ---- K backward straight to global memory
+        {
+            float2 acc[LPT][NE / 2];
+            float tail[LPT];
+#pragma unroll
+            for (int q = 0; q < LPT; ++q) {
+                tail[q] = 0.f;
+#pragma unroll
+                for (int a2 = 0; a2 < NE / 2; ++a2) acc[q][a2] = make_float2(0.f, 0.f);
+            }
+            const float *tT = sT + 2 * NE * NEP;
+#pragma unroll
+            for (int c = 0; c < NE; ++c) {
+                float x[LPT];
+#pragma unroll
+                for (int q = 0; q < LPT; ++q) x[q] = buf[kI[q] + S::PJ * kJ[q] + S::PK * c];
+                float4 rw[NEP / 4];
+#pragma unroll
+                for (int c4 = 0; c4 < NEP / 4; ++c4) rw[c4] = reinterpret_cast<const float4 *>(tT + c * NEP)[c4];
+                row_fma<NE, NEP, LPT>(acc, tail, rw, x);
+            }
+            float *ue = uext + (int64_t)e * NE3;
+#pragma unroll
+            for (int q = 0; q < LPT; ++q)
+                if (kok[q]) {
+#pragma unroll
+                    for (int K = 0; K < NE; ++K) ue[K * NE2 + lane + 32 * q] = acc_at<NE, LPT>(acc, tail, q, K);
+                }
         }
     }
 }
@@ -903,6 +976,52 @@ static CoarseTopo coarse_topo(const sem_mesh *m) {
     return C;
 }
 
+// Deal the NE^2 lines of each pass to (group q, lane) slots: lines in bank
+// order, each to the group holding the fewest lines of its bank so far (then
+// the emptiest), at most 32 per group; a group then meets a bank conflict
+// only where a bank holds more than LPT line starts.
+template <int N>
+static void line_table(std::vector<short> &tab) {
+    using S = SwShape<N>;
+    constexpr int NE = S::NE, LPT = S::LPT;
+    tab.assign(3 * S::SLOTS, (short)-1);
+    for (int ax = 0; ax < 3; ++ax) {
+        std::vector<std::pair<int, int>> byb;  // (bank, line)
+        for (int id = 0; id < S::NE2; ++id) {
+            const int c1 = id % NE, c2 = id / NE;
+            const int base = ax == 0 ? S::PJ * c1 + S::PK * c2 : ax == 1 ? c1 + S::PK * c2 : c1 + S::PJ * c2;
+            byb.push_back({base % 32, id});
+        }
+        std::stable_sort(byb.begin(), byb.end());
+        std::vector<int> size(LPT, 0), cnt(LPT * 32, 0);
+        for (const auto &bl : byb) {
+            int best = -1;
+            for (int q = 0; q < LPT; ++q) {
+                if (size[q] >= 32) continue;
+                if (best < 0 || cnt[q * 32 + bl.first] < cnt[best * 32 + bl.first] ||
+                    (cnt[q * 32 + bl.first] == cnt[best * 32 + bl.first] && size[q] < size[best]))
+                    best = q;
+            }
+            tab[ax * S::SLOTS + best * 32 + size[best]] = (short)bl.second;
+            ++size[best];
+            ++cnt[best * 32 + bl.first];
+        }
+    }
+}
+
+static void line_table_n(int N, std::vector<short> &tab) {
+    switch (N) {
+        case 2: line_table<2>(tab); break;
+        case 3: line_table<3>(tab); break;
+        case 4: line_table<4>(tab); break;
+        case 5: line_table<5>(tab); break;
+        case 6: line_table<6>(tab); break;
+        case 7: line_table<7>(tab); break;
+        case 8: line_table<8>(tab); break;
+        default: line_table<9>(tab); break;
+    }
+}
+
 static size_t sw_layout(const sem_mesh *m, size_t *off) {
     const int ne = m->N + 3;
     const size_t P = 3 * (size_t)m->E;  // upper bound: every element and axis distinct
@@ -919,6 +1038,7 @@ static size_t sw_layout(const sem_mesh *m, size_t *off) {
     off[12] = take(sizeof(double) * 2 * kCgMaxGrid);
     off[13] = take(sizeof(unsigned) * 4);
     off[14] = take(sizeof(float) * 2 * kMaxN1);
+    off[15] = take(sizeof(short) * 3 * 32 * 5);  // LPT <= 5 (N <= 9)
     return o;
 }
 
@@ -940,7 +1060,7 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
     const sem_mesh *m = sw->m;
     const SwArgs A = sw_args(m);
     const bool coarse = coarse_iters > 0;
-    const size_t smem = sizeof(float) * kSwWarps * S::WARP_FLOATS;
+    const size_t smem = sizeof(float) * kSwWarps * S::WARP_FLOATS + sizeof(short) * 3 * S::SLOTS;
     static int per_sm = 0;  // resident CTAs per SM of this instantiation (device-independent shape)
     if (per_sm == 0) {
         SEM_CUDA_CHECK(cudaFuncSetAttribute(schwarz_local_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -951,8 +1071,8 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
     }
     int64_t g = (m->E + kSwWarps - 1) / kSwWarps;
     if (g > (int64_t)m->num_sms * per_sm) g = (int64_t)m->num_sms * per_sm;
-    schwarz_local_kernel<N><<<(int)g, kSwWarps * 32, smem, st>>>(r, sw->S, sw->L, sw->prob, sw->J1, A, done,
-                                                                  sw->uext, coarse ? sw->rce : nullptr);
+    schwarz_local_kernel<N><<<(int)g, kSwWarps * 32, smem, st>>>(r, sw->S, sw->L, sw->prob, sw->J1, sw->lines, A,
+                                                                  done, sw->uext, coarse ? sw->rce : nullptr);
     SEM_CUDA_CHECK(cudaGetLastError());
     const CoarseTopo C = coarse_topo(m);
     if (coarse) {
@@ -1012,7 +1132,7 @@ extern "C" {
 
 size_t sem_schwarz_workspace_bytes(const sem_mesh *m, const sem_mesh *mc) {
     if (!m || !mc) return 0;
-    size_t off[15];
+    size_t off[16];
     return sw_layout(m, off);
 }
 
@@ -1027,7 +1147,7 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
     for (int a = 0; a < 3; ++a)
         if (mc->nel[a] != m->nel[a] || mc->periodic[a] != m->periodic[a])
             return fail(SEM_ERR_INVALID_ARG, "the coarse mesh must have the same topology");
-    size_t off[15];
+    size_t off[16];
     const size_t need = sw_layout(m, off);
     if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign || bytes < need)
         return fail(SEM_ERR_WORKSPACE, "Schwarz workspace NULL, misaligned or smaller than sem_schwarz_workspace_bytes");
@@ -1143,6 +1263,9 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
     sw->partial = reinterpret_cast<double *>(base + off[12]);
     sw->bar = reinterpret_cast<unsigned *>(base + off[13]);
     sw->J1 = reinterpret_cast<float *>(base + off[14]);
+    sw->lines = reinterpret_cast<short *>(base + off[15]);
+    std::vector<short> ltab;
+    line_table_n(N, ltab);
     const CoarseTopo C = coarse_topo(m);
     sw->nv = C.nvt;
     sw->ws_bytes = need;
@@ -1158,6 +1281,8 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
         ce = cudaMemcpyAsync(sw->prob, prob.data(), sizeof(int) * prob.size(), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(sw->J1, J1.data(), sizeof(float) * J1.size(), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(sw->lines, ltab.data(), sizeof(short) * ltab.size(), cudaMemcpyHostToDevice, st);
     // the coarse operator: N = 1 element matrices (in the extended-solution
     // buffer, free until the first application), then the vertex stencil
     if (ce == cudaSuccess) {
