@@ -249,8 +249,10 @@ __device__ __forceinline__ void face_status(int e, int nel, int per, bool lo, in
 // weight 1/mult computed from the point's position (a power of two, the same
 // value as the mesh's stored 1/mult).
 // WRITEW: the assembled, masked w is also written to wout (the flexible CG of
-// a general preconditioner needs <z, A p> in the next iteration).  wout must
-// not be W.w: the x pass of this launch reads W.w's raw line ends.
+// a general preconditioner needs <z, A p> in the next iteration), and dinv is
+// not read (the <r, D^-1 r> partial is then 0; the preconditioner's own
+// kernel forms rho).  wout must not be W.w: the x pass of this launch reads
+// W.w's raw line ends.
 template <typename T, int N, bool VEC, bool WRITEW = false>
 __global__ void __launch_bounds__(kPThreads)
     pcg_update_box_kernel(T *__restrict__ x, const T *__restrict__ dinv, BoxTopo B, PcgWork<T> W,
@@ -276,7 +278,12 @@ __global__ void __launch_bounds__(kPThreads)
         load_line<T, N1, VEC>(W.w + base, w);
         load_line<T, N1, VEC>(x + base, xv);
         load_line<T, N1, VEC>(W.r + base, r);
-        load_line<T, N1, VEC>(dinv + base, di);
+        if (WRITEW) {  // flexible CG: z comes from the preconditioner, <r, D^-1 r> is not used
+#pragma unroll
+            for (int i = 0; i < N1; ++i) di[i] = T(0);
+        } else {
+            load_line<T, N1, VEC>(dinv + base, di);
+        }
         // y and z status of the whole line
         int sy = 0, sz = 0;
         bool dy = false, dz = false;
