@@ -617,23 +617,81 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
 
 // Flexible CG with a general preconditioner z = M r: rho = <r, z> and the
 // Polak-Ribiere beta = <z, r_new - r_old> / rho_old = -alpha <z, A p> / rho_old
-// (A p assembled in wa by the update; rho_old kept in rho_prev by the update).
-template <typename T>
+// (A p assembled in wa by the update; rho_old kept in rho_prev by the update),
+// line-wise on the box topology (one thread per r-line, as the update): 1/mult
+// from the point's position instead of a stored array, so only r, z and wa are
+// read.
+template <int N, bool VEC>
 __global__ void __launch_bounds__(kPThreads)
-    fpcg_dots_kernel(const T *__restrict__ r, const T *__restrict__ z, const T *__restrict__ wa,
-                     const T *__restrict__ minv, int64_t n, PcgWork<T> W, int first) {
+    fpcg_dots_box_kernel(const float *__restrict__ r, const float *__restrict__ z, const float *__restrict__ wa,
+                         BoxTopo B, PcgWork<float> W, int first) {
     if (W.scal->done) return;
-    T f0 = T(0), f1 = T(0);
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
-        const T mi = minv[l], zl = z[l];
-        f0 = fma(r[l] * zl, mi, f0);
-        if (!first) f1 = fma(wa[l] * zl, mi, f1);
+    constexpr int N1 = N + 1, NL = N1 * N1;
+    float f0 = 0.f, f1 = 0.f;
+    const int nx = B.nel[0], ny = B.nel[1];
+    const int64_t nlines = B.E * NL;
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < nlines;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = L / NL;
+        const int jk = (int)(L - e * NL);
+        const int j = jk % N1, k = jk / N1;
+        const int ex = (int)(e % nx);
+        const int64_t eyz = e / nx;
+        const int ey = (int)(eyz % ny), ez = (int)(eyz / ny);
+        const int64_t base = L * N1;
+        float rv[N1], zv[N1], wv[N1];
+        load_line<float, N1, VEC>(r + base, rv);
+        load_line<float, N1, VEC>(z + base, zv);
+        if (!first) load_line<float, N1, VEC>(wa + base, wv);
+        int sy = 0, sz = 0, sx0 = 0, sxN = 0;
+        bool dd = false;
+        if (j == 0 || j == N) face_status(ey, ny, B.per[1], j == 0, 4, 8, B.faces, sy, dd);
+        if (k == 0 || k == N) face_status(ez, B.nel[2], B.per[2], k == 0, 16, 32, B.faces, sz, dd);
+        face_status(ex, nx, B.per[0], true, 1, 2, B.faces, sx0, dd);
+        face_status(ex, nx, B.per[0], false, 1, 2, B.faces, sxN, dd);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int sh = (i == 0 ? sx0 : (i == N ? sxN : 0)) + sy + sz;
+            const float mi = sh == 0 ? 1.f : (sh == 1 ? 0.5f : (sh == 2 ? 0.25f : 0.125f));
+            f0 = fmaf(rv[i] * zv[i], mi, f0);
+            if (!first) f1 = fmaf(wv[i] * zv[i], mi, f1);
+        }
     }
     double v[2] = {(double)f0, (double)f1}, t[2];
     if (grid_reduce<2>(v, W.partial, &W.scal->cnt[0], t)) {
         PcgScal *s = W.scal;
         s->beta = first ? 0.0 : -s->alpha * t[1] / s->rho_prev;
         s->rho = t[0];
+    }
+}
+
+template <int N>
+static int launch_fpcg_dots_box_n(const sem_mesh *m, const float *r, const float *z, const float *wa,
+                                  const PcgWork<float> &W, int first, cudaStream_t st) {
+    constexpr int N1 = N + 1;
+    const BoxTopo B = box_topo(m);
+    const bool vec = ((N1 * sizeof(float)) % 16 == 0);
+    auto kv = fpcg_dots_box_kernel<N, ((N1 * sizeof(float)) % 16 == 0)>;
+    auto ks = fpcg_dots_box_kernel<N, false>;
+    auto kern = vec ? kv : ks;
+    int per_sm = 0;
+    SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, 0));
+    int grid = m->num_sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > kPBlocks) grid = kPBlocks;
+    kern<<<grid, kPThreads, 0, st>>>(r, z, wa, B, W, first);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+static int launch_fpcg_dots_box(const sem_mesh *m, const float *r, const float *z, const float *wa,
+                                const PcgWork<float> &W, int first, cudaStream_t st) {
+    switch (m->N) {
+#define SEM_FD_CASE(n) \
+    case n: return launch_fpcg_dots_box_n<n>(m, r, z, wa, W, first, st);
+        SEM_FD_CASE(2) SEM_FD_CASE(3) SEM_FD_CASE(4) SEM_FD_CASE(5) SEM_FD_CASE(6) SEM_FD_CASE(7)
+        SEM_FD_CASE(8) SEM_FD_CASE(9)
+#undef SEM_FD_CASE
+        default: return fail(SEM_ERR_UNSUPPORTED, "order N not built");
     }
 }
 
@@ -655,9 +713,8 @@ static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float 
         for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
             int s = schwarz_apply_f32(sw, W.r, z, coarse_iters, coarse_tol, &W.scal->done, st);
             if (s != SEM_OK) return s;
-            fpcg_dots_kernel<float><<<kPBlocks, kPThreads, 0, st>>>(W.r, z, wa, m->minv32, m->nloc, W,
-                                                                    launched == 0 ? 1 : 0);
-            SEM_CUDA_CHECK(cudaGetLastError());
+            s = launch_fpcg_dots_box(m, W.r, z, wa, W, launched == 0 ? 1 : 0, st);
+            if (s != SEM_OK) return s;
             c.tax.start(st);
             s = ax_cg_launch_f32(m, cg, W.w, st);
             c.tax.stop(st);

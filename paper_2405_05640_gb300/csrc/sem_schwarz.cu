@@ -158,7 +158,7 @@ static long long qlen(double h) { return std::llround(std::log2(h) * 1024.0); }
 // ---------------------------------------------------------------- kernels
 
 constexpr int kSwWarps = 4;       // elements (one per warp) per CTA of the local solve
-constexpr int kCgThreads = 512;   // coarse CG CTA
+constexpr int kCgThreads = 256;   // coarse CG CTA (256 measured faster than 512 and 1024)
 constexpr int kCgMaxGrid = 1024;  // coarse CG CTAs at most (one per SM)
 
 struct SwArgs {
