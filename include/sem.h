@@ -242,6 +242,12 @@ typedef struct {
     int coarse_iters;      /* Schwarz: coarse-level CG iterations per application
                               (0: one-level Schwarz; 3 suffice on the channel) */
     double coarse_tol;     /* Schwarz: coarse-level relative tolerance (0 = 1e-2) */
+    int outer_pair;        /* SEM_PCG_MIXED: 1 forms the FP64 outer residual b - A x
+                              with the operator in FP32-pair arithmetic (SEM_F64_PAIR,
+                              mesh built with SEM_GEOM_PAIR, else
+                              SEM_ERR_INVALID_ARG): ~2^-42 of the line-wise
+                              magnitudes instead of FP64 rounding, 5x faster on
+                              GB300; 0 (default): the FP64 operator */
 } sem_pcg_opts;
 
 typedef struct {

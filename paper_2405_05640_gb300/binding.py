@@ -52,7 +52,8 @@ class PcgOpts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("h1", ctypes.c_double),
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int),
-                ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double)]
+                ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double),
+                ("outer_pair", ctypes.c_int)]
 
 
 class PcgStats(ctypes.Structure):
@@ -300,7 +301,8 @@ class Mesh:
 
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
-                 mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2) -> PcgOpts:
+                 mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2,
+                 outer_pair=False) -> PcgOpts:
         """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
         preconditioner of the mixed solver), its coarse level solved by
         coarse_iters Jacobi-CG iterations (3: on the 32^3 channel, N = 7, more
@@ -308,6 +310,7 @@ class Mesh:
         o = PcgOpts()
         o.schwarz = schwarz.handle.value if schwarz is not None else None
         o.coarse_iters, o.coarse_tol = int(coarse_iters), float(coarse_tol)
+        o.outer_pair = int(bool(outer_pair))
         o.profile = int(bool(profile))
         o.mixed_restart = int(bool(mixed_restart))
         o.tol, o.tol_is_relative, o.max_iter, o.precision = float(tol), int(relative), int(max_iter), int(precision)

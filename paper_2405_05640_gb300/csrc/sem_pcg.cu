@@ -799,7 +799,7 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
     SEM_CUDA_CHECK(cudaMemsetAsync(M.in.scal, 0, sizeof(PcgScal), st));
     const double *w0 = nullptr;
     if (o->use_initial_guess) {
-        int s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
+        int s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c, o->outer_pair != 0);
         if (s != SEM_OK) return s;
         w0 = M.w64;
     } else {
@@ -850,7 +850,7 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         inner_total = (o->mixed_restart || sw) ? inner_total + hi.iter : hi.iter;
         // x += ||r|| d; r = b - A x in FP64
         ir_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, M.d32, n, M.scal_out);
-        s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c);
+        s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c, o->outer_pair != 0);
         if (s != SEM_OK) return s;
         ir_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(b, M.w64, M.r64, m->minv, n, M.partial_out, M.scal_out,
                                                            o->tol, o->tol_is_relative);
@@ -887,6 +887,8 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_F64_PAIR needs a mesh built with SEM_GEOM_PAIR");
     if (o->precision == SEM_PCG_F64_PAIR && (o->h2 != 0.0 || o->h1 != 1.0))
         return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_F64_PAIR solves the Poisson operator (h1 = 1, h2 = 0)");
+    if (o->outer_pair && (o->precision != SEM_PCG_MIXED || !m->G2))
+        return fail(SEM_ERR_INVALID_ARG, "outer_pair: SEM_PCG_MIXED on a mesh built with SEM_GEOM_PAIR");
     if (o->precision == SEM_PCG_MIXED && !m->G32)
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_MIXED needs a mesh built with SEM_GEOM_F32");
     if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))

@@ -135,3 +135,54 @@ def test_full_size_pcg_schwarz_true_residual():
     rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
     assert rel <= 1.05e-8, rel
     assert st["iters"] < 200, st["iters"]
+
+
+# ------------------------------------------------------------------ FP32-pair outer residual
+
+@pytest.mark.parametrize("case", [inputs.channel(5, 7), inputs.deformed_cube(4, 5)], ids=["channel5", "deformed4"])
+@pytest.mark.parametrize("use_schwarz", [False, True], ids=["jacobi", "schwarz"])
+def test_pcg_mixed_outer_pair_true_residual(case, use_schwarz):
+    """The mixed solver with its FP64 outer residual formed by the FP32-pair
+    operator: the oracle-computed true residual meets the tolerance and the
+    solution matches the FP64 oracle's."""
+    V = case.vertices()
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True, geom_pair=True)
+    kw = {}
+    if use_schwarz:
+        gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+        kw = dict(schwarz=binding.Schwarz(gm, gc), coarse_iters=3)
+    b = om.scatter(case.rhs_global())
+    xo, _, _, _ = om.pcg(b, tol=1e-12, max_iter=20000)
+    xg, st = gm.pcg(_dev(b), tol=1e-10, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-3,
+                    outer_pair=True, **kw)
+    assert st["status"] == 0, st
+    r = b - om.apply(_host(xg))
+    assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 1.05e-10
+    assert _rel(_host(xg), xo) <= 1e-8
+
+
+def test_pcg_outer_pair_needs_pair_geometry():
+    case = SW_CASES[0]
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+    import torch
+    b = torch.ones(gm.nloc, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.SemError) as ei:
+        gm.pcg(b, tol=1e-8, precision=binding.SEM_PCG_MIXED, outer_pair=True)
+    assert ei.value.status == binding.SEM_ERR_INVALID_ARG
+
+
+def test_full_size_pcg_schwarz_outer_pair_true_residual():
+    case = inputs.channel(32, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True, geom_pair=True)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    S = binding.Schwarz(gm, gc)
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    xg, st = gm.pcg(_dev(b), tol=1e-8, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
+                    schwarz=S, coarse_iters=3, coarse_tol=1e-2, outer_pair=True)
+    assert st["status"] == 0
+    r = b - om.apply(_host(xg))
+    rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
+    assert rel <= 1.05e-8, rel
