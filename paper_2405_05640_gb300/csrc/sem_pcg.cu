@@ -590,13 +590,11 @@ static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max
         for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
             // p <- dinv r + beta p; w = A_L p; alpha = rho / <p, w>   (one kernel)
             c.tax.start(st);
-            int s = (sizeof(T) == 4)
-                        ? ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg),
-                                           reinterpret_cast<float *>(W.w), st)
-                        : pair ? ax_cg_launch_pair(m, reinterpret_cast<const CgFuse<double> &>(cg),
-                                                   reinterpret_cast<double *>(W.w), st)
-                               : ax_cg_launch_f64(m, reinterpret_cast<const CgFuse<double> &>(cg),
-                                                  reinterpret_cast<double *>(W.w), h1, h2, st);
+            int s;
+            if constexpr (sizeof(T) == 4)
+                s = ax_cg_launch_f32(m, cg, W.w, st);
+            else
+                s = pair ? ax_cg_launch_pair(m, cg, W.w, st) : ax_cg_launch_f64(m, cg, W.w, h1, h2, st);
             c.tax.stop(st);
             if (s != SEM_OK) return s;
             // w <- M Q Q^T w, axis by axis: the y and z passes here, the x
