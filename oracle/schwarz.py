@@ -26,7 +26,9 @@ The reading implemented here (additive, two levels, symmetric):
   vertices; P interpolates vertex values to the GLL points element by
   element, P^T r sums r / mult into the vertices; A_c^{-1} by CG to 1e-12.
 * Krylov.  Flexible PCG (Polak-Ribiere beta), which also tolerates the
-  inexact coarse solves of the GPU path.
+  inexact coarse solves of the GPU path.  Restarted flexible GMRES (the
+  Krylov method the paper names for the pressure) is here too, to compare
+  the two on the same preconditioner.
 """
 from __future__ import annotations
 
@@ -211,3 +213,57 @@ def fpcg(m: Mesh, b, precond, tol=1e-10, max_iter=5000):
         rz = rz_new
         p = z + beta * p
     return x, max_iter, rel
+
+
+def fgmres(m: Mesh, b, precond, restart=30, tol=1e-10, max_iter=5000):
+    """Restarted flexible GMRES(restart), right-preconditioned (the
+    preconditioned directions z_j = M v_j are kept, x += Z y), modified
+    Gram-Schmidt Arnoldi in the multiplicity-weighted inner product, Givens
+    rotations for the least-squares problem; each cycle restarts from the
+    true residual.  Returns (x, iterations, rel_res)."""
+    x = np.zeros_like(b)
+    bn = math.sqrt(m.glsc3(b, b))
+    if bn == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while True:
+        r = b - m.apply(x)
+        beta = math.sqrt(m.glsc3(r, r))
+        if beta <= tol * bn or it >= max_iter:
+            return x, it, beta / bn
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        k = 0
+        for j in range(restart):
+            z = precond(V[j])
+            Z.append(z)
+            w = m.apply(z)
+            for i in range(j + 1):
+                H[i, j] = m.glsc3(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = math.sqrt(m.glsc3(w, w))
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            if abs(g[j + 1]) <= tol * bn or it >= max_iter or d == 0.0:
+                break
+            V.append(w / math.sqrt(m.glsc3(w, w)))
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        for i in range(k):
+            x = x + y[i] * Z[i]

@@ -74,3 +74,19 @@ def test_workspace_size_accounts_for_all_arrays(lib):
     assert n >= 8 * nloc * 10
     d.geom_flags = binding.SEM_GEOM_F32
     assert lib.sem_mesh_workspace_bytes(ctypes.byref(d)) >= n + 4 * nloc * 8
+
+
+def test_schwarz_and_solver_option_host_checks(lib):
+    """The hybrid Schwarz entry points reject bad arguments before any
+    device work (no GPU needed)."""
+    assert lib.sem_schwarz_workspace_bytes(None, None) == 0
+    out = ctypes.c_void_p()
+    assert lib.sem_schwarz_create(None, None, None, 0, None, ctypes.byref(out)) == binding.SEM_ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.sem_schwarz_apply(None, None, None, 3, 1e-2, None) == binding.SEM_ERR_INVALID_ARG
+    assert lib.sem_schwarz_problems(None) == -1
+    assert lib.sem_schwarz_destroy(None) == binding.SEM_OK
+    # the solver options carry the Schwarz handle, its coarse settings and the
+    # FP32-pair outer-residual switch at the end of the struct
+    names = [f[0] for f in binding.PcgOpts._fields_]
+    assert names[-4:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair"]

@@ -95,3 +95,40 @@ def test_flexible_pcg_converges_faster_to_the_same_solution(case):
     assert st == 0 and rel <= 1e-12
     assert its <= 0.5 * itj, (its, itj)
     assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_fgmres_equals_dense_solve_and_matches_fcg():
+    """Restarted flexible GMRES: without preconditioner on a tiny mesh it
+    reproduces the dense solve (also across restarts); with the hybrid
+    Schwarz preconditioner it reaches the plain solution in about as many
+    iterations as flexible CG (the preconditioner is symmetric positive
+    definite, so CG's short recurrence loses nothing)."""
+    case = inputs.BoxCase("tiny", 3, (2, 2, 1), (0, 0, 0), inputs.ALL_FACES, jitter=0.1, seed=5)
+    V = case.vertices()
+    m = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    A = _dense(m)
+    free = m.apply_mask(np.ones(m.nloc))
+    rng = np.random.default_rng(11)
+    b = m.apply_mask(m.scatter(rng.standard_normal(m.nglob)))
+    first = np.zeros(m.nglob, dtype=np.int64)
+    first[m.gid[::-1]] = np.arange(m.nloc)[::-1]
+    keep = free[first] != 0
+    bg = b[first]
+    xd = np.zeros(m.nglob)
+    xd[keep] = np.linalg.solve(A[np.ix_(keep, keep)], bg[keep])
+    for restart in (200, 7):
+        x, it, rel = sw.fgmres(m, b, lambda r: r, restart=restart, tol=1e-12)
+        assert rel <= 1e-12
+        assert np.abs(x[first] - xd).max() <= 1e-9 * np.abs(xd).max(), restart
+    case = inputs.channel(4, 5)
+    V = case.vertices()
+    H = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V)
+    m = H.m
+    b = m.scatter(case.rhs_global())
+    xo, itj, _, _ = m.pcg(b, tol=1e-10, max_iter=20000)
+    xf, itf, relf = sw.fpcg(m, b, H.apply, tol=1e-10)
+    xg, itg, relg = sw.fgmres(m, b, H.apply, restart=30, tol=1e-10)
+    assert relg <= 1e-10
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert itg <= 1.5 * itf and itf <= 1.5 * itg, (itg, itf)
+    assert itg <= 0.5 * itj, (itg, itj)
