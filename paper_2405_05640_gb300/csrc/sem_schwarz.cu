@@ -20,20 +20,22 @@
 // GB300 design (FP32, the inner solver's precision): the 1-D eigenproblems
 // are solved once on the host (Cholesky + cyclic Jacobi) and cached by their
 // key (lengths and boundary flags: a tensor-product mesh has few distinct
-// ones).  One warp per element gathers the extended residual from its
-// neighbours with computed indices (box topology) into a padded shared block
-// (strides chosen so the lanes' line accesses meet few bank conflicts along
-// all three directions), each lane owning whole 1-D lines: a contraction
-// reads the lane's lines once and the table rows as broadcast 16-byte loads,
-// so shared traffic is ~1/3 of one load per multiply-add.  The same warp
-// restricts the residual to the element vertices.  The coarse problem is
-// assembled once into a 27-point stencil on the global vertex grid and solved
-// by one cooperative kernel (Jacobi-CG, two grid barriers per iteration, the
-// search direction double-buffered so the operator rebuilds it on the fly).
-// A last kernel, one CTA per element, sums each point's value over the (up
-// to 2 x 2 x 2) overlapping subdomains in a fixed order and adds the
-// trilinear prolongation of the coarse solution: deterministic, copies of a
-// node bit-identical, no atomics.
+// ones).  One warp per element, each lane owning whole 1-D lines: the K
+// forward pass reads the extended residual straight from global memory
+// (neighbour offsets computed from the box topology) and also restricts it
+// to the element vertices; the J and I passes run through a padded shared
+// block whose lines are dealt to the lanes by per-pass tables that avoid
+// bank conflicts (the I pass does forward, division and backward in
+// registers); the K backward pass stores straight to global memory.  Table
+// rows are broadcast 16-byte loads and the multiply-adds packed FP32x2.  The
+// coarse problem is assembled once into a 27-point stencil on the global
+// vertex grid and solved by one cooperative kernel (Jacobi-CG, two grid
+// barriers per iteration, the search direction double-buffered so the
+// operator rebuilds it on the fly).  A last kernel, one thread per (i, j)
+// column of an element, sums each point's value over the (up to 2 x 2 x 2)
+// overlapping subdomains in a fixed order and adds the trilinear
+// prolongation of the coarse solution: deterministic, copies of a node
+// bit-identical, no atomics.
 
 #include <algorithm>
 #include <cmath>
