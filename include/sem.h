@@ -492,6 +492,25 @@ int sem_schwarz_create(const sem_mesh *mesh, const sem_mesh *coarse, void *d_wor
 int sem_schwarz_destroy(sem_schwarz *sw);
 /* Number of distinct 1-D eigenproblems solved at set-up. */
 int sem_schwarz_problems(const sem_schwarz *sw);
+/* The set-up's 1-D problem of one direction of an extended element (host
+ * computation, no GPU): stiffness and mass of the left neighbour, the
+ * element and the right neighbour (lengths hL, h, hR > 0) on the N + 3
+ * extended GLL points; flags bit 0: a left neighbour exists, bit 1: a right
+ * one, bit 2: the element's low face is Dirichlet, bit 3: its high face (such
+ * points are decoupled as identity rows).  Writes S[(N+3)^2] (row-major, row
+ * = point, column = mode; S^T B S = I) and lambda[N+3] (A S = B S Lambda,
+ * unsorted).  SEM_ERR_UNSUPPORTED outside 2 <= N <= 9, SEM_ERR_INVALID_ARG
+ * for NULL outputs, lengths <= 0 or unknown flags. */
+int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double *S, double *lambda);
+/* The local-solve kernel's line tables for order N (host, no GPU): for each
+ * of the three line directions (along I, J, K), *slots = 32 LPT entries (LPT
+ * lines per lane) holding the line dealt to (group q = slot / 32, lane =
+ * slot % 32), or -1; line id c1 + (N+3) c2 with (c1, c2) = (J, K), (I, K),
+ * (I, J).  The I and J tables spread the lines' shared-memory banks; the K
+ * passes use the natural order (slot = line).  *pj, *pk: the shared-block
+ * strides the tables were built for.  out needs 3 *slots shorts (cap: its
+ * length; SEM_ERR_WORKSPACE if smaller). */
+int sem_schwarz_line_table(int N, short *out, int cap, int *slots, int *pj, int *pk);
 /* z = M r (device FP32 E-layout, r continuous and zero on Dirichlet nodes;
  * z continuous, every copy of a node bit-identical, zero on Dirichlet
  * nodes).  Stream-ordered, no host synchronisation; three kernels (local

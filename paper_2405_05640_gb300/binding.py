@@ -149,6 +149,9 @@ _SIGS = {
     "sem_schwarz_create": ([_VP, _VP, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "sem_schwarz_destroy": ([_VP], ctypes.c_int),
     "sem_schwarz_problems": ([_VP], ctypes.c_int),
+    "sem_schwarz_fdm_1d": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP],
+                           ctypes.c_int),
+    "sem_schwarz_line_table": ([ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
     "sem_schwarz_apply": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP], ctypes.c_int),
     "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
                        ctypes.c_int),
@@ -647,6 +650,28 @@ def perf_model(P_opt, C, C_max=None):
     check(lib().sem_perf_model(len(P), _VP(P.ctypes.data), None if cap is None else _VP(cap.ctypes.data),
                                float(C), ctypes.byref(t), _VP(out.ctypes.data)), "sem_perf_model")
     return t.value, out
+
+
+def schwarz_fdm_1d(N, h, hL, hR, flags):
+    """sem_schwarz_fdm_1d: (S[(N+3), (N+3)], lambda[N+3]) of one direction of
+    an extended element (host computation)."""
+    import numpy as np
+    ne = N + 3
+    S = np.zeros(ne * ne)
+    lam = np.zeros(ne)
+    check(lib().sem_schwarz_fdm_1d(int(N), float(h), float(hL), float(hR), int(flags),
+                                   S.ctypes.data_as(_VP), lam.ctypes.data_as(_VP)), "sem_schwarz_fdm_1d")
+    return S.reshape(ne, ne), lam
+
+
+def schwarz_line_table(N):
+    """sem_schwarz_line_table: (table[3][slots], PJ, PK)."""
+    import numpy as np
+    out = np.zeros(3 * 32 * 5, dtype=np.int16)
+    slots, pj, pk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().sem_schwarz_line_table(int(N), out.ctypes.data_as(_VP), out.size, ctypes.byref(slots),
+                                       ctypes.byref(pj), ctypes.byref(pk)), "sem_schwarz_line_table")
+    return out[:3 * slots.value].reshape(3, slots.value), pj.value, pk.value
 
 
 class Schwarz:

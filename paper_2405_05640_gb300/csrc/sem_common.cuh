@@ -230,6 +230,11 @@ int dealias_metric_launch(const sem_mesh *m, double *W, cudaStream_t st);
 int advect_weak_launch(const sem_mesh *m, const double *W, const double *const u[3], double *const out[3],
                        cudaStream_t st);
 
+// Host GLL data of order N (sem_mesh.cu): nodes, weights, D_ij = l_j'(xi_i)
+// (row-major, (N+1)^2).
+void gll_host(int N, double *xi, double *rho);
+void deriv_host(int N, const double *x, double *D);
+
 // Hybrid Schwarz preconditioner (sem_schwarz.cu): z = M r in FP32; done
 // (optional device flag): set -> the kernels return at once.
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,

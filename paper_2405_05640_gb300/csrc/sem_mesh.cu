@@ -50,7 +50,7 @@ static void legendre_pair(int N, double x, double *PN, double *PNm1) {
     *PNm1 = a;
 }
 
-static void gll_host(int N, double *xi, double *rho) {
+void gll_host(int N, double *xi, double *rho) {
     for (int i = 0; i <= N; ++i) {
         double x = -std::cos(M_PI * i / N);
         if (i > 0 && i < N) {
@@ -79,7 +79,7 @@ static void gll_host(int N, double *xi, double *rho) {
 
 // D_ij = l_j'(xi_i) by the barycentric formula: lambda_j = 1/prod_{k!=j}(x_j-x_k),
 // D_ij = (lambda_j/lambda_i)/(x_i-x_j), D_ii = -sum_{j!=i} D_ij.
-static void deriv_host(int N, const double *x, double *D) {
+void deriv_host(int N, const double *x, double *D) {
     const int n1 = N + 1;
     double lam[kMaxN1];
     for (int j = 0; j < n1; ++j) {

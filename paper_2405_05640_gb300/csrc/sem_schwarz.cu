@@ -157,6 +157,54 @@ struct FdmKey {
 };
 static long long qlen(double h) { return std::llround(std::log2(h) * 1024.0); }
 
+// Reference 1-D stiffness Ah[i][j] = sum_q D_qi rho_q D_qj and mass weights
+// Bh[i] = rho_i on [-1, 1].
+static void ref_1d(int N, const double *rho, const double *D, double *Ah, double *Bh) {
+    const int n1 = N + 1;
+    for (int i = 0; i < n1; ++i) {
+        Bh[i] = rho[i];
+        for (int j = 0; j < n1; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < n1; ++q) s += D[q * n1 + i] * rho[q] * D[q * n1 + j];
+            Ah[i * n1 + j] = s;
+        }
+    }
+}
+
+// The 1-D problem of an extended element along one axis (N + 3 points):
+// stiffness and mass of the left neighbour, the element and the right
+// neighbour (lengths hL, h, hR) assembled on 3N + 1 points and restricted to
+// the N + 3 extended ones; a point without a neighbour (hasL / hasR false)
+// and a Dirichlet boundary point (dirL / dirR) decoupled as identity rows;
+// then A S = B S Lambda by gen_eig.
+static void fdm_1d(int N, const double *Ah, const double *Bh, double h, double hL, double hR, bool hasL, bool hasR,
+                   bool dirL, bool dirR, double *S, double *lam) {
+    const int n1 = N + 1, ne = N + 3, M3 = 3 * N + 1;
+    std::vector<double> Af(M3 * M3, 0.0), Bf(M3 * M3, 0.0), A(ne * ne), B(ne * ne);
+    const double hh[3] = {hL, h, hR};
+    for (int q = 0; q < 3; ++q)
+        for (int i = 0; i < n1; ++i) {
+            const int gi = q * N + i;
+            Bf[gi * M3 + gi] += 0.5 * hh[q] * Bh[i];
+            for (int j = 0; j < n1; ++j) Af[gi * M3 + q * N + j] += (2.0 / hh[q]) * Ah[i * n1 + j];
+        }
+    for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < ne; ++j) {
+            A[i * ne + j] = Af[(N - 1 + i) * M3 + (N - 1 + j)];
+            B[i * ne + j] = Bf[(N - 1 + i) * M3 + (N - 1 + j)];
+        }
+    const int dead[4] = {!hasL ? 0 : -1, dirL ? 1 : -1, !hasR ? ne - 1 : -1, dirR ? ne - 2 : -1};
+    for (int d : dead) {
+        if (d < 0) continue;
+        for (int q = 0; q < ne; ++q) {
+            A[d * ne + q] = A[q * ne + d] = 0.0;
+            B[d * ne + q] = B[q * ne + d] = 0.0;
+        }
+        A[d * ne + d] = B[d * ne + d] = 1.0;
+    }
+    gen_eig(ne, A.data(), B.data(), S, lam);
+}
+
 // ---------------------------------------------------------------- kernels
 
 constexpr int kSwWarps = 4;       // elements (one per warp) per CTA of the local solve
@@ -978,16 +1026,20 @@ static CoarseTopo coarse_topo(const sem_mesh *m) {
     return C;
 }
 
-// Deal the NE^2 lines of each pass to (group q, lane) slots: lines in bank
-// order, each to the group holding the fewest lines of its bank so far (then
-// the emptiest), at most 32 per group; a group then meets a bank conflict
-// only where a bank holds more than LPT line starts.
+// Deal the NE^2 lines of the I and J passes to (group q, lane) slots: lines
+// in bank order, each to the group holding the fewest lines of its bank so
+// far (then the emptiest), at most 32 per group; a group then meets a bank
+// conflict only where a bank holds more than LPT line starts.  The K passes
+// read and write global memory and keep the natural order (slot = line), so
+// that a warp's accesses for one K are 32 consecutive points; table 2 records
+// that order.
 template <int N>
 static void line_table(std::vector<short> &tab) {
     using S = SwShape<N>;
     constexpr int NE = S::NE, LPT = S::LPT;
     tab.assign(3 * S::SLOTS, (short)-1);
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int id = 0; id < S::NE2; ++id) tab[2 * S::SLOTS + id] = (short)id;
+    for (int ax = 0; ax < 2; ++ax) {
         std::vector<std::pair<int, int>> byb;  // (bank, line)
         for (int id = 0; id < S::NE2; ++id) {
             const int c1 = id % NE, c2 = id / NE;
@@ -1176,21 +1228,12 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
         }
     // reference 1-D stiffness and mass
     std::vector<double> Ah(n1 * n1, 0.0), Bh(n1, 0.0);
-    for (int i = 0; i < n1; ++i) {
-        Bh[i] = m->rho[i];
-        for (int j = 0; j < n1; ++j) {
-            double s = 0.0;
-            for (int q = 0; q < n1; ++q) s += m->D.d[q * n1 + i] * m->rho[q] * m->D.d[q * n1 + j];
-            Ah[i * n1 + j] = s;
-        }
-    }
+    ref_1d(N, m->rho, m->D.d, Ah.data(), Bh.data());
     std::map<FdmKey, int> cache;
     std::vector<float> Stab, Ltab;
     std::vector<int> prob(3 * E);
     const int stride[3] = {1, m->nel[0], m->nel[0] * m->nel[1]};
-    std::vector<double> A(ne * ne), B(ne * ne), Sd(ne * ne), ld(ne);
-    const int M3 = 3 * N + 1;
-    std::vector<double> Af(M3 * M3), Bf(M3 * M3);
+    std::vector<double> Sd(ne * ne), ld(ne);
     for (int64_t e = 0; e < E; ++e) {
         const int coord[3] = {(int)(e % m->nel[0]), (int)((e / m->nel[0]) % m->nel[1]),
                               (int)(e / ((int64_t)m->nel[0] * m->nel[1]))};
@@ -1209,30 +1252,7 @@ int sem_schwarz_create(const sem_mesh *m, const sem_mesh *mc, void *ws, size_t b
                 prob[3 * e + a] = it->second;
                 continue;
             }
-            std::fill(Af.begin(), Af.end(), 0.0);
-            std::fill(Bf.begin(), Bf.end(), 0.0);
-            const double hh[3] = {hL, h, hR};
-            for (int q = 0; q < 3; ++q)
-                for (int i = 0; i < n1; ++i) {
-                    const int gi = q * N + i;
-                    Bf[gi * M3 + gi] += 0.5 * hh[q] * Bh[i];
-                    for (int j = 0; j < n1; ++j) Af[gi * M3 + q * N + j] += (2.0 / hh[q]) * Ah[i * n1 + j];
-                }
-            for (int i = 0; i < ne; ++i)
-                for (int j = 0; j < ne; ++j) {
-                    A[i * ne + j] = Af[(N - 1 + i) * M3 + (N - 1 + j)];
-                    B[i * ne + j] = Bf[(N - 1 + i) * M3 + (N - 1 + j)];
-                }
-            const int dead[4] = {!hasL ? 0 : -1, dirL ? 1 : -1, !hasR ? ne - 1 : -1, dirR ? ne - 2 : -1};
-            for (int d : dead) {
-                if (d < 0) continue;
-                for (int q = 0; q < ne; ++q) {
-                    A[d * ne + q] = A[q * ne + d] = 0.0;
-                    B[d * ne + q] = B[q * ne + d] = 0.0;
-                }
-                A[d * ne + d] = B[d * ne + d] = 1.0;
-            }
-            gen_eig(ne, A.data(), B.data(), Sd.data(), ld.data());
+            fdm_1d(N, Ah.data(), Bh.data(), h, hL, hR, hasL, hasR, dirL, dirR, Sd.data(), ld.data());
             const int id = (int)(Ltab.size() / ne);
             for (int q = 0; q < ne * ne; ++q) Stab.push_back((float)Sd[q]);
             for (int q = 0; q < ne; ++q) Ltab.push_back((float)ld[q]);
@@ -1311,6 +1331,39 @@ int sem_schwarz_destroy(sem_schwarz *sw) {
 }
 
 int sem_schwarz_problems(const sem_schwarz *sw) { return sw ? sw->P : -1; }
+
+int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double *S, double *lambda) {
+    if (N < 2 || N > 9) return fail(SEM_ERR_UNSUPPORTED, "Schwarz preconditioner built for 2 <= N <= 9");
+    if (!S || !lambda || !(h > 0.0) || !(hL > 0.0) || !(hR > 0.0) || (flags & ~15))
+        return fail(SEM_ERR_INVALID_ARG, "NULL output, non-positive length or unknown flag");
+    double xi[kMaxN1], rho[kMaxN1], D[kMaxN1 * kMaxN1], Ah[kMaxN1 * kMaxN1], Bh[kMaxN1];
+    gll_host(N, xi, rho);
+    deriv_host(N, xi, D);
+    ref_1d(N, rho, D, Ah, Bh);
+    fdm_1d(N, Ah, Bh, h, hL, hR, flags & 1, flags & 2, flags & 4, flags & 8, S, lambda);
+    return SEM_OK;
+}
+
+int sem_schwarz_line_table(int N, short *out, int cap, int *slots, int *pj, int *pk) {
+    if (N < 2 || N > 9) return fail(SEM_ERR_UNSUPPORTED, "Schwarz preconditioner built for 2 <= N <= 9");
+    if (!out || !slots || !pj || !pk) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    std::vector<short> t;
+    line_table_n(N, t);
+    if (cap < (int)t.size()) return fail(SEM_ERR_WORKSPACE, "line table larger than cap");
+    std::copy(t.begin(), t.end(), out);
+    *slots = (int)t.size() / 3;
+    switch (N) {
+#define SEM_LT_CASE(n)              \
+    case n:                         \
+        *pj = SwShape<n>::PJ;       \
+        *pk = SwShape<n>::PK;       \
+        break;
+        SEM_LT_CASE(2) SEM_LT_CASE(3) SEM_LT_CASE(4) SEM_LT_CASE(5) SEM_LT_CASE(6) SEM_LT_CASE(7)
+        SEM_LT_CASE(8) SEM_LT_CASE(9)
+#undef SEM_LT_CASE
+    }
+    return SEM_OK;
+}
 
 int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
                       void *stream) {
