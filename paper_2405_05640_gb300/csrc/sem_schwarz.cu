@@ -38,6 +38,7 @@
 // bit-identical, no atomics.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -1115,13 +1116,17 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
     const SwArgs A = sw_args(m);
     const bool coarse = coarse_iters > 0;
     const size_t smem = sizeof(float) * kSwWarps * S::WARP_FLOATS + sizeof(short) * 3 * S::SLOTS;
-    static int per_sm = 0;  // resident CTAs per SM of this instantiation (device-independent shape)
+    // resident CTAs per SM of this instantiation, queried once (concurrent
+    // first callers store the same value)
+    static std::atomic<int> per_sm_cache{0};
+    int per_sm = per_sm_cache.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         SEM_CUDA_CHECK(cudaFuncSetAttribute(schwarz_local_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_local_kernel<N>,
                                                                      kSwWarps * 32, smem));
         if (per_sm < 1) per_sm = 1;
+        per_sm_cache.store(per_sm, std::memory_order_relaxed);
     }
     int64_t g = (m->E + kSwWarps - 1) / kSwWarps;
     if (g > (int64_t)m->num_sms * per_sm) g = (int64_t)m->num_sms * per_sm;
@@ -1147,9 +1152,12 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
         P.C = C;
         P.iters = coarse_iters;
         P.tol2 = coarse_tol * coarse_tol;
-        static int cg_per_sm = 0;
-        if (cg_per_sm == 0)
+        static std::atomic<int> cg_cache{0};
+        int cg_per_sm = cg_cache.load(std::memory_order_relaxed);
+        if (cg_per_sm == 0) {
             SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cg_per_sm, coarse_cg_kernel, kCgThreads, 0));
+            cg_cache.store(cg_per_sm, std::memory_order_relaxed);
+        }
         int gc = (C.nvt + kCgThreads - 1) / kCgThreads;
         gc = std::min(gc, std::min(m->num_sms * std::max(cg_per_sm, 1), kCgMaxGrid));
         gc = std::min(gc, m->num_sms);
