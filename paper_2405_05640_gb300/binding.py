@@ -696,7 +696,9 @@ class Schwarz:
             _lib.sem_schwarz_destroy(h)
             self.handle = None
 
-    def apply(self, r, coarse_iters=0, coarse_tol=1e-3, z=None):
+    def apply(self, r, coarse_iters=3, coarse_tol=1e-2, z=None):
+        """z = M r (sem_schwarz_apply), FP32 E-layout tensors; coarse_iters = 0:
+        the one-level (local solves only) preconditioner."""
         import torch
         if z is None:
             z = torch.empty_like(r)
