@@ -189,6 +189,13 @@ class HybridSchwarz:
             z = z + self.cl.apply(r)
         return self.m.apply_mask(z)
 
+    def apply_multiplicative(self, r):
+        """The levels one after the other: the coarse correction x_c, then
+        the local solves on the updated residual r - A x_c (one more
+        operator application per preconditioning step)."""
+        xc = self.m.apply_mask(self.cl.apply(r))
+        return self.m.apply_mask(xc + self.sw.apply(r - self.m.apply(xc)))
+
 
 def fpcg(m: Mesh, b, precond, tol=1e-10, max_iter=5000):
     """Flexible PCG (Polak-Ribiere beta); returns (x, iterations, rel_res)."""
