@@ -502,6 +502,18 @@ int sem_schwarz_problems(const sem_schwarz *sw);
  * unsorted).  SEM_ERR_UNSUPPORTED outside 2 <= N <= 9, SEM_ERR_INVALID_ARG
  * for NULL outputs, lengths <= 0 or unknown flags. */
 int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double *S, double *lambda);
+/* The coarse operator the set-up assembles, computed on the host by the
+ * same code (no GPU): from the N = 1 geometric factors G[E][6][8] (FP64,
+ * rr, ss, tt, rs, rt, st at the element vertices, quadrature weights
+ * included; E = nel[0] nel[1] nel[2], elements x fastest), the 27-point
+ * stencil sten[27][nv] (offset (ox, oy, oz) in {-1,0,1}^3 at index
+ * (ox+1) + 3(oy+1) + 9(oz+1); vertex v = vx + nv0 (vy + nv1 vz), nv_a =
+ * nel_a + (periodic_a ? 0 : 1), nv = nv0 nv1 nv2) with rows and columns of
+ * Dirichlet vertices (faces bits as in sem_mesh_desc) zeroed, and cdinv[nv]
+ * = 1 / assembled diagonal (0 on Dirichlet vertices).  FP32 outputs, host
+ * arrays owned by the caller.  SEM_ERR_INVALID_ARG for NULL or nel < 1. */
+int sem_schwarz_coarse_operator(const int *nel, const int *periodic, int faces, const double *G, float *sten,
+                                float *cdinv);
 /* The local-solve kernel's line tables for order N (host, no GPU): for each
  * of the three line directions (along I, J, K), *slots = 32 LPT entries (LPT
  * lines per lane) holding the line dealt to (group q = slot / 32, lane =

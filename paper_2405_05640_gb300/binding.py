@@ -152,6 +152,7 @@ _SIGS = {
     "sem_schwarz_fdm_1d": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP],
                            ctypes.c_int),
     "sem_schwarz_line_table": ([ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "sem_schwarz_coarse_operator": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
     "sem_schwarz_apply": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP], ctypes.c_int),
     "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
                        ctypes.c_int),
@@ -662,6 +663,22 @@ def schwarz_fdm_1d(N, h, hL, hR, flags):
     check(lib().sem_schwarz_fdm_1d(int(N), float(h), float(hL), float(hR), int(flags),
                                    S.ctypes.data_as(_VP), lam.ctypes.data_as(_VP)), "sem_schwarz_fdm_1d")
     return S.reshape(ne, ne), lam
+
+
+def schwarz_coarse_operator(nel, periodic, faces, G):
+    """sem_schwarz_coarse_operator: (sten[27][nv], cdinv[nv]) from the N = 1
+    geometric factors G[E][6][8] (host computation)."""
+    import numpy as np
+    nel_a = np.ascontiguousarray(nel, dtype=np.int32)
+    per = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)
+    nv = int(np.prod([n + (0 if p else 1) for n, p in zip(nel, periodic)]))
+    Gc = np.ascontiguousarray(G, dtype=np.float64)
+    sten = np.zeros((27, nv), dtype=np.float32)
+    cdinv = np.zeros(nv, dtype=np.float32)
+    check(lib().sem_schwarz_coarse_operator(nel_a.ctypes.data_as(_VP), per.ctypes.data_as(_VP), int(faces),
+                                            Gc.ctypes.data_as(_VP), sten.ctypes.data_as(_VP),
+                                            cdinv.ctypes.data_as(_VP)), "sem_schwarz_coarse_operator")
+    return sten, cdinv
 
 
 def schwarz_line_table(N):

@@ -753,43 +753,47 @@ __global__ void __launch_bounds__(256, 3)
 // G[e][6][8] (rr, ss, tt, rs, rt, st at the 8 vertices, quadrature weights
 // included): Ae[e][p][j] = sum_q grad phi_p(q) . G(q) grad phi_j(q), with
 // d phi_j / dr at vertex q = +-1/2 where q agrees with j off that axis.
+// Column j of one element (Ge: its 48 factors, Ae_e: its 64 entries).  Host
+// and device: the set-up kernel and the host query run this same code.
+__host__ __device__ __forceinline__ void coarse_elem_col(const double *Ge, int j, float *Ae_e) {
+    double col[8] = {};
+    for (int q = 0; q < 8; ++q) {
+        double gj[3];
+        for (int a = 0; a < 3; ++a) {
+            const int mask = 7 & ~(1 << a);
+            gj[a] = ((q ^ j) & mask) ? 0.0 : (((j >> a) & 1) ? 0.5 : -0.5);
+        }
+        const double grr = Ge[q], gss = Ge[8 + q], gtt = Ge[16 + q], grs = Ge[24 + q], grt = Ge[32 + q],
+                     gst = Ge[40 + q];
+        const double v0 = grr * gj[0] + grs * gj[1] + grt * gj[2];
+        const double v1 = grs * gj[0] + gss * gj[1] + gst * gj[2];
+        const double v2 = grt * gj[0] + gst * gj[1] + gtt * gj[2];
+        for (int p = 0; p < 8; ++p) {
+            double gp[3];
+            for (int a = 0; a < 3; ++a) {
+                const int mask = 7 & ~(1 << a);
+                gp[a] = ((q ^ p) & mask) ? 0.0 : (((p >> a) & 1) ? 0.5 : -0.5);
+            }
+            col[p] += gp[0] * v0 + gp[1] * v1 + gp[2] * v2;
+        }
+    }
+    for (int p = 0; p < 8; ++p) Ae_e[p * 8 + j] = (float)col[p];
+}
+
 __global__ void coarse_elem_kernel(const double *__restrict__ G, int E, float *__restrict__ Ae) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)E * 8;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = t / 8;
-        const int j = (int)(t - e * 8);
-        const double *Ge = G + e * 48;
-        double col[8] = {};
-        for (int q = 0; q < 8; ++q) {
-            double gj[3];
-            for (int a = 0; a < 3; ++a) {
-                const int mask = 7 & ~(1 << a);
-                gj[a] = ((q ^ j) & mask) ? 0.0 : (((j >> a) & 1) ? 0.5 : -0.5);
-            }
-            const double grr = Ge[q], gss = Ge[8 + q], gtt = Ge[16 + q], grs = Ge[24 + q], grt = Ge[32 + q],
-                         gst = Ge[40 + q];
-            const double v0 = grr * gj[0] + grs * gj[1] + grt * gj[2];
-            const double v1 = grs * gj[0] + gss * gj[1] + gst * gj[2];
-            const double v2 = grt * gj[0] + gst * gj[1] + gtt * gj[2];
-            for (int p = 0; p < 8; ++p) {
-                double gp[3];
-                for (int a = 0; a < 3; ++a) {
-                    const int mask = 7 & ~(1 << a);
-                    gp[a] = ((q ^ p) & mask) ? 0.0 : (((p >> a) & 1) ? 0.5 : -0.5);
-                }
-                col[p] += gp[0] * v0 + gp[1] * v1 + gp[2] * v2;
-            }
-        }
-        for (int p = 0; p < 8; ++p) Ae[e * 64 + p * 8 + j] = (float)col[p];
+        coarse_elem_col(G + e * 48, (int)(t - e * 8), Ae + e * 64);
     }
 }
 
-__device__ __forceinline__ bool vertex_masked(const CoarseTopo &C, int v, int a) {
+__host__ __device__ __forceinline__ bool vertex_masked(const CoarseTopo &C, int v, int a) {
     return !C.per[a] && ((v == 0 && ((C.faces >> (2 * a)) & 1)) || (v == C.nv[a] - 1 && ((C.faces >> (2 * a + 1)) & 1)));
 }
 
 // Neighbour coordinate v + o along an axis (periodic wrap); -1 outside.
-__device__ __forceinline__ int nb_coord(int v, int o, int nv, int per) {
+__host__ __device__ __forceinline__ int nb_coord(int v, int o, int nv, int per) {
     int w = v + o;
     if (per) w = (w + nv) % nv;
     return (w < 0 || w >= nv) ? -1 : w;
@@ -797,7 +801,7 @@ __device__ __forceinline__ int nb_coord(int v, int o, int nv, int per) {
 
 // Element coordinate of the element holding vertex coordinate v at local
 // vertex s (0 or 1); -1 if none.
-__device__ __forceinline__ int elem_coord(int v, int s, int nel, int per) {
+__host__ __device__ __forceinline__ int elem_coord(int v, int s, int nel, int per) {
     int c = v - s;
     if (per) c = (c + nel) % nel;
     return (c < 0 || c >= nel) ? -1 : c;
@@ -807,45 +811,50 @@ __device__ __forceinline__ int elem_coord(int v, int s, int nel, int per) {
 // sten[o][v] = sum over the (up to 8) elements e holding v at local vertex s
 // (s in a fixed order) of Ae[e][s][s + o] for s + o in {0,1}^3 (periodic
 // aliases included); rows and columns of Dirichlet vertices zeroed; cdinv the
-// inverse of the assembled diagonal (0 on Dirichlet vertices).
+// inverse of the assembled diagonal (0 on Dirichlet vertices).  One vertex;
+// host and device.
+__host__ __device__ __forceinline__ void coarse_stencil_row(const float *Ae, const CoarseTopo &C, int v, float *sten,
+                                                            float *cdinv) {
+    const int vc[3] = {v % C.nv[0], (v / C.nv[0]) % C.nv[1], v / (C.nv[0] * C.nv[1])};
+    const bool mv = vertex_masked(C, vc[0], 0) || vertex_masked(C, vc[1], 1) || vertex_masked(C, vc[2], 2);
+    double diag = 0.0;
+    for (int o = 0; o < 27; ++o) {
+        const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+        int nc[3];
+        bool ok = true, mn = false;
+        for (int a = 0; a < 3; ++a) {
+            nc[a] = nb_coord(vc[a], od[a], C.nv[a], C.per[a]);
+            ok = ok && nc[a] >= 0;
+        }
+        double sum = 0.0;
+        if (ok) {
+            for (int a = 0; a < 3; ++a) mn = mn || vertex_masked(C, nc[a], a);
+            for (int s = 0; s < 8; ++s) {
+                const int sd[3] = {s & 1, (s >> 1) & 1, s >> 2};
+                int ec[3], td = 0;
+                bool in = true;
+                for (int a = 0; a < 3; ++a) {
+                    ec[a] = elem_coord(vc[a], sd[a], C.nel[a], C.per[a]);
+                    const int ta = sd[a] + od[a];
+                    in = in && ec[a] >= 0 && ta >= 0 && ta <= 1;
+                    td |= (ta & 1) << a;
+                }
+                if (!in) continue;
+                const int64_t e = ec[0] + (int64_t)C.nel[0] * (ec[1] + (int64_t)C.nel[1] * ec[2]);
+                sum += Ae[e * 64 + s * 8 + td];
+            }
+            const int nbv = nc[0] + C.nv[0] * (nc[1] + C.nv[1] * nc[2]);
+            if (nbv == v) diag += sum;
+        }
+        sten[(int64_t)o * C.nvt + v] = (ok && !mv && !mn) ? (float)sum : 0.f;
+    }
+    cdinv[v] = (mv || !(diag > 0.0)) ? 0.f : (float)(1.0 / diag);
+}
+
 __global__ void coarse_stencil_kernel(const float *__restrict__ Ae, CoarseTopo C, float *__restrict__ sten,
                                       float *__restrict__ cdinv) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < C.nvt; v += gridDim.x * blockDim.x) {
-        const int vc[3] = {v % C.nv[0], (v / C.nv[0]) % C.nv[1], v / (C.nv[0] * C.nv[1])};
-        const bool mv = vertex_masked(C, vc[0], 0) || vertex_masked(C, vc[1], 1) || vertex_masked(C, vc[2], 2);
-        double diag = 0.0;
-        for (int o = 0; o < 27; ++o) {
-            const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-            int nc[3];
-            bool ok = true, mn = false;
-            for (int a = 0; a < 3; ++a) {
-                nc[a] = nb_coord(vc[a], od[a], C.nv[a], C.per[a]);
-                ok = ok && nc[a] >= 0;
-            }
-            double sum = 0.0;
-            if (ok) {
-                for (int a = 0; a < 3; ++a) mn = mn || vertex_masked(C, nc[a], a);
-                for (int s = 0; s < 8; ++s) {
-                    const int sd[3] = {s & 1, (s >> 1) & 1, s >> 2};
-                    int ec[3], td = 0;
-                    bool in = true;
-                    for (int a = 0; a < 3; ++a) {
-                        ec[a] = elem_coord(vc[a], sd[a], C.nel[a], C.per[a]);
-                        const int ta = sd[a] + od[a];
-                        in = in && ec[a] >= 0 && ta >= 0 && ta <= 1;
-                        td |= (ta & 1) << a;
-                    }
-                    if (!in) continue;
-                    const int64_t e = ec[0] + (int64_t)C.nel[0] * (ec[1] + (int64_t)C.nel[1] * ec[2]);
-                    sum += Ae[e * 64 + s * 8 + td];
-                }
-                const int nbv = nc[0] + C.nv[0] * (nc[1] + C.nv[1] * nc[2]);
-                if (nbv == v) diag += sum;
-            }
-            sten[(int64_t)o * C.nvt + v] = (ok && !mv && !mn) ? (float)sum : 0.f;
-        }
-        cdinv[v] = (mv || !(diag > 0.0)) ? 0.f : (float)(1.0 / diag);
-    }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < C.nvt; v += gridDim.x * blockDim.x)
+        coarse_stencil_row(Ae, C, v, sten, cdinv);
 }
 
 struct CoarseArgs {
@@ -1014,18 +1023,20 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
 
 // ---------------------------------------------------------------- host side
 
-static CoarseTopo coarse_topo(const sem_mesh *m) {
+static CoarseTopo coarse_topo(const int *nel, const int *periodic, int faces) {
     CoarseTopo C;
     C.nvt = 1;
     for (int a = 0; a < 3; ++a) {
-        C.nel[a] = m->nel[a];
-        C.per[a] = m->periodic[a];
-        C.nv[a] = m->nel[a] + (m->periodic[a] ? 0 : 1);
+        C.nel[a] = nel[a];
+        C.per[a] = periodic[a] ? 1 : 0;
+        C.nv[a] = nel[a] + (periodic[a] ? 0 : 1);
         C.nvt *= C.nv[a];
     }
-    C.faces = m->faces;
+    C.faces = faces;
     return C;
 }
+
+static CoarseTopo coarse_topo(const sem_mesh *m) { return coarse_topo(m->nel, m->periodic, m->faces); }
 
 // Deal the NE^2 lines of the I and J passes to (group q, lane) slots: lines
 // in bank order, each to the group holding the fewest lines of its bank so
@@ -1349,6 +1360,20 @@ int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double 
     deriv_host(N, xi, D);
     ref_1d(N, rho, D, Ah, Bh);
     fdm_1d(N, Ah, Bh, h, hL, hR, flags & 1, flags & 2, flags & 4, flags & 8, S, lambda);
+    return SEM_OK;
+}
+
+int sem_schwarz_coarse_operator(const int *nel, const int *periodic, int faces, const double *G, float *sten,
+                                float *cdinv) {
+    if (!nel || !periodic || !G || !sten || !cdinv) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (nel[a] < 1) return fail(SEM_ERR_INVALID_ARG, "nel < 1");
+    const CoarseTopo C = coarse_topo(nel, periodic, faces);
+    const int64_t E = (int64_t)nel[0] * nel[1] * nel[2];
+    std::vector<float> Ae(64 * E);
+    for (int64_t e = 0; e < E; ++e)
+        for (int j = 0; j < 8; ++j) coarse_elem_col(G + e * 48, j, Ae.data() + e * 64);
+    for (int v = 0; v < C.nvt; ++v) coarse_stencil_row(Ae.data(), C, v, sten, cdinv);
     return SEM_OK;
 }
 

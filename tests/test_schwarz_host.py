@@ -10,7 +10,7 @@ import pytest
 import scipy.linalg as sla
 
 from oracle import schwarz as sw
-from paper_2405_05640_gb300 import binding, build
+from paper_2405_05640_gb300 import binding, build, inputs
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,3 +68,80 @@ def test_line_tables_deal_every_line_once(N):
                 worst = max(worst, max(Counter((base % 32).tolist()).values()))
         if N in (3, 4, 6, 7):  # strides chosen so that no bank holds more than LPT line starts
             assert worst == 1, (N, ax, worst)
+
+
+COARSE_CASES = [
+    inputs.channel(3, 7),
+    inputs.deformed_cube(3, 5),
+    inputs.BoxCase("x1_periodic", 4, (1, 3, 2), (1, 0, 1), inputs.Y_FACES),
+    inputs.BoxCase("x2_periodic", 3, (2, 2, 3), (1, 1, 0), 0b110000, jitter=0.1, seed=3),
+]
+
+
+@pytest.mark.parametrize("case", COARSE_CASES, ids=[c.name for c in COARSE_CASES])
+def test_coarse_stencil_equals_oracle_trilinear_operator(case):
+    """The coarse level's assembled 27-point stencil (the set-up's own code,
+    run on the host) against the oracle's N = 1 operator on the same
+    vertices, assembled column by column: entries, Dirichlet rows/columns,
+    periodic aliases (one and two elements across a periodic direction) and
+    the inverse diagonal."""
+    import oracle
+    V = case.vertices()
+    mc = oracle.Mesh(1, case.nel, case.periodic, case.faces, V)
+    sten, cdinv = binding.schwarz_coarse_operator(case.nel, case.periodic, case.faces, mc.G)
+    nel, per = case.nel, case.periodic
+    nv = [n + (0 if p else 1) for n, p in zip(nel, per)]
+    nvt = nv[0] * nv[1] * nv[2]
+
+    def vid(vx, vy, vz):
+        if per[0] and vx == nel[0]:
+            vx = 0
+        if per[1] and vy == nel[1]:
+            vy = 0
+        if per[2] and vz == nel[2]:
+            vz = 0
+        return vx + nv[0] * (vy + nv[1] * vz)
+
+    # the library's vertex numbering against the oracle's global nodes
+    to_g = np.full(nvt, -1)
+    for e in range(mc.E):
+        ex, ey, ez = e % nel[0], (e // nel[0]) % nel[1], e // (nel[0] * nel[1])
+        for c in range(8):
+            v = vid(ex + (c & 1), ey + ((c >> 1) & 1), ez + (c >> 2))
+            g = mc.gid[e * 8 + c]
+            assert to_g[v] in (-1, g)
+            to_g[v] = g
+    assert (to_g >= 0).all() and len(set(to_g.tolist())) == nvt == mc.nglob
+    # dense library operator
+    A = np.zeros((nvt, nvt))
+    for v in range(nvt):
+        vx, vy, vz = v % nv[0], (v // nv[0]) % nv[1], v // (nv[0] * nv[1])
+        for o in range(27):
+            ox, oy, oz = o % 3 - 1, (o // 3) % 3 - 1, o // 9 - 1
+            c = []
+            for w, d, n, p in ((vx, ox, nv[0], per[0]), (vy, oy, nv[1], per[1]), (vz, oz, nv[2], per[2])):
+                w = w + d
+                if p:
+                    w %= n
+                c.append(w if 0 <= w < n else -1)
+            if min(c) < 0:
+                assert sten[o, v] == 0
+                continue
+            A[to_g[v], to_g[c[0] + nv[0] * (c[1] + nv[1] * c[2])]] += sten[o, v]
+    # dense oracle operator, Dirichlet rows and columns removed
+    first = np.zeros(mc.nglob, dtype=np.int64)
+    first[mc.gid[::-1]] = np.arange(mc.nloc)[::-1]
+    free = mc.apply_mask(np.ones(mc.nloc))[first] != 0
+    Ao = np.zeros((mc.nglob, mc.nglob))
+    for c in range(mc.nglob):
+        if not free[c]:
+            continue
+        eg = np.zeros(mc.nglob)
+        eg[c] = 1.0
+        Ao[:, c] = mc.apply(eg[mc.gid])[first]
+    Ao[~free, :] = 0.0
+    scale = np.abs(Ao).max()
+    assert np.abs(A - Ao).max() <= 2e-6 * scale
+    dg = np.diag(Ao)
+    ref = np.where(free, 1.0 / np.where(free, dg, 1.0), 0.0)
+    np.testing.assert_allclose(cdinv[np.argsort(to_g)], ref, rtol=2e-6, atol=0)
