@@ -1,5 +1,8 @@
 """The hybrid Schwarz preconditioner (sem_schwarz_apply, FP32) against the
-FP64 oracle (oracle/schwarz.py).
+FP64 oracle (oracle/schwarz.py), and the solves that use it: FP64 refinement
+around flexible FP32 CG preconditioned by it (solutions and true residuals
+against the oracle, fewer iterations than Jacobi, error paths, the 32^3
+channel), and the FP32-pair outer residual option of the mixed solver.
 
 Bar: FP32 data and arithmetic through six 1-D contractions, a division by the
 eigenvalue sums and the overlap sums: 1e-4 relative 2-norm (the local
