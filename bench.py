@@ -618,10 +618,15 @@ def run_op_schwarz(args, case):
     ext = ((case.N + 3) / (case.N + 1)) ** 3
     nbytes = int((4 + 8 * ext + 4) * case.nloc)
     peak = measured_peaks()["hbm_gbs"]
+    # the local solves' six 1-D contractions: (N+3)^4 multiply-adds each per element
+    flops = 2 * 6 * (case.N + 3) ** 4 * case.E
     print(json.dumps({"op": "schwarz", "nel": args.nel, "N": case.N, "coarse_iters": args.coarse_iters,
                       "subdomain_problems": sw.problems, "ms_per_launch": round(ms, 4),
                       "algorithmic_bytes": nbytes, "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
-                      "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}), flush=True)
+                      "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                      "contraction_flops": flops, "achieved_tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+                      "fp32_peak_tflops": 73.5, "peak_source": "measured FMA-chain probe on GB300 (FP32)",
+                      "fp32_frac": round(flops / (ms * 1e-3) / 1e12 / 73.5, 4)}), flush=True)
 
 
 def run_schwarz(args):
