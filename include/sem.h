@@ -493,7 +493,8 @@ int sem_schwarz_destroy(sem_schwarz *sw);
 /* Number of distinct 1-D eigenproblems solved at set-up. */
 int sem_schwarz_problems(const sem_schwarz *sw);
 /* The set-up's 1-D problem of one direction of an extended element (host
- * computation, no GPU): stiffness and mass of the left neighbour, the
+ * computation, no GPU; the fast-diagonalisation factors of the local solves
+ * of the section 3.1 preconditioner): stiffness and mass of the left neighbour, the
  * element and the right neighbour (lengths hL, h, hR > 0) on the N + 3
  * extended GLL points; flags bit 0: a left neighbour exists, bit 1: a right
  * one, bit 2: the element's low face is Dirichlet, bit 3: its high face (such
@@ -502,8 +503,9 @@ int sem_schwarz_problems(const sem_schwarz *sw);
  * unsorted).  SEM_ERR_UNSUPPORTED outside 2 <= N <= 9, SEM_ERR_INVALID_ARG
  * for NULL outputs, lengths <= 0 or unknown flags. */
 int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double *S, double *lambda);
-/* The coarse operator the set-up assembles, computed on the host by the
- * same code (no GPU): from the N = 1 geometric factors G[E][6][8] (FP64,
+/* The coarse operator the set-up assembles (the preconditioner's trilinear
+ * coarse level, section 3.1), computed on the host by the same code (no
+ * GPU): from the N = 1 geometric factors G[E][6][8] (FP64,
  * rr, ss, tt, rs, rt, st at the element vertices, quadrature weights
  * included; E = nel[0] nel[1] nel[2], elements x fastest), the 27-point
  * stencil sten[27][nv] (offset (ox, oy, oz) in {-1,0,1}^3 at index
@@ -514,7 +516,8 @@ int sem_schwarz_fdm_1d(int N, double h, double hL, double hR, int flags, double 
  * arrays owned by the caller.  SEM_ERR_INVALID_ARG for NULL or nel < 1. */
 int sem_schwarz_coarse_operator(const int *nel, const int *periodic, int faces, const double *G, float *sten,
                                 float *cdinv);
-/* The local-solve kernel's line tables for order N (host, no GPU): for each
+/* The local-solve kernel's line tables for order N (host, no GPU; a GB300
+ * scheduling detail, not from the paper): for each
  * of the three line directions (along I, J, K), *slots = 32 LPT entries (LPT
  * lines per lane) holding the line dealt to (group q = slot / 32, lane =
  * slot % 32), or -1; line id c1 + (N+3) c2 with (c1, c2) = (J, K), (I, K),
