@@ -16,6 +16,8 @@
 // over k, holding their u column and the t-direction results in registers.
 // Every mbarrier wait is bounded in time; on time-out the kernel records
 // kDevTimeoutTma in the mesh error word and all CTAs leave the loop.
+// This kernel serves the FP32 operator (plain, fused CG, affine and BF16-
+// factor forms); the FP64 operator has its own kernel (sem_ax64.cu).
 
 #include <cuda_bf16.h>
 
@@ -423,14 +425,6 @@ static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const void *G, doubl
     }
 }
 
-int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2, cudaStream_t st,
-                  const int *guard, int gval) {
-    const CgFuse<double> none{};
-    if (h2 != 0.0 || h1 != 1.0)
-        return dispatch_ax<double, true, false>(m, u, w, m->G, h1, h2, m->D, none, st, guard, gval);
-    return dispatch_ax<double, false, false>(m, u, w, m->G, 1.0, 0.0, m->D, none, st, guard, gval);
-}
-
 int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
     const CgFuse<float> none{};
@@ -439,12 +433,6 @@ int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) 
     if (m->G16)
         return dispatch_ax<float, false, false, DMatF, false, true>(m, u, w, m->G16, 1.0, 0.0, m->Df, none, st);
     return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st);
-}
-
-int ax_cg_launch_f64(const sem_mesh *m, const CgFuse<double> &cg, double *w, double h1, double h2,
-                     cudaStream_t st) {
-    if (h2 != 0.0 || h1 != 1.0) return dispatch_ax<double, true, true>(m, nullptr, w, m->G, h1, h2, m->D, cg, st);
-    return dispatch_ax<double, false, true>(m, nullptr, w, m->G, 1.0, 0.0, m->D, cg, st);
 }
 
 int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st) {
@@ -508,7 +496,9 @@ static int time_operator(const sem_mesh *m, const T *G, const DM &Dm, T *bufs, P
         if (sizeof(T) == 4)
             return CG ? ax_cg_launch_f32(m, reinterpret_cast<const CgFuse<float> &>(cg), reinterpret_cast<float *>(w), st)
                       : ax_launch_f32(m, reinterpret_cast<const float *>(u), reinterpret_cast<float *>(w), st);
-        return dispatch_ax<T, false, CG>(m, u, w, G, 1.0, 0.0, Dm, cg, st);
+        return CG ? ax_cg_launch_f64(m, reinterpret_cast<const CgFuse<double> &>(cg), reinterpret_cast<double *>(w),
+                                     1.0, 0.0, st)
+                  : ax_launch_f64(m, reinterpret_cast<const double *>(u), reinterpret_cast<double *>(w), 1.0, 0.0, st);
     };
     for (int q = 0; q < 2; ++q) {
         int s = once();
