@@ -186,9 +186,9 @@ int sem_glsc3(const sem_mesh *mesh, const double *a, const double *b, double *d_
  *  - Scratch: a file-scope device array of 8448 bytes (1024 block partials
  *    and a counter), held by every device that loads the library until the
  *    process exits.  The reduction always runs 1024 blocks, so any mesh the
- *    library accepts fits; the call still checks the need against the array
- *    and rejects it with SEM_ERR_WORKSPACE, and rejects nloc >= 2^31 with
- *    SEM_ERR_INVALID_ARG.
+ *    library accepts fits (the same meshes as sem_glsc3); the call still
+ *    checks the need against the array and rejects it with
+ *    SEM_ERR_WORKSPACE.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.

@@ -390,8 +390,6 @@ int sem_glsc3_noalloc(const sem_mesh *m, const double *a, const double *b, doubl
     if (need > kNoAllocScratchBytes)
         return fail(SEM_ERR_WORKSPACE, "sem_glsc3_noalloc: reduction needs " + std::to_string(need) +
                                            " bytes, static scratch holds " + std::to_string(kNoAllocScratchBytes));
-    if (m->nloc >= (int64_t(1) << 31))
-        return fail(SEM_ERR_INVALID_ARG, "sem_glsc3_noalloc: more than 2^31-1 points");
     void *scratch = nullptr;
     int s = noalloc_scratch_for_current_device(&scratch);
     if (s != SEM_OK) return s;
