@@ -430,14 +430,21 @@ int sem_guess_apply(const sem_mesh *mesh, const float *Y, int ldy, const double 
 /* ---- Batched solves ------------------------------------------------------
  * nsolve independent systems (meshes[i], b[i], x[i]; device FP64 E-layout;
  * meshes may differ in size and order) solved together by the mixed solver
- * (opts->precision must be SEM_PCG_MIXED, every mesh built with
- * SEM_GEOM_F32, x starts from 0).  All decisions of the solver run on the
- * device per solve; check_every FP32 iterations of every unfinished solve
- * plus one FP64 refinement stage form a round, captured once into a CUDA
- * graph (each solve a parallel branch) and replayed until every solve has
- * finished.  stats[i] (host) as for sem_pcg_solve, with wall_ms = the time
- * from the call until solve i was seen finished (round granularity).
- * Waits for `stream`.  Returns SEM_OK when all converged. */
+ * (opts->precision must be SEM_PCG_MIXED with the Jacobi inner solver, every
+ * mesh built with SEM_GEOM_F32, x starts from 0).  One CUDA graph, launched
+ * once: every solve is a parallel branch whose rounds (check_every FP32
+ * iterations plus one FP64 refinement stage) repeat in a device-side WHILE
+ * loop until the solve has converged, failed, spent its round budget
+ * (max_iter / check_every + 64) or met a device timeout; all decisions are
+ * taken on the device, so each solve advances at its own pace and the host
+ * waits once.  The branches carry scheduling priorities by estimated work
+ * (local points x elements along an axis x N; the smallest the greatest
+ * priority, spread over the device's priority levels): small solves are
+ * served first.  stats[i] (host) as for sem_pcg_solve, with wall_ms = device
+ * time from the start of the graph to the end of solve i's last round,
+ * ax_launches = the rounds it ran.  Waits for `stream`.  Returns SEM_OK when
+ * all converged; SEM_ERR_UNSUPPORTED for other precisions, a Schwarz
+ * preconditioner, outer_pair or an initial guess. */
 size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, const sem_pcg_opts *opts);
 int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b,
                           double *const *x, const sem_pcg_opts *opts, sem_pcg_stats *stats,

@@ -32,6 +32,7 @@ struct PcgScal {
     double prev_rr;     // batched solver: FP64 residual of the previous refinement
     int iter, done, status, max_iter;
     int phase;          // batched solver: kBt* state of this solve
+    int rounds;         // batched solver: rounds executed by this solve
     unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
 };
 

@@ -20,6 +20,7 @@
 // once.  Reductions are two-level (block partials, summed in block order by
 // the last block), so results are run-to-run deterministic.
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -903,8 +904,8 @@ static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const s
 
 // ---------------------------------------------------------------- batched solves
 //
-// Many independent mixed-precision solves advance together.  Every decision
-// of the solver runs on the device, per solve, as a phase:
+// Many independent mixed-precision solves run in ONE graph launch.  Every
+// decision of the solver runs on the device, per solve, as a phase:
 //   kBtIterate  FP32 CG iterations (the kernels return at once when the
 //               inner solve has paused: its residual fell by inner_tol);
 //   kBtRefine   x += ||r|| d (FP64), r = b - A x (FP64), convergence /
@@ -912,11 +913,15 @@ static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const s
 //   kBtReliable swap the FP64 residual into the FP32 iteration, rescale p,
 //               recompute beta, resume;
 //   kBtFinished nothing more to do.
-// One "round" = K iterations of every solve followed by one refinement
-// stage; a round is captured once into a CUDA graph (each solve a parallel
-// branch) and replayed; the host reads the per-solve phases after each
-// replay (for completion times) and re-captures when half of the captured
-// solves have finished.
+// Per solve the graph holds the start kernels and a WHILE conditional node
+// whose body is one round: K FP32 iterations, the guarded refinement stage,
+// and a kernel that counts the round and sets the node's condition -- loop
+// again unless the solve has finished, its round budget is spent or a
+// bounded wait of one of its kernels gave up (mesh error word).  The solves
+// are parallel branches of the graph, so each iterates at its own pace (a
+// small solve is done after its own rounds, not after the largest one's) and
+// the host waits once, for the whole batch.  The last kernel of each solve
+// records its completion time from the global timer.
 
 constexpr int kBtIterate = 0, kBtRefine = 1, kBtReliable = 2, kBtFinished = 3;
 
@@ -1008,27 +1013,42 @@ __global__ void __launch_bounds__(kPThreads)
     }
 }
 
-// after the start: a solve whose right-hand side is already converged (or
-// holds a NaN) is finished, the others iterate
-__global__ void bt_start_kernel(PcgScal *s) {
+// Start of the graph: the reference time of the completion times.
+__global__ void bt_clock_kernel(unsigned long long *t0) {
+    if (threadIdx.x == 0) *t0 = global_timer_ns();
+}
+
+// After the start: a solve whose right-hand side is already converged (or
+// holds a NaN) is finished, the others iterate; the loop condition follows.
+__global__ void bt_start_kernel(PcgScal *s, cudaGraphConditionalHandle h, unsigned long long *tdone) {
     if (threadIdx.x == 0) {
         s->prev_rr = s->rr;
+        s->rounds = 0;
         s->phase = s->done ? kBtFinished : kBtIterate;
+        if (s->phase == kBtFinished) *tdone = global_timer_ns();
+        cudaGraphSetConditional(h, s->phase == kBtFinished ? 0u : 1u);
     }
 }
 
-// phases of all solves -> host-visible array and the unfinished count
-__global__ void bt_collect_kernel(PcgScal *const *__restrict__ outs, int nsolve, int *__restrict__ phases,
-                                  int *__restrict__ unfinished) {
-    if (blockIdx.x != 0) return;
-    int cnt = 0;
-    for (int i = threadIdx.x; i < nsolve; i += blockDim.x) {
-        const int ph = outs[i]->phase;
-        phases[i] = ph;
-        cnt += ph != kBtFinished;
+// End of a round: count it; finish the solve when its round budget is spent
+// or a bounded wait of one of its kernels gave up; record the completion
+// time; loop again unless finished.
+__global__ void bt_round_end_kernel(PcgScal *s, const int *__restrict__ err, int max_rounds,
+                                    cudaGraphConditionalHandle h, unsigned long long *tdone) {
+    if (threadIdx.x != 0) return;
+    s->rounds += 1;
+    if (s->phase != kBtFinished) {
+        if (*err != 0) {
+            s->phase = kBtFinished;
+            s->status = SEM_ERR_TIMEOUT;
+        } else if (s->rounds >= max_rounds) {
+            s->phase = kBtFinished;
+            s->status = SEM_ERR_NOT_CONVERGED;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (threadIdx.x == 0) *unfinished = cnt;
+    const bool fin = s->phase == kBtFinished;
+    if (fin) *tdone = global_timer_ns();
+    cudaGraphSetConditional(h, fin ? 0u : 1u);
 }
 
 struct BtSolve {
@@ -1132,7 +1152,7 @@ int sem_pcg_solve_host(const sem_mesh *m, const double *hb, double *hx, const se
 
 size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, const sem_pcg_opts *o) {
     if (!meshes || nsolve <= 0) return 0;
-    size_t t = align_up(sizeof(PcgScal *) * nsolve) + align_up(sizeof(int) * (nsolve + 1));
+    size_t t = align_up(sizeof(unsigned long long) * (nsolve + 1));  // start time, completion times
     for (int i = 0; i < nsolve; ++i) {
         if (!meshes[i]) return 0;
         t += align_up(pcg_scratch_mixed(meshes[i]));
@@ -1140,6 +1160,88 @@ size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, 
     (void)o;
     return t;
 }
+
+}  // extern "C"
+
+namespace sem {
+
+// Streams, events and the graph of one batched call, released on every exit.
+struct BtGraph {
+    std::vector<cudaStream_t> ss, bss;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    ~BtGraph() {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        for (auto q : ss) cudaStreamDestroy(q);
+        for (auto q : bss) cudaStreamDestroy(q);
+        for (auto e : ev) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+        cudaGetLastError();  // errors of a failed capture are reported by the caller
+    }
+};
+
+// Capture solve S on stream q (already part of the capture): the start
+// kernels, then a WHILE node whose body is one round.
+static int bt_capture_solve(BtSolve &S, const sem_pcg_opts *o, int K, int max_rounds, cudaStream_t q,
+                            cudaStream_t bs, unsigned long long *tdone) {
+    const sem_mesh *m = S.m;
+    const int64_t n = m->nloc;
+    const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
+    SEM_CUDA_CHECK(cudaMemsetAsync(S.M.scal_out, 0, sizeof(PcgScal), q));
+    SEM_CUDA_CHECK(cudaMemsetAsync(S.M.in.scal, 0, sizeof(PcgScal), q));
+    SEM_CUDA_CHECK(cudaMemsetAsync(S.x, 0, sizeof(double) * n, q));
+    SEM_CUDA_CHECK(cudaMemsetAsync(S.M.d32, 0, sizeof(float) * n, q));
+    ir_residual_kernel<<<kPBlocks, kPThreads, 0, q>>>(S.b, nullptr, S.M.r64, m->minv, n, S.M.partial_out,
+                                                      S.M.scal_out, o->tol, o->tol_is_relative);
+    pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, q>>>(S.M.r64, nullptr, m->dinv32, m->minv32, n, S.M.in,
+                                                                  S.M.scal_out, itol, 1, o->max_iter);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    SEM_CUDA_CHECK(cudaStreamGetCaptureInfo(q, &cst, nullptr, &g));
+    cudaGraphConditionalHandle h;
+    SEM_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    bt_start_kernel<<<1, 32, 0, q>>>(S.M.scal_out, h, tdone);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    SEM_CUDA_CHECK(cudaStreamGetCaptureInfo(q, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    SEM_CUDA_CHECK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+    SEM_CUDA_CHECK(cudaStreamUpdateCaptureDependencies(q, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // the loop body: one round of this solve
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    SEM_CUDA_CHECK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int s = bt_round(S, o, K, bs);
+    if (s == SEM_OK) {
+        bt_round_end_kernel<<<1, 32, 0, bs>>>(S.M.scal_out, m->d_err, max_rounds, h, tdone);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(e, "bt_round_end_kernel");
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(bs, &out);
+    if (s != SEM_OK) return s;
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (round body)");
+    return SEM_OK;
+}
+
+}  // namespace sem
+
+extern "C" {
 
 int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b, double *const *x,
                           const sem_pcg_opts *o, sem_pcg_stats *stats, void *scratch, size_t scratch_bytes,
@@ -1149,6 +1251,7 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");
     if (o->precision != SEM_PCG_MIXED) return fail(SEM_ERR_UNSUPPORTED, "batched solves use SEM_PCG_MIXED");
     if (o->use_initial_guess) return fail(SEM_ERR_UNSUPPORTED, "batched solves start from x = 0");
+    if (o->schwarz || o->outer_pair) return fail(SEM_ERR_UNSUPPORTED, "batched solves use the Jacobi inner solver");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     for (int i = 0; i < nsolve; ++i) {
         if (!meshes[i] || !b[i] || !x[i]) return fail(SEM_ERR_INVALID_ARG, "NULL mesh, b or x");
@@ -1160,137 +1263,83 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_batched_scratch_bytes or misaligned");
     cudaStream_t st = as_stream(stream);
     char *p = static_cast<char *>(scratch);
-    PcgScal **d_outs = reinterpret_cast<PcgScal **>(p);
-    p += align_up(sizeof(PcgScal *) * nsolve);
-    int *d_phases = reinterpret_cast<int *>(p);  // [nsolve] + unfinished count
-    p += align_up(sizeof(int) * (nsolve + 1));
+    unsigned long long *d_t = reinterpret_cast<unsigned long long *>(p);  // [0]: start, [1 + i]: solve i done
+    p += align_up(sizeof(unsigned long long) * (nsolve + 1));
     std::vector<BtSolve> S(nsolve);
-    std::vector<PcgScal *> outs(nsolve);
     for (int i = 0; i < nsolve; ++i) {
         S[i].m = meshes[i];
         S[i].b = b[i];
         S[i].x = x[i];
         S[i].M = carve_mixed(meshes[i], p);
         p += align_up(pcg_scratch_mixed(meshes[i]));
-        outs[i] = S[i].M.scal_out;
     }
-    SEM_CUDA_CHECK(cudaMemcpyAsync(d_outs, outs.data(), sizeof(PcgScal *) * nsolve, cudaMemcpyHostToDevice, st));
-    // start every solve: x = 0, r = b, inner FP32 start from r / ||r||
-    const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
-    for (int i = 0; i < nsolve; ++i) {
-        const sem_mesh *m = S[i].m;
-        const int64_t n = m->nloc;
-        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.scal_out, 0, sizeof(PcgScal), st));
-        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.in.scal, 0, sizeof(PcgScal), st));
-        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].x, 0, sizeof(double) * n, st));
-        SEM_CUDA_CHECK(cudaMemsetAsync(S[i].M.d32, 0, sizeof(float) * n, st));
-        ir_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(S[i].b, nullptr, S[i].M.r64, m->minv, n,
-                                                           S[i].M.partial_out, S[i].M.scal_out, o->tol,
-                                                           o->tol_is_relative);
-        pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(S[i].M.r64, nullptr, m->dinv32, m->minv32, n,
-                                                                       S[i].M.in, S[i].M.scal_out, itol, 1,
-                                                                       o->max_iter);
-        SEM_CUDA_CHECK(cudaGetLastError());
-    }
-    // solves already converged at the start (b = 0) are finished; the rest iterate
-    for (int i = 0; i < nsolve; ++i) {
-        bt_start_kernel<<<1, 32, 0, st>>>(S[i].M.scal_out);
-    }
-    SEM_CUDA_CHECK(cudaGetLastError());
-
     const int K = o->check_every > 0 ? o->check_every : 16;
-    const int nstreams = nsolve < 16 ? nsolve : 16;
-    // capture happens on a stream of our own (the caller's may be the legacy
-    // default stream, which cannot be captured); the graph runs on `st`
-    std::vector<cudaStream_t> ss(nstreams + 1);
-    std::vector<cudaEvent_t> ev(nstreams + 1);
-    for (auto &q : ss) SEM_CUDA_CHECK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-    for (auto &e : ev) SEM_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaStream_t cs = ss[nstreams];
-    auto cleanup = [&]() {
-        for (auto &q : ss) cudaStreamDestroy(q);
-        for (auto &e : ev) cudaEventDestroy(e);
-    };
-    std::vector<int> active(nsolve), hph(nsolve + 1, kBtIterate);
-    for (int i = 0; i < nsolve; ++i) active[i] = i;
-    std::vector<double> done_ms(nsolve, -1.0);
-    cudaGraphExec_t exec = nullptr;
-    int captured = 0, rounds = 0, status = SEM_OK;
     const int max_rounds = o->max_iter / K + 64;
-    while (true) {
-        if (!exec) {
-            // capture one round of the active solves as parallel branches
-            cudaGraph_t g = nullptr;
-            cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-            if (ce != cudaSuccess) {
-                cleanup();
-                return cuda_fail(ce, "cudaStreamBeginCapture");
-            }
-            cudaEventRecord(ev[nstreams], cs);
-            int s = SEM_OK;
-            for (int q = 0; q < nstreams && s == SEM_OK; ++q) {
-                cudaStreamWaitEvent(ss[q], ev[nstreams], 0);
-                for (size_t a = q; a < active.size() && s == SEM_OK; a += nstreams)
-                    s = bt_round(S[active[a]], o, K, ss[q]);
-                cudaEventRecord(ev[q], ss[q]);
-                cudaStreamWaitEvent(cs, ev[q], 0);
-            }
-            bt_collect_kernel<<<1, 32, 0, cs>>>(d_outs, nsolve, d_phases, d_phases + nsolve);
-            ce = cudaStreamEndCapture(cs, &g);
-            if (s != SEM_OK || ce != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                cleanup();
-                return s != SEM_OK ? s : cuda_fail(ce, "cudaStreamEndCapture");
-            }
-            ce = cudaGraphInstantiate(&exec, g, 0);
-            cudaGraphDestroy(g);
-            if (ce != cudaSuccess) {
-                cleanup();
-                return cuda_fail(ce, "cudaGraphInstantiate");
-            }
-            captured = (int)active.size();
-        }
-        cudaError_t ce = cudaGraphLaunch(exec, st);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hph.data(), d_phases, sizeof(int) * (nsolve + 1),
-                                                    cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            cleanup();
-            return cuda_fail(ce, "batched round");
-        }
-        ++rounds;
-        const double now = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        std::vector<int> still;
-        for (int i : active) {
-            if (hph[i] == kBtFinished) {
-                if (done_ms[i] < 0) done_ms[i] = now;
-            } else {
-                still.push_back(i);
-            }
-        }
-        active.swap(still);
-        if (active.empty()) break;
-        if (rounds >= max_rounds) {
-            status = SEM_ERR_NOT_CONVERGED;
-            break;
-        }
-        if ((int)active.size() * 2 <= captured) {  // re-capture the smaller active set
-            cudaGraphExecDestroy(exec);
-            exec = nullptr;
-        }
+
+    // Shortest job first: every solve's kernels carry a scheduling priority
+    // from the rank of its estimated work, local points x elements along an
+    // axis x N (CG iterations grow like 1/h ~ nel N), the smallest work the
+    // greatest priority, spread evenly over the device's priority levels.
+    // The block scheduler then serves the small solves first: their latency
+    // drops while the batch's total work and end time stay the same.
+    int prio_least = 0, prio_greatest = 0;
+    SEM_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    const int levels = prio_least - prio_greatest + 1;
+    std::vector<int> order(nsolve), prio(nsolve);
+    std::vector<double> work(nsolve);
+    for (int i = 0; i < nsolve; ++i) {
+        const sem_mesh *m = meshes[i];
+        const int nmax = std::max(m->nel[0], std::max(m->nel[1], m->nel[2]));
+        work[i] = (double)m->nloc * nmax * m->N;
+        order[i] = i;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    cleanup();
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] < work[c]; });
+    for (int r = 0; r < nsolve; ++r) prio[order[r]] = prio_greatest + (int)((int64_t)r * levels / nsolve);
+
+    // Build the graph by capture on streams of our own (the caller's may be
+    // the legacy default stream, which cannot be captured): a clock kernel,
+    // then one branch per solve (captured on a stream of the solve's
+    // priority, the loop body too), joined at the end.
+    BtGraph G;
+    G.ss.resize(nsolve);
+    G.bss.resize(levels);
+    G.ev.resize(nsolve + 1);
+    for (int i = 0; i < nsolve; ++i)
+        SEM_CUDA_CHECK(cudaStreamCreateWithPriority(&G.ss[i], cudaStreamNonBlocking, prio[i]));
+    for (int l = 0; l < levels; ++l)
+        SEM_CUDA_CHECK(cudaStreamCreateWithPriority(&G.bss[l], cudaStreamNonBlocking, prio_greatest + l));
+    for (auto &e : G.ev) SEM_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    SEM_CUDA_CHECK(cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking));
+    SEM_CUDA_CHECK(cudaStreamBeginCapture(G.cs, cudaStreamCaptureModeRelaxed));
+    G.capturing = true;
+    bt_clock_kernel<<<1, 32, 0, G.cs>>>(d_t);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    SEM_CUDA_CHECK(cudaEventRecord(G.ev[nsolve], G.cs));
+    for (int i = 0; i < nsolve; ++i) {
+        SEM_CUDA_CHECK(cudaStreamWaitEvent(G.ss[i], G.ev[nsolve], 0));
+        int s = bt_capture_solve(S[i], o, K, max_rounds, G.ss[i], G.bss[prio[i] - prio_greatest], d_t + 1 + i);
+        if (s != SEM_OK) return s;
+        SEM_CUDA_CHECK(cudaEventRecord(G.ev[i], G.ss[i]));
+        SEM_CUDA_CHECK(cudaStreamWaitEvent(G.cs, G.ev[i], 0));
+    }
+    G.capturing = false;
+    SEM_CUDA_CHECK(cudaStreamEndCapture(G.cs, &G.g));
+    SEM_CUDA_CHECK(cudaGraphInstantiate(&G.exec, G.g, cudaGraphInstantiateFlagUseNodePriority));
+    // the one launch of the batch, and the one wait
+    SEM_CUDA_CHECK(cudaGraphLaunch(G.exec, st));
+    SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+
     // per-solve statistics
-    int derr = 0;
+    std::vector<unsigned long long> ht(nsolve + 1, 0ull);
+    SEM_CUDA_CHECK(cudaMemcpy(ht.data(), d_t, sizeof(unsigned long long) * (nsolve + 1), cudaMemcpyDeviceToHost));
+    const int per_round = 3 * K + 7;  // kernels of one round body
+    int status = SEM_OK, derr = 0;
     for (int i = 0; i < nsolve; ++i) {
         PcgScal ho{}, hi{};
-        SEM_CUDA_CHECK(cudaMemcpyAsync(&ho, S[i].M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
-        SEM_CUDA_CHECK(cudaMemcpyAsync(&hi, S[i].M.in.scal, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+        SEM_CUDA_CHECK(cudaMemcpy(&ho, S[i].M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost));
+        SEM_CUDA_CHECK(cudaMemcpy(&hi, S[i].M.in.scal, sizeof(PcgScal), cudaMemcpyDeviceToHost));
         int e = 0;
-        SEM_CUDA_CHECK(cudaMemcpyAsync(&e, meshes[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SEM_CUDA_CHECK(cudaStreamSynchronize(st));
+        SEM_CUDA_CHECK(cudaMemcpy(&e, meshes[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         derr |= e;
         sem_pcg_stats &t = stats[i];
         t = sem_pcg_stats{};
@@ -1302,12 +1351,15 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         t.init_rel_res = 1.0;
         t.status = ho.phase == kBtFinished ? ho.status : SEM_ERR_NOT_CONVERGED;
         if (e) t.status = SEM_ERR_TIMEOUT;
-        t.wall_ms = done_ms[i];
-        t.kernel_launches = rounds;
+        // device time from the start of the batch's graph to this solve's last round
+        t.wall_ms = ht[1 + i] >= ht[0] ? (double)(ht[1 + i] - ht[0]) * 1e-6 : -1.0;
+        t.kernel_launches = 6 + ho.rounds * per_round;
+        t.ax_launches = ho.rounds;  // rounds of the device-side loop
         if (t.status != SEM_OK && status == SEM_OK) status = t.status;
     }
     if (derr) status = SEM_ERR_TIMEOUT;
     if (status != SEM_OK) set_error(sem_status_string(status));
+    (void)t0;
     return status;
 }
 

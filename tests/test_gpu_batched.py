@@ -1,5 +1,6 @@
-"""Batched mixed-precision solves (one CUDA graph per round, device-side
-solver decisions) against the FP64 oracle, solve by solve."""
+"""Batched mixed-precision solves (one CUDA graph launch per batch: a
+device-side WHILE loop of rounds per solve) against the FP64 oracle, solve by
+solve."""
 import numpy as np
 import pytest
 
@@ -41,6 +42,14 @@ def test_batched_solves_match_oracle_and_single_solves():
                               check_every=8)
         assert abs(s1["iters"] - st["iters"]) <= 2, (i, s1["iters"], st["iters"])
         assert st["wall_ms"] > 0
+        # the rounds of each solve ran in the device-side loop of the one
+        # graph launch (8 FP32 iterations per round)
+        assert st["ax_launches"] >= st["iters"] / 8, st
+    # the solves finish at their own pace: the one with the fewest rounds
+    # before the one with the most
+    few = min(range(len(cases)), key=lambda i: stats[i]["ax_launches"])
+    many = max(range(len(cases)), key=lambda i: stats[i]["ax_launches"])
+    assert stats[few]["wall_ms"] <= stats[many]["wall_ms"]
 
 
 def test_batched_reports_non_convergence_per_solve():
