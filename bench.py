@@ -54,7 +54,8 @@ AX_BYTES_PER_POINT = {"f64": 64}
 # DRAM traffic per launch of the operator kernels from one ncu capture
 # (bytes), keyed by the SHA-256 of the kernel source it was taken on; the
 # bench reports null once the source changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"ax64_cg": {"bytes_per_launch": 1408.6e6, "src_sha": "21f1d46784359222",
+                           "from": "profiles/ax64_cg_n7_nel20_ncu_full.md (20^3 case scaled x4.096)"}}
 
 
 def _src_sha(path):
