@@ -800,19 +800,31 @@ def run_schwarz(args):
 def run_tgv_learned(args):
     """The learned-initial-guess workload: TGV Re=1600, 32^3, N=7, dt=1e-3,
     network trained on steps 1-100, pressure solves of steps 101-200 timed
-    per method (plain FP64 from p^{n-1}; FP64 refinement around FP32 PCG from
-    p^{n-1}, from the cubic extrapolation, from the learned guess)."""
+    per method: plain FP64 from p^{n-1}; FP64 refinement around FP32
+    Jacobi-PCG and around flexible FP32 CG with the hybrid Schwarz
+    preconditioner, each from p^{n-1}, from the cubic extrapolation and from
+    the learned guess.  value = speedup of the fastest method over plain
+    FP64; the learned guess's gain is reported over each solver's own
+    extrapolation start."""
     from paper_2405_05640_gb300 import build as _build
     from paper_2405_05640_gb300 import tgv_learned
     _build.build()
     out = tgv_learned.run(nel=args.nel, N=args.order, train_steps=args.train_steps, eval_steps=args.eval_steps,
                           epochs=args.epochs, variant=args.variant)
     m = out["methods"]
-    rec = {"metric": "pressure-solve wall time to 1e-8 over the evaluated TGV steps, learned guess + mixed "
-                     "precision vs plain FP64 (x0 = previous pressure)",
-           "value": m["chosen_learned"]["speedup_vs_plain_f64_prev"], "unit": "x (speedup)",
+    best = max((k for k in m if k != "plain_f64_prev"), key=lambda k: m[k]["speedup_vs_plain_f64_prev"])
+    gain = {}
+    for solver in ("chosen", "schwarz"):
+        a, b = m.get(f"{solver}_learned"), m.get(f"{solver}_extrap")
+        if a and b:
+            gain[solver] = {"iters_learned": a["iters_mean"], "iters_extrap": b["iters_mean"],
+                            "iter_gain": round(1.0 - a["iters_mean"] / b["iters_mean"], 4),
+                            "time_gain": round(1.0 - a["pressure_ms_total"] / b["pressure_ms_total"], 4)}
+    rec = {"metric": "pressure-solve wall time to 1e-8 over the evaluated TGV steps, fastest method vs plain "
+                     "FP64 (x0 = previous pressure)",
+           "value": m[best]["speedup_vs_plain_f64_prev"], "unit": "x (speedup)", "best_method": best,
            "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 network / f32 inner / f64 refinement",
-           "data": "synthetic", "config": {"workload": out["workload"]}, **out}
+           "data": "synthetic", "config": {"workload": out["workload"]}, "learned_gain": gain, **out}
     print(json.dumps(rec), flush=True)
 
 
@@ -872,40 +884,58 @@ def run_batched(args):
 def run_deformed(args):
     """Mixed precision on the deformed cube (64^3 elements, N = 7, vertices
     moved by 0.05 h, Dirichlet walls, random right-hand side): time to 1e-8
-    of plain FP64 PCG and of the chosen solver, and the chosen solution's
-    error against the FP64 solution, both converged to 1e-11."""
+    of plain FP64 PCG, of FP64 refinement around FP32 Jacobi-PCG and around
+    flexible FP32 CG with the hybrid Schwarz preconditioner (its local solves
+    use the elements' mean edge lengths, approximate on deformed elements),
+    and each mixed solution's error against the FP64 solution, all converged
+    to 1e-11."""
     import torch
 
     from paper_2405_05640_gb300 import binding, inputs
     from paper_2405_05640_gb300 import build as _build
     _build.build()
     case = inputs.deformed_cube(args.nel, args.order)
-    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True, geom_bf16=args.bf16)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True, geom_bf16=args.bf16)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    sw = binding.Schwarz(gm, gc)
     b = gm.scatter(torch.from_numpy(case.rhs_global()).cuda())
-    scratch = gm.pcg_scratch(gm.pcg_opts(precision=binding.SEM_PCG_MIXED))
+    solvers = {"plain_fp64": dict(precision=binding.SEM_PCG_F64),
+               "jacobi_mixed": dict(precision=binding.SEM_PCG_MIXED, inner_tol=1e-2),
+               "schwarz_mixed": dict(precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, schwarz=sw, coarse_iters=3,
+                                     coarse_tol=1e-2)}
+    scratch = gm.pcg_scratch(gm.pcg_opts(precision=binding.SEM_PCG_MIXED, schwarz=sw))
     out = {}
-    for name, prec in (("plain_fp64", binding.SEM_PCG_F64), ("chosen", binding.SEM_PCG_MIXED)):
-        kw = dict(tol=TOL, max_iter=100000, precision=prec, inner_tol=1e-2, check_every=32)
+    for name, kw in solvers.items():
+        kw = dict(kw, tol=TOL, max_iter=100000, check_every=8 if "schwarz" in kw else 32)
         gm.pcg(b, scratch=scratch, **kw)  # warm-up
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, st = gm.pcg(b, scratch=scratch, **kw)
-        torch.cuda.synchronize()
-        out[name] = {"time_to_1e-8_ms": round((time.perf_counter() - t0) * 1e3, 1), "iters": st["iters"],
-                     "outer": st["outer_iters"], "rel_res": st["rel_res"]}
+        times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            t0 = time.perf_counter()
+            x, st = gm.pcg(b, scratch=scratch, **kw)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0) * 1e3)
+        out[name] = {"time_to_1e-8_ms": round(statistics.median(times), 1), "iters": st["iters"],
+                     "outer": st["outer_iters"], "rel_res": st["rel_res"], "status": st["status"]}
     xs = {}
-    for name, prec in (("plain_fp64", binding.SEM_PCG_F64), ("chosen", binding.SEM_PCG_MIXED)):
-        xs[name], _ = gm.pcg(b, scratch=scratch, tol=1e-11, max_iter=100000, precision=prec, inner_tol=1e-2,
-                             check_every=32)
-    d = xs["chosen"] - xs["plain_fp64"]
-    err = (gm.glsc3(d, d) / gm.glsc3(xs["plain_fp64"], xs["plain_fp64"])) ** 0.5
-    rec = {"metric": "PCG time-to-1e-8, plain FP64 vs chosen (FP64 refinement around FP32 PCG)",
-           "value": round(out["plain_fp64"]["time_to_1e-8_ms"] / out["chosen"]["time_to_1e-8_ms"], 3),
+    for name, kw in solvers.items():
+        kw = dict(kw, tol=1e-11, max_iter=100000, check_every=8 if "schwarz" in kw else 32)
+        xs[name], _ = gm.pcg(b, scratch=scratch, **kw)
+    ref = xs["plain_fp64"]
+    for name in ("jacobi_mixed", "schwarz_mixed"):
+        d = xs[name] - ref
+        out[name]["rel_err_vs_fp64_at_1e-11"] = (gm.glsc3(d, d) / gm.glsc3(ref, ref)) ** 0.5
+        out[name]["speedup_vs_plain_fp64"] = round(out["plain_fp64"]["time_to_1e-8_ms"] /
+                                                   out[name]["time_to_1e-8_ms"], 3)
+    best = max(("jacobi_mixed", "schwarz_mixed"), key=lambda k: out[k]["speedup_vs_plain_fp64"])
+    rec = {"metric": "PCG time-to-1e-8, plain FP64 vs the fastest mixed solver",
+           "value": out[best]["speedup_vs_plain_fp64"], "best": best,
            "unit": "x (speedup)", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
            "dtype": "f32 inner / f64 refinement",
            "config": {"workload": f"deformed cube {args.nel}^3 elements, N={case.N}, amplitude 0.05 h, seed 0",
-                      "nloc": case.nloc, "n_paper": case.n_paper},
-           "solves": out, "chosen_vs_fp64_solution_rel_err_at_1e-11": err}
+                      "nloc": case.nloc, "n_paper": case.n_paper, "schwarz_subdomain_problems": sw.problems},
+           "solves": out}
     print(json.dumps(rec), flush=True)
 
 

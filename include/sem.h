@@ -557,8 +557,32 @@ int sem_perf_model(int ndev, const double *P_opt, const double *C_max, double C,
                    double *C_split);
 
 /* Read and clear the mesh's device error word after waiting for `stream`:
- * *code = 0 if no kernel on this mesh reported a bounded-wait timeout. */
+ * *code = 0 if no kernel on this mesh reported a bounded-wait timeout, 1 if
+ * a bulk-copy (mbarrier) wait gave up, 2 if a grid-barrier wait gave up.
+ * Every device wait of the library is bounded (1 s of global time); a
+ * kernel that gives up records its code here (first writer wins), leaves
+ * its loop and drains its own copies, so the context stays usable.  The
+ * solvers (sem_pcg_solve*, sem_pcg_solve_batched, the sem_ns_* steps) clear
+ * the word at entry and report a give-up of their own kernels as
+ * SEM_ERR_TIMEOUT; other calls (sem_ax, sem_schwarz_apply, ...) leave it set
+ * until it is read here.  While it is set, the grid barriers of the coarse
+ * Schwarz level leave at once (sem_schwarz_apply then skips the coarse
+ * correction). */
 int sem_mesh_check_device_error(const sem_mesh *mesh, int *code, void *stream);
+
+/* Self-test of the failure detection (not from the paper): launches a kernel
+ * that waits, bounded by limit_s (0 < limit_s <= 10 s), on something nothing
+ * will complete -- kind 0: an mbarrier whose transaction bytes no copy will
+ * bring (the wait of every bulk-copy pipeline of the library); kind 1: two
+ * CTAs on a grid barrier whose target exceeds the grid (the wait of the
+ * cooperative coarse solve).  The wait gives up, writes its code (1 or 2)
+ * into the mesh's error word and the kernel returns; no fault, no trap.
+ * d_scratch: 16 bytes of 16-byte aligned device memory (kind 1; may be NULL
+ * for kind 0).  Stream-ordered; read the result with
+ * sem_mesh_check_device_error.  SEM_ERR_INVALID_ARG for an unknown kind or a
+ * limit outside the range, SEM_ERR_WORKSPACE for missing scratch. */
+int sem_wait_selftest(const sem_mesh *mesh, int kind, double limit_s, void *d_scratch, size_t bytes,
+                      void *stream);
 
 #ifdef __cplusplus
 }

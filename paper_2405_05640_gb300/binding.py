@@ -98,6 +98,7 @@ _SIGS = {
     "sem_pcg_solve_host": ([_VP, _VP, _VP, ctypes.POINTER(PcgOpts), ctypes.POINTER(PcgStats), _VP,
                             ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
+    "sem_wait_selftest": ([_VP, ctypes.c_int, ctypes.c_double, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_gemm_bf16": ([_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                        ctypes.c_int, _VP, _VP], ctypes.c_int),
     "sem_mlp_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
@@ -400,6 +401,16 @@ class Mesh:
         c = ctypes.c_int()
         check(lib().sem_mesh_check_device_error(self.handle, ctypes.byref(c), _stream()), "check_device_error")
         return c.value
+
+    def wait_selftest(self, kind: int, limit_s: float):
+        """sem_wait_selftest: a bounded wait on something nothing completes
+        (kind 0 mbarrier, 1 grid barrier); its code lands in the error word."""
+        import torch
+        scr = torch.empty(16 + 256, dtype=torch.uint8, device="cuda")
+        base = (scr.data_ptr() + 255) // 256 * 256
+        check(lib().sem_wait_selftest(self.handle, int(kind), float(limit_s), _VP(base), 16, _stream()),
+              "sem_wait_selftest")
+        return scr
 
 
 class NSState:

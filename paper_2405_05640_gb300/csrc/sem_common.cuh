@@ -171,6 +171,45 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// Grid-wide barrier of a kernel whose CTAs are all resident (cooperative
+// launch): each CTA adds one arrival to *bar and thread 0 waits until it
+// reaches `target`, giving up after `limit_ns` of global time or at once when
+// another CTA has given up (*err != 0); a give-up writes kDevTimeoutFlag into
+// *err (first writer wins).  Returns false (on every thread of the CTA) when
+// the wait gave up.
+__device__ __forceinline__ bool grid_barrier_bounded(unsigned *bar, unsigned target, int *err,
+                                                     uint64_t limit_ns = 1000000000ull) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        uint64_t t0 = 0;
+        while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (*reinterpret_cast<volatile int *>(err) != 0) {
+                good = 0;
+                break;
+            }
+            const uint64_t t = global_timer_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > limit_ns) {
+                atomicCAS(err, 0, (int)kDevTimeoutFlag);
+                good = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // ---------------------------------------------------------------- host helpers
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
                   cudaStream_t st, const int *guard = nullptr, int gval = 0);

@@ -432,6 +432,28 @@ static int grid_for(int64_t n, int block = 256) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Self-test of the bounded waits: kind 0, one CTA waits on an mbarrier
+// whose 16 transaction bytes no copy will bring (the wait of every bulk-copy
+// pipeline of the library); kind 1, two CTAs wait on a grid barrier whose
+// target exceeds the grid (the wait of the cooperative coarse solve).  Both
+// give up after limit_ns, record their code in the error word and return;
+// nothing is in flight when they exit.
+__global__ void wait_selftest_kernel(int kind, uint64_t limit_ns, unsigned *ctr, int *err) {
+    if (kind == 0) {
+        __shared__ __align__(8) uint64_t bar;
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);
+        __syncthreads();
+        mbar_wait_bounded(&bar, 0, err, kDevTimeoutTma, limit_ns);
+    } else {
+        grid_barrier_bounded(ctr, gridDim.x + 1, err, limit_ns);
+    }
+}
+
 }  // namespace sem
 
 using namespace sem;
@@ -671,6 +693,20 @@ int sem_mesh_field(const sem_mesh *m, int which, double *dst, void *stream) {
             return fail(SEM_ERR_INVALID_ARG, "unknown field");
     }
     SEM_CUDA_CHECK(cudaMemcpyAsync(dst, src, sizeof(double) * m->nloc, cudaMemcpyDeviceToDevice, s));
+    return SEM_OK;
+}
+
+int sem_wait_selftest(const sem_mesh *m, int kind, double limit_s, void *d_scratch, size_t bytes, void *stream) {
+    if (!m) return fail(SEM_ERR_INVALID_ARG, "NULL mesh");
+    if (kind != 0 && kind != 1) return fail(SEM_ERR_INVALID_ARG, "kind must be 0 (mbarrier) or 1 (grid barrier)");
+    if (!(limit_s > 0.0) || limit_s > 10.0) return fail(SEM_ERR_INVALID_ARG, "limit_s must be in (0, 10]");
+    if (kind == 1 && (!d_scratch || bytes < 16 || reinterpret_cast<uintptr_t>(d_scratch) % 16))
+        return fail(SEM_ERR_WORKSPACE, "the grid-barrier self-test needs 16 bytes of aligned device scratch");
+    cudaStream_t st = as_stream(stream);
+    unsigned *ctr = static_cast<unsigned *>(d_scratch);
+    if (kind == 1) SEM_CUDA_CHECK(cudaMemsetAsync(ctr, 0, sizeof(unsigned), st));
+    wait_selftest_kernel<<<kind == 0 ? 1 : 2, 32, 0, st>>>(kind, (uint64_t)(limit_s * 1e9), ctr, m->d_err);
+    SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
 

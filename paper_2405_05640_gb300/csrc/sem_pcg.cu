@@ -898,6 +898,10 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
 
 static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o,
                           sem_pcg_stats *stats, void *scratch, cudaStream_t st) {
+    // every solve reports the timeouts of its own kernels: an earlier call's
+    // give-up (already reported by that call, or read with
+    // sem_mesh_check_device_error) is cleared here
+    SEM_CUDA_CHECK(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
     if (o->precision == SEM_PCG_MIXED) return pcg_mixed(m, b, x, o, stats, scratch, st);
     return pcg_f64(m, b, x, o, stats, scratch, st);
 }
@@ -1262,6 +1266,7 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         reinterpret_cast<uintptr_t>(scratch) % kAlign)
         return fail(SEM_ERR_WORKSPACE, "scratch smaller than sem_pcg_batched_scratch_bytes or misaligned");
     cudaStream_t st = as_stream(stream);
+    for (int i = 0; i < nsolve; ++i) SEM_CUDA_CHECK(cudaMemsetAsync(meshes[i]->d_err, 0, sizeof(int), st));
     char *p = static_cast<char *>(scratch);
     unsigned long long *d_t = reinterpret_cast<unsigned long long *>(p);  // [0]: start, [1 + i]: solve i done
     p += align_up(sizeof(unsigned long long) * (nsolve + 1));

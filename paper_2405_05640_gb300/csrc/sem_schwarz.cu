@@ -869,41 +869,6 @@ struct CoarseArgs {
     double tol2;
 };
 
-// Grid barrier of the cooperative coarse kernel: arrival counter, bounded
-// wait (1 s of global time; another CTA's give-up ends it at once).  Returns
-// false when the wait gave up (error word set).
-__device__ __forceinline__ bool cg_grid_sync(unsigned *bar, unsigned target, int *err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int good = 1;
-        uint64_t t0 = 0;
-        while (true) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-            if (v >= target) break;
-            if (*reinterpret_cast<volatile int *>(err) != 0) {
-                good = 0;
-                break;
-            }
-            const uint64_t t = global_timer_ns();
-            if (t0 == 0) {
-                t0 = t;
-            } else if (t - t0 > 1000000000ull) {
-                atomicCAS(err, 0, kDevTimeoutFlag);
-                good = 0;
-                break;
-            }
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // Block sum of v into partial[blockIdx.x]; after the barrier every CTA sums
 // the partials in the same fixed order (identical totals everywhere).
 __device__ __forceinline__ void cg_block_partial(double v, double *partial) {
@@ -967,7 +932,7 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
         part += (double)b * (double)(di * b);
     }
     cg_block_partial(part, P.partial);
-    if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+    if (!grid_barrier_bounded(P.bar, ++nbar * gridDim.x, P.err)) return;
     double rz = cg_total(P.partial);
     const double rz0 = rz;
     float beta = 0.f;
@@ -999,7 +964,7 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
             part += (double)pv * (double)w;
         }
         cg_block_partial(part, P.partial);
-        if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+        if (!grid_barrier_bounded(P.bar, ++nbar * gridDim.x, P.err)) return;
         const double pw = cg_total(P.partial);
         const float alpha = pw != 0.0 ? (float)(rz / pw) : 0.f;
         part = 0.0;
@@ -1011,7 +976,7 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
             part += (double)rv * (double)(__ldg(P.cdinv + v) * rv);
         }
         cg_block_partial(part, P.partial + kCgMaxGrid);
-        if (!cg_grid_sync(P.bar, ++nbar * gridDim.x, P.err)) return;
+        if (!grid_barrier_bounded(P.bar, ++nbar * gridDim.x, P.err)) return;
         const double rzn = cg_total(P.partial + kCgMaxGrid);
         beta = rz != 0.0 ? (float)(rzn / rz) : 0.f;
         rz = rzn;

@@ -18,9 +18,13 @@ only sequences calls and keeps device buffers):
      samples (tcgen05 GEMMs forward and backward).
   3. From the checkpoint at step train_steps, eval_steps more steps are run
      once per method: plain FP64 PCG from x0 = p^{n-1} (the stronger plain
-     baseline), the chosen solver from p^{n-1}, from p_ext, and from the
-     learned guess p_ext + se * MLP(features).  Pressure-solve wall time
-     includes building the guess.
+     baseline); FP64 refinement around FP32 Jacobi-PCG ("chosen_*") and
+     around flexible FP32 CG with the hybrid Schwarz preconditioner (the
+     paper's pressure preconditioner, "schwarz_*"), each from p^{n-1}, from
+     p_ext and from the learned guess p_ext + se * MLP(features).
+     Pressure-solve wall time includes building the guess.
+  Phase 1 solves with the Schwarz solver when it is among the methods (the
+  pressures, hence the samples, are the same to the tolerance).
 """
 from __future__ import annotations
 
@@ -50,6 +54,7 @@ class GuessNet:
         self.net.set_params(inputs.mlp_init(self.I, self.H, self.O, seed))
         self.X = torch.zeros((self.R, self.I), dtype=torch.bfloat16, device="cuda")
         self.Y = torch.zeros((self.R, self.O), dtype=torch.float32, device="cuda")
+        self.Y0 = torch.zeros((self.R, self.O), dtype=torch.float32, device="cuda")  # no correction
         self.r = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
         self.pext = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
         self.guess = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
@@ -61,6 +66,12 @@ class GuessNet:
 
     def residual(self, b, p1, p2, p3):
         binding.guess_residual(self.gm, b, p1, p2, p3, self.r, self.pext)
+
+    def extrap(self, p1, p2, p3):
+        """The cubic extrapolation alone (no residual: only the network's
+        features need it): Q Q^T p_ext / mult with a zero correction."""
+        binding.guess_apply(self.gm, self.Y0, p1, p2, p3, 0.0, self.guess)
+        return self.guess
 
     def set_scales(self, p1, p2, p3, p4):
         """Feature scales of this sample (after residual()); variant "d3"
@@ -91,9 +102,12 @@ class GuessNet:
         return self.guess
 
 
+METHODS = ("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned", "schwarz_prev", "schwarz_extrap",
+           "schwarz_learned")
+
+
 def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs=8, lr=1e-3, hidden=256,
-        tol=1e-8, seed=0, skip=10, variant="p1",
-        methods=("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned"), log=None):
+        tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, log=None):
     import torch
     log = log or (lambda *a: None)
     t_all = time.perf_counter()
@@ -108,6 +122,14 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     plain = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_F64, use_initial_guess=True,
                         check_every=32)
     vopts = gm.pcg_opts(tol=tol, max_iter=50000, check_every=8)
+    sw = None
+    use_sw = any(m.startswith("schwarz") for m in methods)
+    if use_sw:
+        gc = binding.Mesh(1, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+        sw = binding.Schwarz(gm, gc)
+        schwarz = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
+                              use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2)
+    phase1_opts = schwarz if use_sw else chosen
     g = GuessNet(gm, hidden, seed, variant)
 
     # ---- phase 1: simulate and collect samples
@@ -124,7 +146,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
             if take:
                 g.set_scales(p1, p2, p3, p4)
                 g.features(p1, p2, p3, p4)
-        ps, vs = ns.step_finish(chosen, vopts)
+        ps, vs = ns.step_finish(phase1_opts, vopts)
         phase1.append((ps["iters"], ps["wall_ms"]))
         if have:
             p_new = ns.get(3)
@@ -175,20 +197,22 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
             torch.cuda.synchronize()
             tg = time.perf_counter()
             guess = None
-            if meth in ("chosen_extrap", "chosen_learned"):
+            if meth.endswith("_extrap"):
+                guess = g.extrap(p1, p2, p3)
+                torch.cuda.synchronize()
+            elif meth.endswith("_learned"):
                 g.residual(b, p1, p2, p3)
-                guess = g.pext
-                if meth == "chosen_learned":
-                    g.set_scales(p1, p2, p3, p4)
-                    g.features(p1, p2, p3, p4)
-                    guess = g.predict(p1, p2, p3)
+                g.set_scales(p1, p2, p3, p4)
+                g.features(p1, p2, p3, p4)
+                guess = g.predict(p1, p2, p3)
                 torch.cuda.synchronize()
             guess_ms = (time.perf_counter() - tg) * 1e3
             x0 = guess if guess is not None else p1
             x0c = x0.clone()
-            ps, vs = ns.step_finish(plain if meth.startswith("plain") else chosen, vopts, p_guess=guess)
+            popts = plain if meth.startswith("plain") else schwarz if meth.startswith("schwarz") else chosen
+            ps, vs = ns.step_finish(popts, vopts, p_guess=guess)
             p_new = ns.get(3)
-            if meth == "chosen_learned" and variant == "d3":
+            if meth.endswith("_learned") and variant == "d3":
                 g.update_rho(p_new)
             err = math.sqrt(gm.glsc3(x0c - p_new, x0c - p_new) / max(gm.glsc3(p_new, p_new), 1e-300))
             iters.append(ps["iters"])
@@ -211,6 +235,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
                      "network": f"{g.I}-{g.H}-{g.H}-{g.O} BF16 (tcgen05), {g.net.P} parameters",
                      "variant": variant},
            "phase1_iters_mean": float(np.mean([a for a, _ in phase1])),
+           "phase1_solver": "schwarz" if use_sw else "chosen",
            "methods": results, "wall_s": round(time.perf_counter() - t_all, 1)}
     base = results.get("plain_f64_prev")
     if base:

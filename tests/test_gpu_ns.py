@@ -100,3 +100,51 @@ def test_ns_mixed_pressure_and_guess():
         assert _rel(_host(st.get(3)), on.p) <= 1e-8
         for c in range(3):
             assert _rel(_host(st.get(c)), on.u[c]) <= 1e-9
+
+
+def test_ns_stop_at_k_and_resume_is_bitwise():
+    """Checkpoint / resume: stop after step k, keep every state field on the
+    host (as a checkpoint file would), restore it into a new stepper on the
+    same mesh and step on; the result equals the uninterrupted run bit for
+    bit (BDF3 / EXT3 with dealiased advection, so the whole history is in
+    the state)."""
+    on, gm, st = _tgv_pair(3, 5, 400.0)
+    st.set_scheme(3, dealias=True)
+    po = gm.pcg_opts(tol=1e-12, max_iter=20000, use_initial_guess=True)
+    vo = gm.pcg_opts(tol=1e-12, max_iter=20000)
+    for _ in range(3):
+        st.step(2e-3, po, vo)
+    fields, steps = st.checkpoint()
+    saved = [_host(f).copy() for f in fields]
+    for _ in range(3):
+        st.step(2e-3, po, vo)
+    ref = [_host(f).copy() for f in st.checkpoint()[0]]
+    st2 = binding.NSState(gm, 400.0)
+    st2.set_scheme(3, dealias=True)
+    st2.restore(([_dev(a) for a in saved], steps))
+    for _ in range(3):
+        st2.step(2e-3, po, vo)
+    got = [_host(f) for f in st2.checkpoint()[0]]
+    assert len(got) == len(ref)
+    for w, (a, b) in enumerate(zip(got, ref)):
+        np.testing.assert_array_equal(a, b, err_msg=f"slot {w}")
+
+
+def test_ns_schwarz_pressure_matches_oracle():
+    """The pressure solved by the mixed solver with the hybrid Schwarz
+    preconditioner on the fully periodic TGV box (singular pressure system,
+    coarse level on the periodic vertex grid)."""
+    on, gm, st = _tgv_pair(3, 5, 400.0, geom_f32=True)
+    case = inputs.tgv_box(3, 5)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+    S = binding.Schwarz(gm, gc)
+    po = gm.pcg_opts(tol=1e-11, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-3, schwarz=S,
+                     use_initial_guess=True)
+    vo = gm.pcg_opts(tol=1e-12, max_iter=20000)
+    for n in range(3):
+        on.step(2e-3, p_tol=1e-12, v_tol=1e-12)
+        ps, vs = st.step(2e-3, po, vo)
+        assert ps["status"] == 0 and ps["outer_iters"] >= 1
+        assert _rel(_host(st.get(3)), on.p) <= 1e-8
+        for c in range(3):
+            assert _rel(_host(st.get(c)), on.u[c]) <= 1e-9
