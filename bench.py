@@ -75,14 +75,19 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations in the CPU sample")
     p.add_argument("--plain-steps", type=int, default=2, help="plain FP64 solves timed for comparison")
-    p.add_argument("--op", choices=["ax-f64", "ax-f32", "ax-f64pair", "dssum-f64", "dssum-f32", "schwarz", "pcg-f64"],
+    p.add_argument("--op", choices=["ax-f64", "ax-f32", "ax-f64pair", "dssum-f64", "dssum-f32", "schwarz", "pcg-f64",
+                                    "gemm"],
                    default=None, help="time one entry point alone instead of the solve")
-    p.add_argument("--workload", choices=["channel", "tgv-learned", "batched", "deformed", "tgv-steps", "schwarz"],
+    p.add_argument("--workload", choices=["channel", "tgv-learned", "batched", "deformed", "tgv-steps", "schwarz",
+                                          "tgv-long"],
                    default="channel")
     p.add_argument("--coarse-iters", type=int, default=3, help="Schwarz: coarse-level CG iterations per application")
     p.add_argument("--outer-pair", action="store_true",
-                   help="Schwarz workload: FP64 outer residual with the FP32-pair operator")
+                   help="Schwarz workload: outer residual with the double-float (FP32-pair) operator")
     p.add_argument("--nsolve", type=int, default=64)
+    p.add_argument("--t-end", type=float, default=10.0, help="tgv-long: final time")
+    p.add_argument("--dt", type=float, default=2e-3, help="tgv-long: time step")
+    p.add_argument("--sample-every", type=int, default=25, help="tgv-long: steps between energy samples")
     p.add_argument("--round-iters", type=int, default=16)
     p.add_argument("--train-steps", type=int, default=100)
     p.add_argument("--eval-steps", type=int, default=100)
@@ -515,7 +520,7 @@ def run_ours(args):
                 "hbm_frac": round(f64_bytes / (f64_ms * 1e-3) / 1e9 / hbm, 4),
                 "attainable": "min(HBM, FP64 pipe): FP64 pipe (the HBM bound would allow "
                               f"{round(f64_bytes / (hbm * 1e9) * 1e3, 4)} ms)"}
-    # ---- secondary kernels: the plain FP64 operator, the FP32-pair operator,
+    # ---- secondary kernels: the plain FP64 operator, the double-float operator,
     # the fused FP32 operator of the mixed solvers
     u = torch.randn(case.nloc, dtype=torch.float64, device="cuda")
     w = torch.empty_like(u)
@@ -662,6 +667,8 @@ def run_op(args):
     from paper_2405_05640_gb300 import binding, inputs
     from paper_2405_05640_gb300 import build as _build
     _build.build()
+    if args.op == "gemm":
+        return run_op_gemm(args)
     case = inputs.channel(args.nel, args.order)
     if args.op == "schwarz":
         return run_op_schwarz(args, case)
@@ -696,6 +703,64 @@ def run_op(args):
                       "gdofs": round(case.n_paper / (ms * 1e-3) / 1e9, 3), "algorithmic_bytes": nbytes,
                       "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                       "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}), flush=True)
+
+
+def run_op_gemm(args):
+    """The tcgen05 BF16 GEMM (sem_gemm_bf16: C = act(A B^T + bias), FP32
+    accumulation in TMEM) on the guess network's shapes at the 32^3 TGV mesh
+    (32768 element rows; 2048-256-256-512 layers): the three forward layers
+    and the five backward products, plus one 8192^3 product for the peak;
+    TFLOP/s = 2 M N K / mean launch time (CUDA events, `steps` launches after
+    `warmup`), against the measured cuBLAS BF16 burst peak."""
+    import torch
+
+    from paper_2405_05640_gb300 import binding
+    from paper_2405_05640_gb300 import build as _build
+    _build.build()
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    src = "measured bf16_tflops (burst)" if peak else "fallback"
+    peak = peak or 1900.0
+    R, I, H, O = 32768, 2048, 256, 512
+    shapes = [("fwd W1", R, H, I, 1), ("fwd W2", R, H, H, 1), ("fwd W3", R, O, H, 0),
+              ("bwd dW3", O, H, R, 0), ("bwd dH2", R, H, O, 0), ("bwd dW2", H, H, R, 0),
+              ("bwd dH1", R, H, H, 0), ("bwd dW1", H, I, R, 0), ("square 8192", 8192, 8192, 8192, 0)]
+    s = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rows = []
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for name, M, N, K, act in shapes:
+        A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16)
+        B = torch.randn((N, K), generator=g, device="cuda").to(torch.bfloat16)
+        bias = torch.zeros(N, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            binding.gemm_bf16(A, B, bias, act, err=err)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            binding.gemm_bf16(A, B, bias, act, err=err)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        rows.append({"gemm": name, "M": M, "N": N, "K": K, "ms": round(ms, 4), "tflops": round(tf, 1),
+                     "frac": round(tf / peak, 4)})
+    assert int(err.item()) == 0, "a bounded wait of the GEMM gave up"
+    fwd = [r for r in rows if r["gemm"].startswith("fwd")]
+    bwd = [r for r in rows if r["gemm"].startswith("bwd")]
+    f_fl = sum(2.0 * r["M"] * r["N"] * r["K"] for r in fwd)
+    b_fl = sum(2.0 * r["M"] * r["N"] * r["K"] for r in bwd)
+    print(json.dumps({"op": "gemm", "kernel": "gemm_tn_bf16_kernel (tcgen05.mma kind::f16, TMA, TMEM accumulator)",
+                      "peak_tflops": peak, "peak_source": src, "shapes": rows,
+                      "forward_pass": {"ms": round(sum(r["ms"] for r in fwd), 4),
+                                       "tflops": round(f_fl / (sum(r["ms"] for r in fwd) * 1e-3) / 1e12, 1)},
+                      "backward_pass": {"ms": round(sum(r["ms"] for r in bwd), 4),
+                                        "tflops": round(b_fl / (sum(r["ms"] for r in bwd) * 1e-3) / 1e12, 1)}}),
+          flush=True)
 
 
 def run_op_pcg_f64(args, case):
@@ -791,7 +856,7 @@ def run_schwarz(args):
                       "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
                       "dtype": "f32 inner / f64 refinement",
                       "config": {"workload": WORKLOAD, "coarse_iters": args.coarse_iters,
-                                 "outer_residual": "FP32-pair operator" if args.outer_pair else "FP64 operator"},
+                                 "outer_residual": "double-float operator" if args.outer_pair else "FP64 operator"},
                       "inner_iters": ser["iters"] / args.steps, "outer_iters": st["outer_iters"],
                       "rel_res_fp64": st["rel_res"], "status": st["status"], "gpu_launches": ser["launches"],
                       "subdomain_problems": sw.problems, "clocks": clk.summary()}), flush=True)
@@ -1006,6 +1071,100 @@ def run_tgv_steps(args):
     print(json.dumps(rec), flush=True)
 
 
+def run_tgv_long(args):
+    """A long Taylor-Green vortex run: Re = 1600, [0, 2 pi]^3, nel^3
+    elements, N = 7, BDF3 / EXT3 with dealiased (3/2-rule) advection, the
+    pressure solved by FP64 refinement around flexible FP32 CG with the
+    hybrid Schwarz preconditioner from the cubic extrapolation, the velocity
+    by FP64 Jacobi-CG, to t_end.  Every `sample_every` steps: the kinetic
+    energy E_k = <|u|^2> / 2 and the enstrophy Omega = <|w|^2> / 2 (w = curl u
+    from the library's collocation gradient, integrated element by element
+    with the GLL mass).  Self-consistency of the run: E_k must decrease, and
+    the dissipation -dE_k/dt (central differences of the samples) must match
+    2 nu Omega; both series are reported.  The reference data of the
+    benchmark case are not available here."""
+    import numpy as np
+    import torch
+
+    from paper_2405_05640_gb300 import binding, inputs
+    from paper_2405_05640_gb300 import build as _build
+    _build.build()
+    Re, dt, nu = 1600.0, args.dt, 1.0 / 1600.0
+    case = inputs.tgv_box(args.nel, args.order)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_rx=True, geom_f32=True)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    sw = binding.Schwarz(gm, gc)
+    xyz = gm.coords().cpu().numpy()
+    u0 = torch.from_numpy(np.stack([c.reshape(-1) for c in inputs.tgv_velocity(*xyz)])).cuda()
+    ns = binding.NSState(gm, Re)
+    ns.set_scheme(3, dealias=True)
+    ns.set_velocity(u0)
+    po = gm.pcg_opts(tol=1e-8, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, check_every=8,
+                     schwarz=sw, coarse_iters=3, coarse_tol=1e-2, use_initial_guess=True)
+    vo = gm.pcg_opts(tol=1e-8, max_iter=50000, check_every=8)
+    Bm = gm.field(0)
+    vol = float(Bm.sum())
+    zero = torch.zeros((gm.E, gm.npt), dtype=torch.float32, device="cuda")
+    guess = torch.empty(gm.nloc, dtype=torch.float64, device="cuda")
+
+    def enstrophy():
+        g = [gm.gradient(ns.get(c)) for c in range(3)]  # g[c][m] = d u_c / d x_m
+        wx, wy, wz = g[2][1] - g[1][2], g[0][2] - g[2][0], g[1][0] - g[0][1]
+        return 0.5 * float((Bm * (wx * wx + wy * wy + wz * wz)).sum()) / vol
+
+    nsteps = int(round(args.t_end / dt))
+    t, E, Om, piters, viters = [0.0], [ns.kinetic_energy()], [enstrophy()], [], []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t_wall = time.perf_counter()
+    for n in range(1, nsteps + 1):
+        ns.step_begin(dt)
+        pg = None
+        if n > 3:  # cubic extrapolation of the last three pressures, no correction
+            binding.guess_apply(gm, zero, ns.get(3), ns.get(4), ns.get(5), 0.0, guess)
+            pg = guess
+        ps, vs = ns.step_finish(po, vo, p_guess=pg)
+        piters.append(ps["iters"])
+        viters.append(sum(v["iters"] for v in vs))
+        if ps["status"] != 0 or any(v["status"] != 0 for v in vs):
+            raise RuntimeError(f"step {n}: solver status {ps['status']} / {[v['status'] for v in vs]}")
+        if n % args.sample_every == 0 or n == nsteps:
+            t.append(n * dt)
+            E.append(ns.kinetic_energy())
+            Om.append(enstrophy())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    wall = time.perf_counter() - t_wall
+    t, E, Om = np.array(t), np.array(E), np.array(Om)
+    eps_num = -np.gradient(E, t)      # -dE_k/dt from the samples
+    eps_ens = 2.0 * nu * Om           # 2 nu Omega
+    inner = slice(1, len(t) - 1)
+    mism = np.abs(eps_num[inner] - eps_ens[inner]) / np.maximum(eps_ens[inner], 1e-30)
+    k_peak = int(np.argmax(eps_ens))
+    rec = {"metric": "long TGV run: dissipation self-consistency (-dE_k/dt vs 2 nu Omega) and time per step",
+           "value": round(ms / nsteps, 3), "unit": "ms/step", "higher_is_better": False, "n_gpus": 1,
+           "data": "synthetic", "dtype": "f64 (pressure: f32 inner / f64 refinement)",
+           "config": {"workload": f"TGV Re=1600, {args.nel}^3 elements, N={case.N}, dt={dt:g}, t_end={args.t_end:g}, "
+                                  "BDF3/EXT3, 3/2-rule dealiasing, Schwarz pressure from the cubic extrapolation",
+                      "steps": nsteps, "sample_every": args.sample_every},
+           "wall_s": round(wall, 1),
+           "pressure_iters_mean": round(float(np.mean(piters)), 2),
+           "velocity_iters_mean": round(float(np.mean(viters)) / 3, 2),
+           "energy_monotone": bool(np.all(np.diff(E) < 0)),
+           "E_k0": E[0], "E_k_end": E[-1],
+           "dissipation_peak": {"t": float(t[k_peak]), "2nu_Omega": float(eps_ens[k_peak]),
+                                "minus_dEdt": float(eps_num[k_peak])},
+           "identity_rel_mismatch": {"median": float(np.median(mism)), "max": float(np.max(mism)),
+                                     "at_peak": float(abs(eps_num[k_peak] - eps_ens[k_peak]) / eps_ens[k_peak])},
+           "series": {"t": [round(float(x), 4) for x in t], "E_k": [float(x) for x in E],
+                      "2nu_Omega": [float(x) for x in eps_ens], "minus_dEdt": [float(x) for x in eps_num]}}
+    print(json.dumps(rec), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.workload == "deformed":
@@ -1018,6 +1177,8 @@ def main(argv=None):
         run_tgv_steps(args)
     elif args.workload == "schwarz":
         run_schwarz(args)
+    elif args.workload == "tgv-long":
+        run_tgv_long(args)
     elif args.op:
         run_op(args)
     elif args.impl == "reference":

@@ -53,8 +53,10 @@ extern "C" {
 /* Data types of field arguments. */
 #define SEM_F64 0
 #define SEM_F32 1
-#define SEM_F64_PAIR 2             /* FP64 fields; sem_ax evaluates the operator in
-                                      FP32-pair arithmetic (see sem_ax) */
+#define SEM_F64_PAIR 2             /* FP64 fields, operator evaluated in double-float
+                                      (FP32-pair, ~48-bit) arithmetic: an
+                                      approximation of the FP64 operator, not
+                                      FP64 arithmetic (see sem_ax) */
 
 /* Extra precision copies of the geometric factors that sem_mesh_create
  * builds (bitmask; FP64 factors are always built). */
@@ -144,12 +146,16 @@ int sem_mesh_field(const sem_mesh *mesh, int which, double *dst, void *stream);
  * u, w: device, nloc values of `dtype`:
  *  - SEM_F64: FP64 fields, FP64 arithmetic;
  *  - SEM_F32: FP32 fields, FP32 arithmetic (mesh built with SEM_GEOM_F32);
- *  - SEM_F64_PAIR: FP64 fields (double in, double out); every value is
- *    carried as an unevaluated sum of two floats (48 significant bits) and
- *    the contractions run on the FP32 pipes with exact product and sum error
+ *  - SEM_F64_PAIR: FP64 fields (double in, double out) but NOT FP64
+ *    arithmetic: every value is carried as an unevaluated sum of two floats
+ *    (double-float, 48 significant bits against FP64's 53) and the
+ *    contractions run on the FP32 pipes with exact product and sum error
  *    terms (mesh built with SEM_GEOM_PAIR).  Error about 2^-42 of the
- *    line-wise magnitudes |D^T||G||D||u| (1e-12 in the relative 2-norm on
- *    fields without strong cancellation).  Each element is scaled by a power of two
+ *    line-wise magnitudes |D^T||G||D||u| (FP64: ~2^-50): within 1e-12 of
+ *    the FP64 result in the relative 2-norm on fields without strong
+ *    cancellation, up to ~1e-11 on smooth fields where A u cancels.  For
+ *    residuals of iterative refinement, whose error only has to stay far
+ *    below the solver tolerance.  Each element is scaled by a power of two
  *    (exact) before the split, so any magnitude is handled; values below
  *    2^-74 of the element's largest keep 24 bits, below 2^-126 of it they
  *    count as zero; FP64 denormals count as zero; an Inf or NaN in an
@@ -210,9 +216,12 @@ int sem_glsc3_noalloc(const sem_mesh *mesh, const double *a, const double *b, do
  *   residual has fallen by inner_tol, the FP32 increment is added to the FP64
  *   solution and the FP64 residual b - A x is recomputed; the outer dot
  *   products and the solution are FP64.  Requires SEM_GEOM_F32 in the mesh.
- * precision = SEM_PCG_F64_PAIR: the FP64 solver (FP64 vectors, dot products
- *   and updates) with the operator evaluated in FP32-pair arithmetic (as
- *   sem_ax SEM_F64_PAIR; error ~2^-42 of the line-wise magnitudes).  Poisson
+ * precision = SEM_PCG_F64_PAIR: FP64 vectors, dot products and updates
+ *   with the operator evaluated in double-float arithmetic (as sem_ax
+ *   SEM_F64_PAIR; error ~2^-42 of the line-wise magnitudes): not an FP64
+ *   solve -- it converges in the FP64 solver's iterations and its solution
+ *   meets the tolerance in the FP64 true residual, but differs from the FP64
+ *   solution by the operator's error times the condition number.  Poisson
  *   only (h1 = 1, h2 = 0); requires SEM_GEOM_PAIR in the mesh. */
 #define SEM_PCG_F64 0
 #define SEM_PCG_MIXED 1
@@ -451,22 +460,33 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
                           void *d_scratch, size_t scratch_bytes, void *stream);
 
 /* ---- Autotuner of the operator launch shape -------------------------------
- * Times the operator of `mesh` (precision dtype, plain or fused CG form)
- * over pipeline depths {1, 2, 3} x resident-CTAs-per-SM caps {none, 1, 2, 4}
- * and keeps the fastest for the mesh's order N in the library's launch table
- * (process-wide, all meshes of that order use it).  Scratch: device,
- * sem_autotune_scratch_bytes.  Waits for `stream`.  Not from the paper. */
+ * Times the operator of `mesh` (precision dtype, plain or fused CG form) and
+ * keeps the fastest launch shape for the mesh's order N in the library's
+ * launch table (process-wide, all meshes of that order use it).  FP32:
+ * pipeline depths {1, 2, 3} x resident-CTAs-per-SM caps {none, 1, 2, 4} x
+ * elements per CTA {1, 2, 4} (the block shape; groups of elements where
+ * (N+1)^2 threads leave warps partly empty: 2 <= N <= 9, (N+1)^2 not a
+ * multiple of 32, general or BF16 factors); FP64: the CTA cap only.
+ * Scratch: device, sem_autotune_scratch_bytes.  Waits for `stream`.  Not
+ * from the paper. */
+#define SEM_TUNE_MAX_CONFIGS 48
 typedef struct {
-    int best_stages, best_cap;
+    int best_stages, best_cap, best_epc;
     float best_ms;
     int configs;
-    int stages[16], caps[16];
-    float ms[16];
+    int stages[SEM_TUNE_MAX_CONFIGS], caps[SEM_TUNE_MAX_CONFIGS], epcs[SEM_TUNE_MAX_CONFIGS];
+    float ms[SEM_TUNE_MAX_CONFIGS];
 } sem_tune_result;
 size_t sem_autotune_scratch_bytes(const sem_mesh *mesh);
 int sem_autotune_operator(const sem_mesh *mesh, int dtype, int fused_cg, void *d_scratch, size_t bytes,
                           void *stream, sem_tune_result *out);
-/* Back to the default launch shapes (2 stages, occupancy-limited). */
+/* Set the launch shape of `mesh`'s order for dtype / fused_cg (as the
+ * autotuner would, without timing): stages 1..3, per_sm_cap >= 0 (0 = the
+ * occupancy limit), epc 1, 2 or 4 (elements per CTA; used by the FP32
+ * operator where it builds groups, else 1).  SEM_ERR_INVALID_ARG outside. */
+int sem_autotune_set(const sem_mesh *mesh, int dtype, int fused_cg, int stages, int per_sm_cap, int epc);
+/* Back to the default launch shapes (2 stages, occupancy-limited, 1 element
+ * per CTA). */
 int sem_autotune_reset(void);
 
 /* ---- Hybrid Schwarz preconditioner of the pressure solve ------------------

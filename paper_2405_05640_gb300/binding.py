@@ -68,10 +68,14 @@ class PcgStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+SEM_TUNE_MAX_CONFIGS = 48
+
+
 class TuneResult(ctypes.Structure):
-    _fields_ = [("best_stages", ctypes.c_int), ("best_cap", ctypes.c_int), ("best_ms", ctypes.c_float),
-                ("configs", ctypes.c_int), ("stages", ctypes.c_int * 16), ("caps", ctypes.c_int * 16),
-                ("ms", ctypes.c_float * 16)]
+    _fields_ = [("best_stages", ctypes.c_int), ("best_cap", ctypes.c_int), ("best_epc", ctypes.c_int),
+                ("best_ms", ctypes.c_float), ("configs", ctypes.c_int),
+                ("stages", ctypes.c_int * SEM_TUNE_MAX_CONFIGS), ("caps", ctypes.c_int * SEM_TUNE_MAX_CONFIGS),
+                ("epcs", ctypes.c_int * SEM_TUNE_MAX_CONFIGS), ("ms", ctypes.c_float * SEM_TUNE_MAX_CONFIGS)]
 
 
 _VP = ctypes.c_void_p
@@ -130,6 +134,7 @@ _SIGS = {
     "sem_autotune_scratch_bytes": ([_VP], ctypes.c_size_t),
     "sem_autotune_operator": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(TuneResult)],
                               ctypes.c_int),
+    "sem_autotune_set": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sem_autotune_reset": ([], ctypes.c_int),
     "sem_gradient": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_advect": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -365,6 +370,11 @@ class Mesh:
             raise SemError(status, "sem_pcg_solve_host")
         return x_host, st.as_dict()
 
+    def autotune_set(self, dtype=SEM_F32, fused_cg=True, stages=2, cap=0, epc=1):
+        """sem_autotune_set: this order's launch shape, without timing."""
+        check(lib().sem_autotune_set(self.handle, int(dtype), int(bool(fused_cg)), int(stages), int(cap), int(epc)),
+              "sem_autotune_set")
+
     def autotune(self, dtype=SEM_F32, fused_cg=True):
         """sem_autotune_operator for this mesh's order; returns the result dict."""
         import torch
@@ -374,9 +384,9 @@ class Mesh:
         r = TuneResult()
         check(lib().sem_autotune_operator(self.handle, int(dtype), int(bool(fused_cg)), _VP(base), n, _stream(),
                                           ctypes.byref(r)), "sem_autotune_operator")
-        k = min(r.configs, 16)
-        return {"best_stages": r.best_stages, "best_cap": r.best_cap, "best_ms": r.best_ms,
-                "table": [(r.stages[i], r.caps[i], r.ms[i]) for i in range(k)]}
+        k = min(r.configs, SEM_TUNE_MAX_CONFIGS)
+        return {"best_stages": r.best_stages, "best_cap": r.best_cap, "best_epc": r.best_epc, "best_ms": r.best_ms,
+                "table": [(r.stages[i], r.caps[i], r.epcs[i], r.ms[i]) for i in range(k)]}
 
     # ---- Navier-Stokes building blocks
     def gradient(self, f):

@@ -30,23 +30,27 @@ namespace sem {
 // Slabs per stage: the input field (u; or r, dinv, p in the fused CG mode),
 // the six geometric factors (AFF: the element's 4 affine scalars instead),
 // and B (Helmholtz, FP64).
-template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false>
+// A CTA works on EPC consecutive elements at a time (the "block shape"; 1
+// by default, 2 or 4 where (N+1)^2 threads leave a warp half empty, chosen by
+// the autotuner).  Their slabs are contiguous in every array, so each bulk
+// copy simply covers EPC elements.
+template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false, int EPC = 1>
 __host__ __device__ constexpr int ax_stage_bytes() {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
     constexpr int gsize = AFF ? 16 : 6 * NPT * (G16 ? 2 : (int)sizeof(T));
-    return ((NPT * (CG ? 3 : 1) * (int)sizeof(T) + gsize + (HELM ? NPT * 8 : 0)) + 15) / 16 * 16;
+    return (EPC * (NPT * (CG ? 3 : 1) * (int)sizeof(T) + gsize + (HELM ? NPT * 8 : 0)) + 15) / 16 * 16;
 }
 
-template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false>
+template <int N, typename T, bool HELM, bool CG, bool AFF, bool G16 = false, int EPC = 1>
 __host__ __device__ constexpr int ax_smem_bytes(int nst) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    return nst * ax_stage_bytes<N, T, HELM, CG, AFF, G16>() + 2 * NPT * (int)sizeof(T) +
-           ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 16 * 4 + 64;
+    return nst * ax_stage_bytes<N, T, HELM, CG, AFF, G16, EPC>() + 2 * EPC * NPT * (int)sizeof(T) +
+           ((N1 * N1 * (int)sizeof(T) + 15) / 16 * 16) + 4 * 8 + 32 * 8;
 }
 
-template <int N>
+template <int N, int EPC = 1>
 __host__ __device__ constexpr int ax_threads() {
-    return ((N + 1) * (N + 1) + 31) / 32 * 32;
+    return (EPC * (N + 1) * (N + 1) + 31) / 32 * 32;
 }
 
 // N1 consecutive shared-memory values into registers: 16-byte vector loads
@@ -87,13 +91,15 @@ struct AxArgs {
 };
 
 // Launch shape of the operator per (precision, Helmholtz, fused CG, N):
-// pipeline stages and a cap on resident CTAs per SM (0 = occupancy limit).
-// Defaults: 2 stages, no cap; sem_autotune_operator measures and sets them.
+// pipeline stages, a cap on resident CTAs per SM (0 = occupancy limit) and
+// the elements per CTA (FP32).  Defaults: 2 stages, no cap, 1 element;
+// sem_autotune_operator measures and sets them.
 AxTune g_ax_tune[2][2][2][2][kMaxN1] = {};
 
 static AxTune tune_for(int dt, bool helm, bool cg, bool aff, int N) {
     AxTune t = g_ax_tune[dt][helm][cg][aff][N];
     if (t.nst <= 0) t.nst = 2;
+    if (t.epc <= 0) t.epc = 1;
     return t;
 }
 
@@ -105,13 +111,13 @@ static AxTune tune_for(int dt, bool helm, bool cg, bool aff, int N) {
 //       rho_i rho_j rho_k a_e etc.; G points at the [E][4] scalars (a, b, c, 0);
 //   G16 (FP32 operator): the six factors are stored in BF16 ([E][6][npt],
 //       12 bytes per point) and widened to FP32 in shared memory reads.
-template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16 = false>
-__global__ void __launch_bounds__(ax_threads<N>())
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16 = false, int EPC = 1>
+__global__ void __launch_bounds__(ax_threads<N, EPC>())
     ax_kernel(const T *__restrict__ u, T *__restrict__ w, const void *__restrict__ Gv,
               const double *__restrict__ Bm, const DM Dm, const AxArgs args, const CgFuse<T> cg,
               int *__restrict__ err) {
     constexpr int N1 = N + 1, NPT = N1 * N1 * N1;
-    constexpr int SB = ax_stage_bytes<N, T, HELM, CG, AFF, G16>();
+    constexpr int SB = ax_stage_bytes<N, T, HELM, CG, AFF, G16, EPC>();
     using GT = typename std::conditional<G16, __nv_bfloat16, T>::type;
     const GT *__restrict__ G = static_cast<const GT *>(Gv);
     // Vector r-line loads and D_kl as constant-bank operands cut the shared-
@@ -124,15 +130,19 @@ __global__ void __launch_bounds__(ax_threads<N>())
     if (CG && cg.scal->done) return;  // uniform: the solve has converged or paused
     if (args.guard && *args.guard != args.guard_value) return;  // uniform: not this phase
     const int nst = args.nst;
-    T *svr = reinterpret_cast<T *>(smem + nst * SB);
-    T *svs = svr + NPT;
-    T *sD = svs + NPT;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + nst * SB + 2 * NPT * sizeof(T) +
+    T *svr0 = reinterpret_cast<T *>(smem + nst * SB);
+    T *svs0 = svr0 + EPC * NPT;
+    T *sD = svs0 + EPC * NPT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + nst * SB + 2 * EPC * NPT * sizeof(T) +
                                                  ((N1 * N1 * sizeof(T) + 15) / 16 * 16));
-    double *sred = reinterpret_cast<double *>(bar + 4);  // 8 doubles: per-warp partials
+    double *sred = reinterpret_cast<double *>(bar + 4);  // 32 doubles: per-warp partials
     const int tid = threadIdx.x;
-    const bool active = tid < N1 * N1;
-    const int i = tid % N1, j = tid / N1;
+    const int slot = tid / (N1 * N1);             // element of the CTA's group
+    const bool active = slot < EPC;
+    const int lt = tid - slot * N1 * N1;
+    const int i = lt % N1, j = lt / N1;
+    T *svr = svr0 + (active ? slot : 0) * NPT;
+    T *svs = svs0 + (active ? slot : 0) * NPT;
 
     for (int q = tid; q < N1 * N1; q += blockDim.x) sD[q] = (T)Dm.d[q];
     if (tid == 0) {
@@ -162,75 +172,87 @@ __global__ void __launch_bounds__(ax_threads<N>())
     }
 
     const int64_t E = args.E;
+    const int64_t C = (E + EPC - 1) / EPC;  // element groups
     const int64_t stride = gridDim.x;
     const uint32_t ubytes = NPT * sizeof(T), gbytes = AFF ? 16 : 6 * NPT * sizeof(GT);
     const uint32_t bbytes = HELM ? NPT * sizeof(double) : 0;
+    // stage layout: each input slab holds EPC elements, then EPC G slabs, then EPC B slabs
+    const uint32_t inoff = EPC * ubytes, goff = NIN * EPC * ubytes, boff = goff + EPC * gbytes;
 
     // CG with dinv == nullptr: the preconditioned residual z comes in r and
     // p <- z + beta p (general preconditioner); the dinv slab is not loaded
     const bool jac = CG && cg.dinv != nullptr;
     auto stage_ptr = [&](int s) { return smem + s * SB; };
-    auto issue = [&](int64_t e, int s) {
+    auto group_size = [&](int64_t c) { return (int)((E - c * EPC) < EPC ? (E - c * EPC) : EPC); };
+    auto issue = [&](int64_t c, int s) {
         unsigned char *st = stage_ptr(s);
-        mbar_arrive_expect_tx(&bar[s], NIN * ubytes + gbytes + bbytes - (CG && !jac ? ubytes : 0));
+        const int64_t e = c * EPC;
+        const uint32_t nv = (uint32_t)group_size(c);
+        mbar_arrive_expect_tx(&bar[s], nv * (NIN * ubytes + gbytes + bbytes - (CG && !jac ? ubytes : 0)));
         if (CG) {
-            bulk_g2s(st, cg.r + e * NPT, ubytes, &bar[s]);
-            if (jac) bulk_g2s(st + ubytes, cg.dinv + e * NPT, ubytes, &bar[s]);
-            bulk_g2s(st + 2 * ubytes, cg.p + e * NPT, ubytes, &bar[s]);
+            bulk_g2s(st, cg.r + e * NPT, nv * ubytes, &bar[s]);
+            if (jac) bulk_g2s(st + inoff, cg.dinv + e * NPT, nv * ubytes, &bar[s]);
+            bulk_g2s(st + 2 * inoff, cg.p + e * NPT, nv * ubytes, &bar[s]);
         } else {
-            bulk_g2s(st, u + e * NPT, ubytes, &bar[s]);
+            bulk_g2s(st, u + e * NPT, nv * ubytes, &bar[s]);
         }
-        bulk_g2s(st + NIN * ubytes, AFF ? G + e * 4 : G + e * 6 * NPT, gbytes, &bar[s]);
-        if (HELM) bulk_g2s(st + NIN * ubytes + gbytes, Bm + e * NPT, bbytes, &bar[s]);
+        bulk_g2s(st + goff, AFF ? G + e * 4 : G + e * 6 * NPT, nv * gbytes, &bar[s]);
+        if (HELM) bulk_g2s(st + boff, Bm + e * NPT, nv * bbytes, &bar[s]);
     };
 
     if (args.use_tma && tid == 0) {
         for (int s = 0; s < nst; ++s) {
-            const int64_t e = blockIdx.x + s * stride;
-            if (e < E) issue(e, s);
+            const int64_t c = blockIdx.x + s * stride;
+            if (c < C) issue(c, s);
         }
     }
 
     T pw_acc = T(0);
     int it = 0;
     bool ok = true;
-    for (int64_t e = blockIdx.x; e < E; e += stride, ++it) {
+    for (int64_t c = blockIdx.x; c < C; c += stride, ++it) {
         const int s = it % nst;
         const uint32_t parity = (it / nst) & 1;
         unsigned char *st = stage_ptr(s);
+        const int nv = group_size(c);
+        const bool mine_el = active && slot < nv;  // this thread's element exists
+        const int64_t e = c * EPC + (active ? slot : 0);
         if (args.use_tma) {
             bool mine = mbar_wait_bounded(&bar[s], parity, err, kDevTimeoutTma);
             ok = __syncthreads_and(mine);
             if (!ok) break;
         } else {
+            const int64_t e0 = c * EPC;
             T *dst = reinterpret_cast<T *>(st);
             if (CG) {
-                for (int q = tid; q < NPT; q += blockDim.x) {
-                    dst[q] = cg.r[e * NPT + q];
-                    if (jac) dst[NPT + q] = cg.dinv[e * NPT + q];
-                    dst[2 * NPT + q] = cg.p[e * NPT + q];
+                for (int q = tid; q < nv * NPT; q += blockDim.x) {
+                    dst[q] = cg.r[e0 * NPT + q];
+                    if (jac) dst[EPC * NPT + q] = cg.dinv[e0 * NPT + q];
+                    dst[2 * EPC * NPT + q] = cg.p[e0 * NPT + q];
                 }
             } else {
-                for (int q = tid; q < NPT; q += blockDim.x) dst[q] = u[e * NPT + q];
+                for (int q = tid; q < nv * NPT; q += blockDim.x) dst[q] = u[e0 * NPT + q];
             }
-            const GT *gs = AFF ? G + e * 4 : G + e * 6 * NPT;
-            GT *gd = reinterpret_cast<GT *>(st + NIN * ubytes);
-            for (int q = tid; q < (AFF ? 4 : 6 * NPT); q += blockDim.x) gd[q] = gs[q];
+            const GT *gs = AFF ? G + e0 * 4 : G + e0 * 6 * NPT;
+            GT *gd = reinterpret_cast<GT *>(st + goff);
+            for (int q = tid; q < nv * (AFF ? 4 : 6 * NPT); q += blockDim.x) gd[q] = gs[q];
             if (HELM) {
-                double *db = reinterpret_cast<double *>(st + NIN * ubytes + gbytes);
-                for (int q = tid; q < NPT; q += blockDim.x) db[q] = Bm[e * NPT + q];
+                double *db = reinterpret_cast<double *>(st + boff);
+                for (int q = tid; q < nv * NPT; q += blockDim.x) db[q] = Bm[e0 * NPT + q];
             }
             __syncthreads();
         }
-        // the operand: u, or the updated search direction p (CG)
-        T *su = reinterpret_cast<T *>(st) + (CG ? 2 * NPT : 0);
-        const GT *sg = reinterpret_cast<const GT *>(st + NIN * ubytes);
-        const double *sb = reinterpret_cast<const double *>(st + NIN * ubytes + gbytes);
+        // the operand: u, or the updated search direction p (CG); this
+        // thread's element's slabs
+        const int sl = active ? slot : 0;
+        T *su = reinterpret_cast<T *>(st) + (CG ? 2 * EPC * NPT : 0) + sl * NPT;
+        const GT *sg = reinterpret_cast<const GT *>(st + goff) + sl * (AFF ? 4 : 6 * NPT);
+        const double *sb = reinterpret_cast<const double *>(st + boff) + sl * NPT;
         if (CG) {
-            const T *sr = reinterpret_cast<const T *>(st);
-            const T *sdi = sr + NPT;
+            const T *sr = reinterpret_cast<const T *>(st) + sl * NPT;
+            const T *sdi = sr + EPC * NPT;
             T *pe = cg.p + e * NPT;
-            if (active) {
+            if (mine_el) {
 #pragma unroll
                 for (int k = 0; k < N1; ++k) {
                     const int q = i + N1 * (j + N1 * k);
@@ -243,7 +265,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
         }
 
         T ru[N1], rvt[N1];
-        if (active) {
+        if (mine_el) {
 #pragma unroll
             for (int k = 0; k < N1; ++k) ru[k] = su[i + N1 * (j + N1 * k)];
 #pragma unroll
@@ -282,7 +304,7 @@ __global__ void __launch_bounds__(ax_threads<N>())
             }
         }
         __syncthreads();
-        if (active) {
+        if (mine_el) {
             T *we = w + e * NPT;
 #pragma unroll
             for (int k = 0; k < N1; ++k) {
@@ -314,10 +336,10 @@ __global__ void __launch_bounds__(ax_threads<N>())
         }
         __syncthreads();  // stage s and svr/svs free again
         if (args.use_tma && tid == 0) {
-            const int64_t en = e + nst * stride;
-            if (en < E) {
+            const int64_t cn = c + nst * stride;
+            if (cn < C) {
                 fence_proxy_async_smem();
-                issue(en, s);
+                issue(cn, s);
             }
         }
     }
@@ -325,8 +347,8 @@ __global__ void __launch_bounds__(ax_threads<N>())
         // a wait gave up: drain the copies this CTA still has in flight (bounded)
         for (int s = 0; s < nst; ++s) {
             const int itn = it + ((s - it % nst) + nst) % nst;
-            const int64_t en = blockIdx.x + (int64_t)itn * stride;
-            if (en < E) mbar_wait_bounded(&bar[s], (itn / nst) & 1, err, kDevTimeoutTma);
+            const int64_t cn = blockIdx.x + (int64_t)itn * stride;
+            if (cn < C) mbar_wait_bounded(&bar[s], (itn / nst) & 1, err, kDevTimeoutTma);
         }
     }
     if (CG) {
@@ -370,27 +392,27 @@ __global__ void __launch_bounds__(ax_threads<N>())
 
 // ---------------------------------------------------------------- launch
 
-template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16>
-static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const void *G, double h1, double h2,
-                       const DM &Dm, const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st) {
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16, int EPC>
+static int launch_ax_epc(const sem_mesh *m, const T *u, T *w, const void *G, double h1, double h2, const DM &Dm,
+                         const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st, const AxTune &tune) {
     constexpr int NPT = (N + 1) * (N + 1) * (N + 1);
-    constexpr int threads = ax_threads<N>();
-    auto kern = ax_kernel<N, T, HELM, CG, AFF, DM, G16>;
+    constexpr int threads = ax_threads<N, EPC>();
+    auto kern = ax_kernel<N, T, HELM, CG, AFF, DM, G16, EPC>;
     int dev_max = 0;
     SEM_CUDA_CHECK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, AFF, N);
     int nst = tune.nst < 1 ? 1 : (tune.nst > 3 ? 3 : tune.nst);
-    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG, AFF, G16>(nst) > dev_max) --nst;
-    const int smem = ax_smem_bytes<N, T, HELM, CG, AFF, G16>(nst);
-    if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element does not fit in shared memory");
+    while (nst > 1 && ax_smem_bytes<N, T, HELM, CG, AFF, G16, EPC>(nst) > dev_max) --nst;
+    const int smem = ax_smem_bytes<N, T, HELM, CG, AFF, G16, EPC>(nst);
+    if (smem > dev_max) return fail(SEM_ERR_UNSUPPORTED, "element group does not fit in shared memory");
     SEM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     SEM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) per_sm = 1;
     if (tune.per_sm_cap > 0 && per_sm > tune.per_sm_cap) per_sm = tune.per_sm_cap;
+    const int64_t groups = (m->E + EPC - 1) / EPC;
     int64_t grid = (int64_t)m->num_sms * per_sm;
     if (grid > kAxMaxGrid) grid = kAxMaxGrid;
-    if (grid > m->E) grid = m->E;
+    if (grid > groups) grid = groups;
     AxArgs a;
     a.E = m->E;
     a.nst = nst;
@@ -409,6 +431,27 @@ static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const void *G, doubl
     kern<<<(int)grid, threads, smem, st>>>(u, w, G, m->B, Dm, a, cg, m->d_err);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
+}
+
+// Element groups of 2 and 4 are built for the FP32 operator of the general
+// and the BF16-factor forms (the solvers' inner loops, incl. the batched
+// one) at the orders whose (N+1)^2 lines leave warps partly empty.
+template <int N, typename T, bool AFF>
+constexpr bool ax_has_groups() {
+    return sizeof(T) == 4 && !AFF && N >= 2 && N <= 9 && ((N + 1) * (N + 1)) % 32 != 0;
+}
+
+template <int N, typename T, bool HELM, bool CG, bool AFF, typename DM, bool G16>
+static int launch_ax_n(const sem_mesh *m, const T *u, T *w, const void *G, double h1, double h2,
+                       const DM &Dm, const CgFuse<T> &cg, const int *guard, int gval, cudaStream_t st) {
+    const AxTune tune = tune_for(sizeof(T) == 8 ? 0 : 1, HELM, CG, AFF, N);
+    if constexpr (ax_has_groups<N, T, AFF>() && !HELM) {
+        if (tune.epc == 2)
+            return launch_ax_epc<N, T, HELM, CG, AFF, DM, G16, 2>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st, tune);
+        if (tune.epc == 4)
+            return launch_ax_epc<N, T, HELM, CG, AFF, DM, G16, 4>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st, tune);
+    }
+    return launch_ax_epc<N, T, HELM, CG, AFF, DM, G16, 1>(m, u, w, G, h1, h2, Dm, cg, guard, gval, st, tune);
 }
 
 template <typename T, bool HELM, bool CG, typename DM, bool AFF = false, bool G16 = false>
@@ -549,42 +592,64 @@ int sem_autotune_operator(const sem_mesh *m, int dtype, int fused_cg, void *scra
     const int dt = dtype == SEM_F64 ? 0 : 1, cg = fused_cg ? 1 : 0, N = m->N;
     AxTune &slot = g_ax_tune[dt][0][cg][dt == 1 && m->aff32 ? 1 : 0][N];
     const AxTune saved = slot;
-    const int stages[3] = {1, 2, 3}, caps[4] = {0, 1, 2, 4};
+    // the FP64 operator keeps one element per CTA and stages nothing across
+    // elements: only its CTA cap is tuned; the FP32 one sweeps pipeline depth
+    // x CTA cap x elements per CTA (groups where (N+1)^2 lines leave warps
+    // partly empty; see ax_has_groups)
+    const bool groups = dt == 1 && !m->aff32 && N >= 2 && N <= 9 && ((N + 1) * (N + 1)) % 32 != 0;
+    const int stages[3] = {1, 2, 3}, caps[4] = {0, 1, 2, 4}, epcs[3] = {1, 2, 4};
+    const int na = dt == 0 ? 1 : 3, ne = groups ? 3 : 1;
     float best = 1e30f;
-    AxTune bt{2, 0};
+    AxTune bt{2, 0, 1};
     out->configs = 0;
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 4; ++c) {
-            slot = AxTune{stages[a], caps[c]};
-            float ms = 0.f;
-            int s;
-            if (dt == 1 && cg)
-                s = time_operator<float, true>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st, &ms);
-            else if (dt == 1)
-                s = time_operator<float, false>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st, &ms);
-            else if (cg)
-                s = time_operator<double, true>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st, &ms);
-            else
-                s = time_operator<double, false>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st, &ms);
-            if (s != SEM_OK) {
-                slot = saved;
-                return s;
+    for (int a = 0; a < na; ++a)
+        for (int c = 0; c < 4; ++c)
+            for (int g = 0; g < ne; ++g) {
+                slot = AxTune{dt == 0 ? 2 : stages[a], caps[c], epcs[g]};
+                float ms = 0.f;
+                int s;
+                if (dt == 1 && cg)
+                    s = time_operator<float, true>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st,
+                                                   &ms);
+                else if (dt == 1)
+                    s = time_operator<float, false>(m, m->G32, m->Df, static_cast<float *>(bufs), scal, partial, 10, st,
+                                                    &ms);
+                else if (cg)
+                    s = time_operator<double, true>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st, &ms);
+                else
+                    s = time_operator<double, false>(m, m->G, m->D, static_cast<double *>(bufs), scal, partial, 5, st,
+                                                     &ms);
+                if (s != SEM_OK) {
+                    slot = saved;
+                    return s;
+                }
+                if (out->configs < SEM_TUNE_MAX_CONFIGS) {
+                    out->stages[out->configs] = slot.nst;
+                    out->caps[out->configs] = caps[c];
+                    out->epcs[out->configs] = epcs[g];
+                    out->ms[out->configs] = ms;
+                }
+                ++out->configs;
+                if (ms < best) {
+                    best = ms;
+                    bt = slot;
+                }
             }
-            if (out->configs < 16) {
-                out->stages[out->configs] = stages[a];
-                out->caps[out->configs] = caps[c];
-                out->ms[out->configs] = ms;
-            }
-            ++out->configs;
-            if (ms < best) {
-                best = ms;
-                bt = slot;
-            }
-        }
     slot = bt;
     out->best_stages = bt.nst;
     out->best_cap = bt.per_sm_cap;
+    out->best_epc = bt.epc;
     out->best_ms = best;
+    return SEM_OK;
+}
+
+int sem_autotune_set(const sem_mesh *m, int dtype, int fused_cg, int stages, int per_sm_cap, int epc) {
+    if (!m) return fail(SEM_ERR_INVALID_ARG, "NULL mesh");
+    if (dtype != SEM_F64 && dtype != SEM_F32) return fail(SEM_ERR_INVALID_ARG, "unknown dtype");
+    if (stages < 1 || stages > 3 || per_sm_cap < 0 || (epc != 1 && epc != 2 && epc != 4))
+        return fail(SEM_ERR_INVALID_ARG, "stages 1..3, per_sm_cap >= 0, epc 1, 2 or 4");
+    const int dt = dtype == SEM_F64 ? 0 : 1;
+    g_ax_tune[dt][0][fused_cg ? 1 : 0][dt == 1 && m->aff32 ? 1 : 0][m->N] = AxTune{stages, per_sm_cap, epc};
     return SEM_OK;
 }
 
@@ -593,7 +658,7 @@ int sem_autotune_reset(void) {
         for (auto &b : a)
             for (auto &c : b)
                 for (auto &d : c)
-                    for (auto &f : d) f = AxTune{0, 0};
+                    for (auto &f : d) f = AxTune{0, 0, 0};
     return SEM_OK;
 }
 

@@ -230,6 +230,7 @@ int gs_launch(const sem_mesh *m, void *u, int dtype, int mode, cudaStream_t st, 
 struct AxTune {
     int nst;         // pipeline stages, 0 = default (2)
     int per_sm_cap;  // resident CTAs per SM cap, 0 = occupancy limit
+    int epc;         // FP32 operator: elements per CTA (1, 2, 4), 0 = default (1)
 };
 extern AxTune g_ax_tune[2][2][2][2][kMaxN1];
 int jacobi_diag_launch(const sem_mesh *m, double *diag, cudaStream_t st);

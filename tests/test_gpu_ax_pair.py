@@ -1,14 +1,19 @@
-"""The FP64 operator evaluated in FP32-pair arithmetic (sem_ax, SEM_F64_PAIR)
-against the FP64 oracle.
+"""The FP64-in/out operator evaluated in double-float arithmetic (sem_ax,
+SEM_F64_PAIR) against the FP64 oracle.  It is not FP64 arithmetic and its
+bars are those of its format, not FP64's:
 
-Bar: the same 1e-12 relative 2-norm as the FP64 operator on rough fields.
-The pair format carries 48 significant bits and every product and line sum
-keeps its exact rounding error, but the anchored sums and the FP32 low parts
-leave about 2^-42 of the line-wise magnitudes |D^T||G||D||u|; on smooth
-fields, where A u cancels strongly, that measure is the bar (2^-41,
-pointwise) with 1e-11 in the relative 2-norm.  The
-element-wise power-of-two scaling makes the result exactly homogeneous:
-w(2^k u) = 2^k w(u) bit for bit.
+Rough fields: the 1e-12 relative 2-norm of the FP64 operator.  The pair
+format carries 48 significant bits and every product and line sum keeps its
+exact rounding error, but the anchored sums and the FP32 low parts leave
+about 2^-42 of the line-wise magnitudes |D^T||G||D||u|; on smooth fields,
+where A u cancels strongly, that measure is the bar (2^-41, pointwise) with
+1e-11 in the relative 2-norm.  The element-wise power-of-two scaling makes
+the result exactly homogeneous: w(2^k u) = 2^k w(u) bit for bit.
+
+Solves with FP64 vectors around this operator (SEM_PCG_F64_PAIR) are gated
+like the other non-FP64 paths: the oracle's own true residual of the
+returned solution, the iteration count of the FP64 solver (same Krylov
+process) and continuity.
 """
 import numpy as np
 import pytest
@@ -106,7 +111,7 @@ def test_full_size_ax_pair_sampled_elements():
     assert _rel(w[sel], ref) <= AX_TOL
 
 
-# ------------------------------------------------------------------ the FP64 solver on the pair operator
+# ------------------------------------------------------------------ FP64 vectors around the double-float operator
 # Gate as for the other non-FP64 paths: the oracle's own residual of the
 # returned solution, the iteration count of the FP64 solver (same Krylov
 # process), and continuity (every copy of a node holds the same value).

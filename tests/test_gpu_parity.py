@@ -378,20 +378,46 @@ def test_full_size_deformed64_mixed_true_residual():
 
 
 def test_autotune_reports_and_keeps_the_fastest():
-    """The autotuner times every (pipeline depth, CTA cap) of the operator,
-    keeps the fastest in the launch table, and the operator stays correct
-    under it."""
+    """The autotuner times every launch shape of the operator -- FP32:
+    pipeline depth x CTA cap x elements per CTA (N = 5: 36 of 64 threads of
+    a one-element CTA have a line), FP64: CTA cap -- keeps the fastest in the
+    launch table, and the operator stays correct under it."""
     torch = _torch()
     case = inputs.channel(6, 5)
     om, gm = _pair(case, geom_f32=True)
     try:
-        for dt, cg in ((binding.SEM_F32, True), (binding.SEM_F64, False)):
+        for dt, cg, n in ((binding.SEM_F32, True, 36), (binding.SEM_F64, False, 4)):
             r = gm.autotune(dt, cg)
-            assert len(r["table"]) == 12
-            best = min(r["table"], key=lambda t: t[2])
-            assert (r["best_stages"], r["best_cap"]) == best[:2]
-            assert r["best_ms"] == pytest.approx(best[2])
+            assert len(r["table"]) == n
+            best = min(r["table"], key=lambda t: t[3])
+            assert (r["best_stages"], r["best_cap"], r["best_epc"]) == best[:3]
+            assert r["best_ms"] == pytest.approx(best[3])
         u = np.random.default_rng(3).standard_normal(om.nloc)
         assert _rel(_host(gm.ax(_dev(u))), om.ax_local(u)) <= AX_TOL
     finally:
         binding.lib().sem_autotune_reset()
+
+
+@pytest.mark.parametrize("epc", [2, 4])
+@pytest.mark.parametrize("stages", [1, 2])
+def test_fp32_operator_element_groups_match_oracle(epc, stages):
+    """Block shapes of 2 and 4 elements per CTA (incl. a last group with
+    fewer elements: E = 3 x 4 x 5 = 60 is not a multiple of 8 groups of 4 in
+    a wave): the FP32 operator and the mixed solve against the oracle."""
+    torch = _torch()
+    for case in (inputs.BoxCase("g5", 5, (3, 4, 5), (0, 1, 0), inputs.ALL_FACES, perturb_amp=0.05, seed=7),
+                 inputs.BoxCase("g9", 9, (3, 1, 3), (1, 0, 0), inputs.Y_FACES, jitter=0.05, seed=8)):
+        om, gm = _pair(case, geom_f32=True)
+        try:
+            gm.autotune_set(binding.SEM_F32, False, stages, 0, epc)
+            gm.autotune_set(binding.SEM_F32, True, stages, 0, epc)
+            u = np.random.default_rng(4).standard_normal(om.nloc)
+            w = _host(gm.ax(_dev(u).float()).double())
+            assert _rel(w, om.ax_local(u)) <= 5e-6
+            b = om.scatter(case.rhs_global())
+            xg, st = gm.pcg(_dev(b), tol=1e-10, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2)
+            assert st["status"] == 0
+            r = b - om.apply(_host(xg))
+            assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 1.05e-10
+        finally:
+            binding.lib().sem_autotune_reset()
