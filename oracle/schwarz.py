@@ -6,9 +6,10 @@ The paper (section 3.1) solves the pressure with a Krylov method and "a
 hybrid-Schwarz multigrid preconditioner" and gives no formulas; the method
 it names is the overlapping Schwarz / fast-diagonalisation preconditioner of
 the SEM literature it cites for the numerics (Deville, Fischer & Mund 2002).
-The reading implemented here (additive, two levels, symmetric):
+The reading implemented here (additive, symmetric; two levels, or three
+with an intermediate order M damped by w_M):
 
-  z = M r = sum_e R_e^T A_e^{-1} R_e r  +  P A_c^{-1} P^T r
+  z = M r = sum_e R_e^T A_e^{-1} R_e r  [+ w_M P_M S_M P_M^T r]  +  P A_c^{-1} P^T r
 
 * Local solves.  Subdomain e is element e extended by one GLL point into each
   neighbour (N+3 points per direction).  Along each direction the 1-D
@@ -177,14 +178,71 @@ class CoarseLevel:
         return self.prolong(xc)
 
 
+def lagrange_interp(M, N):
+    """J[i, a] = l^M_a(xi^N_i): the order-M GLL Lagrange basis evaluated at the
+    order-N GLL points (Lagrange's product formula; exactly 1 / 0 where the
+    point sets share a node, so element faces map to faces)."""
+    xm, _ = gll(M)
+    xn, _ = gll(N)
+    J = np.zeros((N + 1, M + 1))
+    for i, x in enumerate(xn):
+        for a in range(M + 1):
+            if abs(x - xm[a]) < 1e-14:
+                J[i, :] = 0.0
+                J[i, a] = 1.0
+                break
+            J[i, a] = np.prod([(x - xm[b]) / (xm[a] - xm[b]) for b in range(M + 1) if b != a])
+    return J
+
+
+class MidLevel:
+    """Intermediate level of the multigrid: the overlapping Schwarz of the
+    order-M discretisation on the same elements, reached by element-wise
+    interpolation.  P_M x interpolates a continuous order-M field to the
+    order-N points; its adjoint in the unique-node products is
+    P_M^T r = Q_M Q_M^T J^T (r / mult_N) (masked); the level applies
+    P_M S_M P_M^T."""
+
+    def __init__(self, N, M, nel, periodic, faces, verts, mesh: Mesh):
+        self.N, self.M, self.m = N, M, mesh
+        self.mm = Mesh(M, nel, periodic, faces, verts)
+        self.sw = SchwarzFDM(M, nel, periodic, faces, verts, self.mm)
+        self.J = lagrange_interp(M, N)
+
+    def restrict(self, r):
+        E, n1 = self.m.E, self.N + 1
+        rl = (r / self.m.mult).reshape(E, n1, n1, n1)
+        J = self.J
+        rm = np.einsum("ia,jb,kc,ekji->ecba", J, J, J, rl).reshape(-1)
+        return self.mm.apply_mask(self.mm.dssum(rm))
+
+    def prolong(self, xm):
+        E, m1, J = self.m.E, self.M + 1, self.J
+        return np.einsum("ia,jb,kc,ecba->ekji", J, J, J, xm.reshape(E, m1, m1, m1)).reshape(-1)
+
+    def apply(self, r):
+        return self.prolong(self.sw.apply(self.restrict(r)))
+
+
 class HybridSchwarz:
-    def __init__(self, N, nel, periodic, faces, verts, mesh: Mesh | None = None, coarse=True):
+    """z = S_N r + w_M P_M S_M P_M^T r + P_1 A_1^{-1} P_1^T r (masked): the fine
+    overlapping Schwarz, an optional intermediate order-M Schwarz level with
+    weight w_M (mid_order = None: two levels) and the trilinear coarse
+    level.  The levels are added (symmetric); the intermediate one is damped
+    because its correction overlaps the fine level's."""
+
+    def __init__(self, N, nel, periodic, faces, verts, mesh: Mesh | None = None, coarse=True, mid_order=None,
+                 mid_weight=0.15):
         self.m = mesh if mesh is not None else Mesh(N, nel, periodic, faces, verts)
         self.sw = SchwarzFDM(N, nel, periodic, faces, verts, self.m)
         self.cl = CoarseLevel(N, nel, periodic, faces, verts, self.m) if coarse else None
+        self.mid = MidLevel(N, mid_order, nel, periodic, faces, verts, self.m) if mid_order else None
+        self.mid_weight = mid_weight
 
     def apply(self, r):
         z = self.sw.apply(r)
+        if self.mid is not None:
+            z = z + self.mid_weight * self.mid.apply(r)
         if self.cl is not None:
             z = z + self.cl.apply(r)
         return self.m.apply_mask(z)

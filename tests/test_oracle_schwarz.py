@@ -149,3 +149,71 @@ def test_multiplicative_levels_gain_nothing_over_additive():
     assert rela <= 1e-10 and relm <= 1e-10
     assert np.linalg.norm(xa - xm) <= 1e-8 * np.linalg.norm(xa)
     assert abs(ita - itm) <= max(2, ita // 10), (ita, itm)
+
+
+# ------------------------------------------------------------------ intermediate (order-M) level
+
+@pytest.mark.parametrize("M,N", [(1, 3), (2, 5), (3, 7), (4, 9)])
+def test_lagrange_interp_exact_to_degree_M(M, N):
+    xm, _ = oracle.gll(M)
+    xn, _ = oracle.gll(N)
+    J = sw.lagrange_interp(M, N)
+    for k in range(M + 1):
+        assert np.abs(J @ xm ** k - xn ** k).max() <= 1e-13
+    # and not beyond: degree M + 1 is not reproduced
+    assert np.abs(J @ xm ** (M + 1) - xn ** (M + 1)).max() > 1e-3
+    # the end points map to end points exactly (faces to faces)
+    assert np.array_equal(J[0], np.eye(M + 1)[0]) and np.array_equal(J[N], np.eye(M + 1)[M])
+    assert np.abs(J.sum(axis=1) - 1.0).max() <= 1e-14
+
+
+def test_mid_transfer_pair():
+    case = inputs.BoxCase("aff", 5, (2, 3, 2), (0, 0, 0), inputs.ALL_FACES, lo=(0.0, -1.0, 0.5), hi=(2.0, 1.0, 1.5))
+    V = case.vertices()
+    m = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    L = sw.MidLevel(case.N, 3, case.nel, case.periodic, case.faces, V, m)
+    # on affine elements the prolongation reproduces polynomials of degree <= M exactly
+    f = lambda x, y, z: 0.3 * x ** 3 - 1.1 * x * y * z + 0.7 * y ** 2 + z - 0.5
+    xm, ym, zm = L.mm.xyz
+    pf = L.prolong(f(xm, ym, zm).reshape(-1))
+    x, y, z = m.xyz
+    assert np.abs(pf - f(x, y, z).reshape(-1)).max() <= 1e-12
+    # the restriction is its adjoint in the unique-node products
+    rng = np.random.default_rng(9)
+    r = m.scatter(rng.standard_normal(m.nglob))
+    xmid = L.mm.scatter(rng.standard_normal(L.mm.nglob))
+    lhs = float(np.sum(L.prolong(xmid) * r / m.mult))
+    rm = L.mm.dssum(np.einsum("ia,jb,kc,ekji->ecba", L.J, L.J, L.J,
+                              (r / m.mult).reshape(m.E, case.N + 1, case.N + 1, case.N + 1)).reshape(-1))
+    rhs = float(np.sum(xmid * rm / L.mm.mult))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_three_level_preconditioner_spd_and_solves():
+    case = inputs.deformed_cube(3, 5)
+    V = case.vertices()
+    H = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V, mid_order=3)
+    m = H.m
+    rng = np.random.default_rng(11)
+    x = m.apply_mask(m.scatter(rng.standard_normal(m.nglob)))
+    y = m.apply_mask(m.scatter(rng.standard_normal(m.nglob)))
+    a, b = m.glsc3(x, H.apply(y)), m.glsc3(y, H.apply(x))
+    assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    assert m.glsc3(x, H.apply(x)) > 0 and m.glsc3(y, H.apply(y)) > 0
+    bb = m.scatter(case.rhs_global())
+    xo, _, _, st = m.pcg(bb, tol=1e-12, max_iter=20000)
+    x3, _, rel = sw.fpcg(m, bb, H.apply, tol=1e-12)
+    assert st == 0 and rel <= 1e-12
+    assert np.linalg.norm(x3 - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_three_level_fewer_iterations_on_the_channel():
+    case = inputs.channel(4, 7)
+    V = case.vertices()
+    H2 = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V)
+    H3 = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V, mesh=H2.m, mid_order=3)
+    m = H2.m
+    b = m.scatter(case.rhs_global())
+    _, i2, _ = sw.fpcg(m, b, H2.apply, tol=1e-10)
+    _, i3, _ = sw.fpcg(m, b, H3.apply, tol=1e-10)
+    assert i3 <= 0.9 * i2, (i3, i2)
