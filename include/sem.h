@@ -257,6 +257,11 @@ typedef struct {
                               SEM_ERR_INVALID_ARG): ~2^-42 of the line-wise
                               magnitudes instead of FP64 rounding, 5x faster on
                               GB300; 0 (default): the FP64 operator */
+    const struct sem_schwarz *schwarz_mid;  /* with schwarz: the intermediate level of the
+                              Schwarz multigrid (a Schwarz object built on the
+                              order-M mesh of the same elements, M < N, see
+                              sem_schwarz_apply3); NULL: two levels */
+    double mid_weight;     /* its weight w_M (0 = 0.15) */
 } sem_pcg_opts;
 
 typedef struct {
@@ -561,6 +566,25 @@ int sem_schwarz_line_table(int N, short *out, int cap, int *slots, int *pj, int 
  * the mesh's error word (reported as SEM_ERR_TIMEOUT by the solver). */
 int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
                       void *stream);
+
+/* The three-level Schwarz multigrid (section 3.1 names a hybrid-Schwarz
+ * multigrid; its depth is read here as the paper's solver, Neko, uses it:
+ * fine order N, an intermediate order M, the trilinear coarse level):
+ *   z = S_N r + w_M P_M S_M P_M^T r + P A_c^{-1} P^T r,
+ * S_N r + P A_c^{-1} P^T r as sem_schwarz_apply(sw, ...); S_M the
+ * overlapping Schwarz of `mid` (a Schwarz object built on the order-M mesh
+ * of the same elements and topology, M < N; its coarse level is not used);
+ * P_M element-wise interpolation from the order-M GLL points to the order-N
+ * ones (exact for degree <= M), P_M^T r = Q_M Q_M^T J^T (r / mult) masked.
+ * The levels are added (symmetric); w_M > 0 damps the intermediate level,
+ * whose correction overlaps the fine one (0.15 on the channel).  r, z:
+ * device FP32 E-layout as sem_schwarz_apply; d_work: device, 256-byte
+ * aligned, sem_schwarz_mid_work_bytes(mid) bytes.  Stream-ordered.
+ * SEM_ERR_INVALID_ARG for a mismatched `mid` or w_M <= 0, SEM_ERR_WORKSPACE
+ * for missing work space. */
+size_t sem_schwarz_mid_work_bytes(const sem_schwarz *mid);
+int sem_schwarz_apply3(const sem_schwarz *sw, const sem_schwarz *mid, double mid_weight, const float *r, float *z,
+                       int coarse_iters, double coarse_tol, void *d_work, size_t bytes, void *stream);
 
 /* ---- Performance model for splitting one problem over devices -----------
  * Section 4.1 (Eq. 2-7): a homogeneous cost C (here: element-iterations of a

@@ -53,7 +53,7 @@ class PcgOpts(ctypes.Structure):
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int),
                 ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double),
-                ("outer_pair", ctypes.c_int)]
+                ("outer_pair", ctypes.c_int), ("schwarz_mid", ctypes.c_void_p), ("mid_weight", ctypes.c_double)]
 
 
 class PcgStats(ctypes.Structure):
@@ -159,6 +159,9 @@ _SIGS = {
                            ctypes.c_int),
     "sem_schwarz_line_table": ([ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
     "sem_schwarz_coarse_operator": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "sem_schwarz_mid_work_bytes": ([_VP], ctypes.c_size_t),
+    "sem_schwarz_apply3": ([_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, ctypes.c_size_t,
+                            _VP], ctypes.c_int),
     "sem_schwarz_apply": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP], ctypes.c_int),
     "sem_perf_model": ([ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP],
                        ctypes.c_int),
@@ -312,13 +315,15 @@ class Mesh:
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
                  mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2,
-                 outer_pair=False) -> PcgOpts:
+                 outer_pair=False, schwarz_mid=None, mid_weight=0.15) -> PcgOpts:
         """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
         preconditioner of the mixed solver), its coarse level solved by
         coarse_iters Jacobi-CG iterations (3: on the 32^3 channel, N = 7, more
         do not lower the outer iteration count) to coarse_tol."""
         o = PcgOpts()
         o.schwarz = schwarz.handle.value if schwarz is not None else None
+        o.schwarz_mid = schwarz_mid.handle.value if schwarz_mid is not None else None
+        o.mid_weight = float(mid_weight)
         o.coarse_iters, o.coarse_tol = int(coarse_iters), float(coarse_tol)
         o.outer_pair = int(bool(outer_pair))
         o.profile = int(bool(profile))
@@ -742,4 +747,16 @@ class Schwarz:
             z = torch.empty_like(r)
         check(lib().sem_schwarz_apply(self.handle, _ptr(r), _ptr(z), int(coarse_iters), float(coarse_tol), _stream()),
               "sem_schwarz_apply")
+        return z
+
+    def apply3(self, mid, r, mid_weight=0.15, coarse_iters=3, coarse_tol=1e-2, z=None):
+        """z = M r with the intermediate level `mid` (sem_schwarz_apply3)."""
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        n = lib().sem_schwarz_mid_work_bytes(mid.handle)
+        work = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        base = (work.data_ptr() + 255) // 256 * 256
+        check(lib().sem_schwarz_apply3(self.handle, mid.handle, float(mid_weight), _ptr(r), _ptr(z), int(coarse_iters),
+                                       float(coarse_tol), _VP(base), n, _stream()), "sem_schwarz_apply3")
         return z

@@ -282,6 +282,12 @@ int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coars
                       const int *done, cudaStream_t st);
 // The (fine) mesh a Schwarz object was built on.
 const sem_mesh *schwarz_mesh(const sem_schwarz *sw);
+// Intermediate (order-M) level of the Schwarz multigrid (sem_schwarz.cu):
+// z += w P_M S_M P_M^T r; work: schwarz_mid_work_bytes; done: guard flag.
+size_t schwarz_mid_work_bytes(const sem_schwarz *mid);
+int schwarz_mid_check(const sem_schwarz *sw, const sem_schwarz *mid);
+int schwarz_mid_apply_add(const sem_schwarz *sw, const sem_schwarz *mid, double w, const float *r, float *z,
+                          void *work, const int *done, cudaStream_t st);
 
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies

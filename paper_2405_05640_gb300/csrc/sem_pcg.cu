@@ -466,7 +466,9 @@ static size_t pcg_scratch_mixed(const sem_mesh *m) {
 }
 
 static size_t pcg_scratch(const sem_mesh *m, const sem_pcg_opts *o) {
-    return (o && o->precision == SEM_PCG_MIXED) ? pcg_scratch_mixed(m) : pcg_scratch_f64(m);
+    if (o && o->precision == SEM_PCG_MIXED)
+        return pcg_scratch_mixed(m) + (o->schwarz && o->schwarz_mid ? schwarz_mid_work_bytes(o->schwarz_mid) : 0);
+    return pcg_scratch_f64(m);
 }
 
 static PcgWork<double> carve_f64(const sem_mesh *m, void *scratch) {
@@ -700,7 +702,7 @@ static int launch_fpcg_dots_box(const sem_mesh *m, const float *r, const float *
 // the assembled A p); host check every `check` iterations.
 static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float *wa, float *x, const sem_schwarz *sw,
                            int coarse_iters, double coarse_tol, int max_iter, int check, cudaStream_t st, SolveCtx &c,
-                           PcgScal *h) {
+                           PcgScal *h, const sem_schwarz *mid = nullptr, double mid_w = 0.0, void *mid_work = nullptr) {
     CgFuse<float> cg{z, nullptr, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
     while (true) {
@@ -712,6 +714,11 @@ static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float 
         for (int q = 0; q < check && launched < max_iter; ++q, ++launched) {
             int s = schwarz_apply_f32(sw, W.r, z, coarse_iters, coarse_tol, &W.scal->done, st);
             if (s != SEM_OK) return s;
+            if (mid) {  // the intermediate level of the multigrid
+                s = schwarz_mid_apply_add(sw, mid, mid_w, W.r, z, mid_work, &W.scal->done, st);
+                if (s != SEM_OK) return s;
+                c.launches += 4;
+            }
             s = launch_fpcg_dots_box(m, W.r, z, wa, W, launched == 0 ? 1 : 0, st);
             if (s != SEM_OK) return s;
             c.tax.start(st);
@@ -841,7 +848,9 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         int s;
         if (sw)
             s = cg_loop_schwarz(m, M.in, M.z32, M.wa32, M.d32, sw, o->coarse_iters, o->coarse_tol > 0 ? o->coarse_tol : 1e-2,
-                                o->max_iter - inner_total, check, st, cin, &hi);
+                                o->max_iter - inner_total, check, st, cin, &hi, o->schwarz_mid,
+                                o->mid_weight > 0.0 ? o->mid_weight : 0.15,
+                                static_cast<char *>(scratch) + pcg_scratch_mixed(m));
         else
             s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st, cin,
                                &hi);
@@ -882,6 +891,13 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_INVALID_ARG, "the Schwarz preconditioner was built on another mesh");
     if (o->schwarz && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
         return fail(SEM_ERR_UNSUPPORTED, "the Schwarz preconditioner is built for the Poisson operator");
+    if (o->schwarz_mid && !o->schwarz)
+        return fail(SEM_ERR_INVALID_ARG, "schwarz_mid is the intermediate level of a Schwarz preconditioner");
+    if (o->schwarz_mid) {
+        int s = schwarz_mid_check(o->schwarz, o->schwarz_mid);
+        if (s != SEM_OK) return s;
+        if (o->mid_weight < 0.0) return fail(SEM_ERR_INVALID_ARG, "mid_weight < 0");
+    }
     if (o->precision == SEM_PCG_F64_PAIR && !m->G2)
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_F64_PAIR needs a mesh built with SEM_GEOM_PAIR");
     if (o->precision == SEM_PCG_F64_PAIR && (o->h2 != 0.0 || o->h1 != 1.0))
@@ -1255,7 +1271,8 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");
     if (o->precision != SEM_PCG_MIXED) return fail(SEM_ERR_UNSUPPORTED, "batched solves use SEM_PCG_MIXED");
     if (o->use_initial_guess) return fail(SEM_ERR_UNSUPPORTED, "batched solves start from x = 0");
-    if (o->schwarz || o->outer_pair) return fail(SEM_ERR_UNSUPPORTED, "batched solves use the Jacobi inner solver");
+    if (o->schwarz || o->schwarz_mid || o->outer_pair)
+        return fail(SEM_ERR_UNSUPPORTED, "batched solves use the Jacobi inner solver");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     for (int i = 0; i < nsolve; ++i) {
         if (!meshes[i] || !b[i] || !x[i]) return fail(SEM_ERR_INVALID_ARG, "NULL mesh, b or x");

@@ -1162,6 +1162,207 @@ int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coars
 
 const sem_mesh *schwarz_mesh(const sem_schwarz *sw) { return sw ? sw->m : nullptr; }
 
+// ---------------------------------------------------------------- intermediate level
+//
+// The multigrid's intermediate level: the overlapping Schwarz of the order-M
+// discretisation on the same elements (a Schwarz object built on the order-M
+// mesh), reached by element-wise interpolation between the GLL point sets:
+//   z += w P_M S_M P_M^T r,  P_M^T r = Q_M Q_M^T J^T (r / mult_N) (masked),
+// with J[i][a] = l^M_a(xi^N_i).  One CTA per element (grid-stride), the three
+// 1-D contractions through shared memory, every sum in a fixed order; J's
+// end rows are exact unit vectors, so the copies of a face point of the
+// prolongation are bit-identical (z stays continuous).
+
+struct MidJ {
+    float J[kMaxN1 * kMaxN1];  // J[i * (M+1) + a]
+};
+constexpr int kMidThreads = 256;
+constexpr int kMidEpb = 4;  // elements per CTA and pass: 4 consecutive slabs, coalesced
+
+// P_M^T r element-wise (before the order-M gather-scatter): rm = J^T J^T J^T
+// (r / mult), the three contractions through shared memory for kMidEpb
+// elements at a time; J in shared memory.
+template <int N, int M>
+__global__ void __launch_bounds__(kMidThreads)
+    mid_restrict_kernel(const float *__restrict__ r, const float *__restrict__ minv, const MidJ Jp, int64_t E,
+                        const int *__restrict__ done, float *__restrict__ rm) {
+    if (done && *done) return;
+    constexpr int N1 = N + 1, M1 = M + 1, NPT = N1 * N1 * N1, MPT = M1 * M1 * M1, B = kMidEpb;
+    __shared__ float sJ[N1 * M1];
+    __shared__ float sa[B * NPT], s1[B * N1 * N1 * M1], s2[B * N1 * M1 * M1];
+    for (int q = threadIdx.x; q < N1 * M1; q += blockDim.x) sJ[q] = Jp.J[q];
+    const int64_t G = (E + B - 1) / B;
+    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+        const int64_t e0 = g * B;
+        const int nv = (int)((E - e0) < B ? (E - e0) : B);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * NPT; q += blockDim.x) sa[q] = r[e0 * NPT + q] * minv[e0 * NPT + q];
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * N1 * N1 * M1; q += blockDim.x) {  // (e, k, j, a): over i
+            const int a = q % M1, ekj = q / M1;
+            float t = 0.f;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) t = fmaf(sJ[i * M1 + a], sa[ekj * N1 + i], t);
+            s1[q] = t;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * N1 * M1 * M1; q += blockDim.x) {  // (e, k, b, a): over j
+            const int a = q % M1, b = (q / M1) % M1, ek = q / (M1 * M1);
+            float t = 0.f;
+#pragma unroll
+            for (int j = 0; j < N1; ++j) t = fmaf(sJ[j * M1 + b], s1[(ek * N1 + j) * M1 + a], t);
+            s2[q] = t;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * MPT; q += blockDim.x) {  // (e, c, b, a): over k
+            const int ba = q % (M1 * M1), c = (q / (M1 * M1)) % M1, el = q / MPT;
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) t = fmaf(sJ[k * M1 + c], s2[(el * N1 + k) * M1 * M1 + ba], t);
+            rm[e0 * MPT + q] = t;
+        }
+    }
+}
+
+// z += w P_M zm element-wise (zm continuous: the copies of a face point get
+// the same bits, J's end rows being exact unit vectors).
+template <int N, int M>
+__global__ void __launch_bounds__(kMidThreads)
+    mid_prolong_add_kernel(const float *__restrict__ zm, const MidJ Jp, float w, int64_t E,
+                           const int *__restrict__ done, float *__restrict__ z) {
+    if (done && *done) return;
+    constexpr int N1 = N + 1, M1 = M + 1, NPT = N1 * N1 * N1, MPT = M1 * M1 * M1, B = kMidEpb;
+    __shared__ float sJ[N1 * M1];
+    __shared__ float s0[B * MPT], s1[B * M1 * M1 * N1], s2[B * M1 * N1 * N1];
+    for (int q = threadIdx.x; q < N1 * M1; q += blockDim.x) sJ[q] = Jp.J[q];
+    const int64_t G = (E + B - 1) / B;
+    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+        const int64_t e0 = g * B;
+        const int nv = (int)((E - e0) < B ? (E - e0) : B);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * MPT; q += blockDim.x) s0[q] = zm[e0 * MPT + q];
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * M1 * M1 * N1; q += blockDim.x) {  // (e, c, b, i): over a
+            const int i = q % N1, ecb = q / N1;
+            float t = 0.f;
+#pragma unroll
+            for (int a = 0; a < M1; ++a) t = fmaf(sJ[i * M1 + a], s0[ecb * M1 + a], t);
+            s1[q] = t;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * M1 * N1 * N1; q += blockDim.x) {  // (e, c, j, i): over b
+            const int i = q % N1, j = (q / N1) % N1, ec = q / (N1 * N1);
+            float t = 0.f;
+#pragma unroll
+            for (int b = 0; b < M1; ++b) t = fmaf(sJ[j * M1 + b], s1[(ec * M1 + b) * N1 + i], t);
+            s2[q] = t;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nv * NPT; q += blockDim.x) {  // (e, k, j, i): over c
+            const int ji = q % (N1 * N1), k = (q / (N1 * N1)) % N1, el = q / NPT;
+            float t = 0.f;
+#pragma unroll
+            for (int c = 0; c < M1; ++c) t = fmaf(sJ[k * M1 + c], s2[(el * M1 + c) * N1 * N1 + ji], t);
+            z[e0 * NPT + q] = fmaf(w, t, z[e0 * NPT + q]);
+        }
+    }
+}
+
+template <int N, int M>
+static int mid_launch_nm(bool prolong, const float *in, const float *minv, const MidJ &J, float w, int64_t E,
+                         int num_sms, const int *done, float *out, cudaStream_t st) {
+    const int64_t G = (E + kMidEpb - 1) / kMidEpb;
+    const int grid = (int)(G < (int64_t)num_sms * 8 ? G : (int64_t)num_sms * 8);
+    if (prolong)
+        mid_prolong_add_kernel<N, M><<<grid, kMidThreads, 0, st>>>(in, J, w, E, done, out);
+    else
+        mid_restrict_kernel<N, M><<<grid, kMidThreads, 0, st>>>(in, minv, J, E, done, out);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+template <int N>
+static int mid_launch_n(int M, bool prolong, const float *in, const float *minv, const MidJ &J, float w, int64_t E,
+                        int num_sms, const int *done, float *out, cudaStream_t st) {
+    switch (M) {
+#define SEM_MID_M(mm) \
+    case mm:           \
+        if constexpr (mm < N) return mid_launch_nm<N, mm>(prolong, in, minv, J, w, E, num_sms, done, out, st); \
+        break;
+        SEM_MID_M(2) SEM_MID_M(3) SEM_MID_M(4) SEM_MID_M(5) SEM_MID_M(6) SEM_MID_M(7) SEM_MID_M(8)
+#undef SEM_MID_M
+        default: break;
+    }
+    return fail(SEM_ERR_UNSUPPORTED, "intermediate order outside 2 <= M < N");
+}
+
+static int mid_launch(int N, int M, bool prolong, const float *in, const float *minv, const MidJ &J, float w,
+                      int64_t E, int num_sms, const int *done, float *out, cudaStream_t st) {
+    switch (N) {
+#define SEM_MID_N(nn) \
+    case nn: return mid_launch_n<nn>(M, prolong, in, minv, J, w, E, num_sms, done, out, st);
+        SEM_MID_N(3) SEM_MID_N(4) SEM_MID_N(5) SEM_MID_N(6) SEM_MID_N(7) SEM_MID_N(8) SEM_MID_N(9)
+#undef SEM_MID_N
+        default: return fail(SEM_ERR_UNSUPPORTED, "intermediate level built for 3 <= N <= 9");
+    }
+}
+
+// J[i][a] = l^M_a(xi^N_i) by Lagrange's product formula (host, FP64).
+static void mid_interp(const sem_mesh *fine, const sem_mesh *mid, MidJ &out) {
+    const int N1 = fine->N + 1, M1 = mid->N + 1;
+    for (int q = 0; q < kMaxN1 * kMaxN1; ++q) out.J[q] = 0.f;
+    for (int i = 0; i < N1; ++i) {
+        const double x = fine->xi[i];
+        int hit = -1;
+        for (int a = 0; a < M1; ++a)
+            if (std::fabs(x - mid->xi[a]) < 1e-14) hit = a;
+        for (int a = 0; a < M1; ++a) {
+            double v = 1.0;
+            if (hit >= 0) {
+                v = a == hit ? 1.0 : 0.0;
+            } else {
+                for (int b = 0; b < M1; ++b)
+                    if (b != a) v *= (x - mid->xi[b]) / (mid->xi[a] - mid->xi[b]);
+            }
+            out.J[i * M1 + a] = (float)v;
+        }
+    }
+}
+
+size_t schwarz_mid_work_bytes(const sem_schwarz *mid) {
+    return mid ? 2 * align_up(sizeof(float) * mid->m->nloc) : 0;
+}
+
+// The same elements and topology, a lower order, both Schwarz objects on
+// meshes of their own (else SEM_ERR_INVALID_ARG).
+int schwarz_mid_check(const sem_schwarz *sw, const sem_schwarz *mid) {
+    if (!sw || !mid) return fail(SEM_ERR_INVALID_ARG, "NULL Schwarz object");
+    const sem_mesh *f = sw->m, *m = mid->m;
+    if (m->N >= f->N || m->E != f->E || m->faces != f->faces)
+        return fail(SEM_ERR_INVALID_ARG, "the intermediate level needs a lower order on the same elements");
+    for (int a = 0; a < 3; ++a)
+        if (m->nel[a] != f->nel[a] || m->periodic[a] != f->periodic[a])
+            return fail(SEM_ERR_INVALID_ARG, "the intermediate level needs the same topology");
+    return SEM_OK;
+}
+
+// z += w P_M S_M P_M^T r (FP32; work: schwarz_mid_work_bytes; done: guard).
+int schwarz_mid_apply_add(const sem_schwarz *sw, const sem_schwarz *mid, double w, const float *r, float *z,
+                          void *work, const int *done, cudaStream_t st) {
+    const sem_mesh *f = sw->m, *m = mid->m;
+    MidJ J;
+    mid_interp(f, m, J);
+    float *rm = static_cast<float *>(work);
+    float *zm = reinterpret_cast<float *>(static_cast<char *>(work) + align_up(sizeof(float) * m->nloc));
+    int s = mid_launch(f->N, m->N, false, r, f->minv32, J, 0.f, f->E, f->num_sms, done, rm, st);
+    if (s != SEM_OK) return s;
+    s = gs_launch(m, rm, SEM_F32, kGsSumMask, st, done, 0);
+    if (s != SEM_OK) return s;
+    s = schwarz_apply_f32(mid, rm, zm, 0, 0.0, done, st);
+    if (s != SEM_OK) return s;
+    return mid_launch(f->N, m->N, true, zm, nullptr, J, (float)w, f->E, f->num_sms, done, z, st);
+}
+
 }  // namespace sem
 
 using namespace sem;
@@ -1369,6 +1570,24 @@ int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coars
     if (r == z) return fail(SEM_ERR_INVALID_ARG, "r and z must not overlap");
     if (coarse_iters < 0) return fail(SEM_ERR_INVALID_ARG, "coarse_iters < 0");
     return schwarz_apply_f32(sw, r, z, coarse_iters, coarse_tol, nullptr, as_stream(stream));
+}
+
+size_t sem_schwarz_mid_work_bytes(const sem_schwarz *mid) { return schwarz_mid_work_bytes(mid); }
+
+int sem_schwarz_apply3(const sem_schwarz *sw, const sem_schwarz *mid, double mid_weight, const float *r, float *z,
+                       int coarse_iters, double coarse_tol, void *d_work, size_t bytes, void *stream) {
+    if (!sw || !r || !z) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (r == z) return fail(SEM_ERR_INVALID_ARG, "r and z must not overlap");
+    if (coarse_iters < 0) return fail(SEM_ERR_INVALID_ARG, "coarse_iters < 0");
+    int s = schwarz_mid_check(sw, mid);
+    if (s != SEM_OK) return s;
+    if (!(mid_weight > 0.0)) return fail(SEM_ERR_INVALID_ARG, "mid_weight must be > 0");
+    if (!d_work || bytes < schwarz_mid_work_bytes(mid) || reinterpret_cast<uintptr_t>(d_work) % kAlign)
+        return fail(SEM_ERR_WORKSPACE, "work smaller than sem_schwarz_mid_work_bytes or misaligned");
+    cudaStream_t st = as_stream(stream);
+    s = schwarz_apply_f32(sw, r, z, coarse_iters, coarse_tol, nullptr, st);
+    if (s != SEM_OK) return s;
+    return schwarz_mid_apply_add(sw, mid, mid_weight, r, z, d_work, nullptr, st);
 }
 
 }  // extern "C"

@@ -86,7 +86,11 @@ def test_schwarz_and_solver_option_host_checks(lib):
     assert lib.sem_schwarz_apply(None, None, None, 3, 1e-2, None) == binding.SEM_ERR_INVALID_ARG
     assert lib.sem_schwarz_problems(None) == -1
     assert lib.sem_schwarz_destroy(None) == binding.SEM_OK
-    # the solver options carry the Schwarz handle, its coarse settings and the
-    # FP32-pair outer-residual switch at the end of the struct
+    # the solver options carry the Schwarz handle, its coarse settings, the
+    # double-float outer-residual switch and the intermediate multigrid level
+    # at the end of the struct
     names = [f[0] for f in binding.PcgOpts._fields_]
-    assert names[-4:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair"]
+    assert names[-6:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair", "schwarz_mid", "mid_weight"]
+    assert lib.sem_schwarz_mid_work_bytes(None) == 0
+    assert lib.sem_schwarz_apply3(None, None, 0.15, None, None, 3, 1e-2, None, 0, None) == \
+        binding.SEM_ERR_INVALID_ARG

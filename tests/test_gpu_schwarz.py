@@ -189,3 +189,97 @@ def test_full_size_pcg_schwarz_outer_pair_true_residual():
     r = b - om.apply(_host(xg))
     rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
     assert rel <= 1.05e-8, rel
+
+
+# ------------------------------------------------------------------ the intermediate multigrid level
+
+MID_CASES = [(inputs.channel(4, 7), 3), (inputs.deformed_cube(3, 5), 3), (SW_CASES[0], 2),
+             (inputs.BoxCase("n9", 9, (2, 3, 2), (0, 1, 0), inputs.ALL_FACES, perturb_amp=0.05, seed=5), 4)]
+MID_IDS = [f"{c.name}_M{M}" for c, M in MID_CASES]
+
+
+def _setup_mid(case, M):
+    V = case.vertices()
+    H = sw.HybridSchwarz(case.N, case.nel, case.periodic, case.faces, V, mid_order=M, mid_weight=0.15)
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gmid = binding.Mesh(M, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    return H, gm, binding.Schwarz(gm, gc), binding.Schwarz(gmid, gc), gc, gmid
+
+
+@pytest.mark.parametrize("case,M", MID_CASES, ids=MID_IDS)
+def test_schwarz_three_levels_match_oracle(case, M):
+    """z = S_N r + 0.15 P_M S_M P_M^T r + coarse (sem_schwarz_apply3) against
+    the oracle's three-level preconditioner, at the two-level bar; copies
+    bit-identical and Dirichlet nodes 0."""
+    import torch
+    H, gm, S, Smid, gc, gmid = _setup_mid(case, M)
+    r = _rhs(H)
+    rt = torch.from_numpy(r.astype(np.float32)).cuda()
+    z = _host(S.apply3(Smid, rt, mid_weight=0.15, coarse_iters=400, coarse_tol=1e-9)).astype(np.float64)
+    assert _rel(z, H.apply(r)) <= SW_TOL
+    one = np.zeros(H.m.nglob)
+    one[H.m.gid] = z
+    np.testing.assert_array_equal(z, one[H.m.gid])
+    assert np.all(z[H.m.apply_mask(np.ones(H.m.nloc)) == 0] == 0)
+
+
+@pytest.mark.parametrize("case,M", MID_CASES[:2], ids=MID_IDS[:2])
+def test_pcg_schwarz_three_levels_matches_oracle(case, M):
+    """The mixed solver with the three-level preconditioner: the FP64
+    oracle's solution to 1e-10 at tau = 1e-12, the true residual, and on the
+    channel fewer inner iterations than with two levels."""
+    H, gm, S, Smid, gc, gmid = _setup_mid(case, M)
+    om = H.m
+    b = om.scatter(case.rhs_global())
+    xo, _, _, sto = om.pcg(b, tol=1e-12, max_iter=20000)
+    kw = dict(tol=1e-12, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-4, schwarz=S,
+              coarse_iters=5, coarse_tol=1e-3)
+    xg, st = gm.pcg(_dev(b), schwarz_mid=Smid, mid_weight=0.15, **kw)
+    assert sto == 0 and st["status"] == 0, st
+    assert _rel(_host(xg), xo) <= 1e-10
+    r = b - om.apply(_host(xg))
+    assert np.sqrt(om.glsc3(r, r) / om.glsc3(b, b)) <= 1.5e-12
+    if case.name == "channel":
+        _, s2 = gm.pcg(_dev(b), **kw)
+        assert st["iters"] < s2["iters"], (st["iters"], s2["iters"])
+
+
+def test_full_size_pcg_schwarz_three_levels_true_residual():
+    """The 32^3 channel (N = 7) to 1e-8 with the three-level preconditioner
+    (intermediate order 3, weight 0.15): oracle-computed true residual, and
+    fewer inner iterations than with two levels."""
+    case = inputs.channel(32, 7)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gmid = binding.Mesh(3, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    S, Smid = binding.Schwarz(gm, gc), binding.Schwarz(gmid, gc)
+    om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
+    b = om.scatter(case.rhs_global())
+    kw = dict(tol=1e-8, max_iter=20000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, schwarz=S,
+              coarse_iters=3, coarse_tol=1e-2, check_every=8)
+    xg, st = gm.pcg(_dev(b), schwarz_mid=Smid, mid_weight=0.15, **kw)
+    assert st["status"] == 0
+    r = b - om.apply(_host(xg))
+    rel = np.sqrt(om.glsc3(r, r) / om.glsc3(b, b))
+    assert rel <= 1.05e-8, rel
+    _, s2 = gm.pcg(_dev(b), **kw)
+    assert st["iters"] < s2["iters"], (st["iters"], s2["iters"])
+
+
+def test_schwarz_three_levels_reject_mismatched_mid():
+    case = inputs.channel(3, 5)
+    V = case.vertices()
+    gm = binding.Mesh(case.N, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    gc = binding.Mesh(1, case.nel, case.periodic, case.faces, V, geom_f32=True)
+    S = binding.Schwarz(gm, gc)
+    other = inputs.channel(4, 3)
+    go = binding.Mesh(3, other.nel, other.periodic, other.faces, other.vertices(), geom_f32=True)
+    goc = binding.Mesh(1, other.nel, other.periodic, other.faces, other.vertices(), geom_f32=True)
+    bad = binding.Schwarz(go, goc)
+    b = _dev(np.zeros(gm.nloc))
+    for mid in (bad, S):  # other elements; same order
+        with pytest.raises(binding.SemError) as ei:
+            gm.pcg(b + 1.0, precision=binding.SEM_PCG_MIXED, schwarz=S, schwarz_mid=mid)
+        assert ei.value.status == binding.SEM_ERR_INVALID_ARG
