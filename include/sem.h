@@ -463,6 +463,17 @@ size_t sem_pcg_batched_scratch_bytes(const sem_mesh *const *meshes, int nsolve, 
 int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b,
                           double *const *x, const sem_pcg_opts *opts, sem_pcg_stats *stats,
                           void *d_scratch, size_t scratch_bytes, void *stream);
+/* The same batched solve with the hybrid Schwarz preconditioner (section
+ * 3.1's pressure preconditioner) per solve: schwarz[i] built on meshes[i]
+ * (sem_schwarz_create), coarse_iters / coarse_tol from opts (opts->schwarz
+ * stays NULL).  The inner FP32 solve of each refinement is flexible CG,
+ * restarted from the new FP64 residual at every refinement; the coarse CG
+ * runs as separate launches (no grid barrier: the solves' graph branches run
+ * concurrently).  Scratch as sem_pcg_batched_scratch_bytes.
+ * SEM_ERR_INVALID_ARG if schwarz[i] was built on another mesh. */
+int sem_pcg_solve_batched_schwarz(const sem_mesh *const *meshes, const struct sem_schwarz *const *schwarz,
+                                  int nsolve, const double *const *b, double *const *x, const sem_pcg_opts *opts,
+                                  sem_pcg_stats *stats, void *d_scratch, size_t scratch_bytes, void *stream);
 
 /* ---- Autotuner of the operator launch shape -------------------------------
  * Times the operator of `mesh` (precision dtype, plain or fused CG form) and

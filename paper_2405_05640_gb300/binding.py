@@ -129,6 +129,8 @@ _SIGS = {
     "sem_guess_target": ([_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int, _VP], ctypes.c_int),
     "sem_guess_apply": ([_VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, _VP, _VP], ctypes.c_int),
     "sem_pcg_batched_scratch_bytes": ([_VP, ctypes.c_int, ctypes.POINTER(PcgOpts)], ctypes.c_size_t),
+    "sem_pcg_solve_batched_schwarz": ([_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(PcgOpts), _VP, _VP,
+                                       ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_pcg_solve_batched": ([_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(PcgOpts), _VP, _VP, ctypes.c_size_t, _VP],
                               ctypes.c_int),
     "sem_autotune_scratch_bytes": ([_VP], ctypes.c_size_t),
@@ -643,9 +645,10 @@ def guess_apply(mesh, Y, p1, p2, p3, pscale, out):
                                 _ptr(out), _stream()), "sem_guess_apply")
 
 
-def pcg_solve_batched(meshes, bs, xs=None, scratch=None, raise_on_error=True, **kw):
+def pcg_solve_batched(meshes, bs, xs=None, scratch=None, raise_on_error=True, schwarz=None, **kw):
     """sem_pcg_solve_batched over lists of Mesh and device FP64 right-hand
-    sides; returns (xs, list of stats dicts)."""
+    sides (schwarz: a list of Schwarz objects, one per mesh ->
+    sem_pcg_solve_batched_schwarz); returns (xs, list of stats dicts)."""
     import torch
     n = len(meshes)
     opts = meshes[0].pcg_opts(precision=SEM_PCG_MIXED, **kw)
@@ -659,8 +662,13 @@ def pcg_solve_batched(meshes, bs, xs=None, scratch=None, raise_on_error=True, **
         scratch = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
     base = (scratch.data_ptr() + 255) // 256 * 256
     stats = (PcgStats * n)()
-    st = lib().sem_pcg_solve_batched(mh, n, bh, xh, ctypes.byref(opts), stats, _VP(base),
-                                     scratch.numel() - (base - scratch.data_ptr()), _stream())
+    nb = scratch.numel() - (base - scratch.data_ptr())
+    if schwarz is not None:
+        sh = (_VP * n)(*[w.handle.value for w in schwarz])
+        st = lib().sem_pcg_solve_batched_schwarz(mh, sh, n, bh, xh, ctypes.byref(opts), stats, _VP(base), nb,
+                                                 _stream())
+    else:
+        st = lib().sem_pcg_solve_batched(mh, n, bh, xh, ctypes.byref(opts), stats, _VP(base), nb, _stream())
     if raise_on_error and st != SEM_OK:
         raise SemError(st, "sem_pcg_solve_batched")
     return xs, [s.as_dict() for s in stats]

@@ -33,6 +33,7 @@ struct PcgScal {
     int iter, done, status, max_iter;
     int phase;          // batched solver: kBt* state of this solve
     int rounds;         // batched solver: rounds executed by this solve
+    int inner_done;     // batched solver: inner iterations of the inner solves already restarted
     unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
 };
 
@@ -277,9 +278,11 @@ void gll_host(int N, double *xi, double *rho);
 void deriv_host(int N, const double *x, double *D);
 
 // Hybrid Schwarz preconditioner (sem_schwarz.cu): z = M r in FP32; done
-// (optional device flag): set -> the kernels return at once.
+// (optional device flag): set -> the kernels return at once; coop: the
+// coarse CG as one cooperative kernel (grid barriers), else as separate
+// launches (for graphs whose branches run concurrently).
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      const int *done, cudaStream_t st);
+                      const int *done, cudaStream_t st, bool coop = true);
 // The (fine) mesh a Schwarz object was built on.
 const sem_mesh *schwarz_mesh(const sem_schwarz *sw);
 // Intermediate (order-M) level of the Schwarz multigrid (sem_schwarz.cu):

@@ -111,10 +111,25 @@ __device__ __forceinline__ void set_start_flags(PcgScal *s, double bb, double rr
 // In the mixed solver b is the FP64 outer residual and `scale` = 1/||b||
 // comes from the outer scalars (scale_src), so the inner system is O(1).
 template <typename T, typename TB>
+__device__ __forceinline__ bool pcg_init_body(const TB *__restrict__ b, const T *__restrict__ ax0,
+                                              const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
+                                              PcgWork<T> W, const PcgScal *__restrict__ scale_src, double tol,
+                                              int rel, int max_iter);
+
+template <typename T, typename TB>
 __global__ void __launch_bounds__(kPThreads)
     pcg_init_kernel(const TB *__restrict__ b, const T *__restrict__ ax0, const T *__restrict__ dinv,
                     const T *__restrict__ minv, int64_t n, PcgWork<T> W, const PcgScal *__restrict__ scale_src,
                     double tol, int rel, int max_iter) {
+    pcg_init_body<T, TB>(b, ax0, dinv, minv, n, W, scale_src, tol, rel, max_iter);
+}
+
+// Returns true on the thread that wrote the scalars.
+template <typename T, typename TB>
+__device__ __forceinline__ bool pcg_init_body(const TB *__restrict__ b, const T *__restrict__ ax0,
+                                              const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
+                                              PcgWork<T> W, const PcgScal *__restrict__ scale_src, double tol,
+                                              int rel, int max_iter) {
     const double sc = scale_src ? scale_src->scale : 1.0;
     double v[3] = {0.0, 0.0, 0.0};
     T f[3] = {T(0), T(0), T(0)};  // per-thread partials in T (FP32: no FP64 pipe per element)
@@ -149,7 +164,9 @@ __global__ void __launch_bounds__(kPThreads)
         s->max_iter = max_iter;
         s->beta = 0.0;
         set_start_flags(s, t[0], t[1]);
+        return true;
     }
+    return false;
 }
 
 // 16-byte vector of T (float4 / double2) as an array.
@@ -627,6 +644,7 @@ __global__ void __launch_bounds__(kPThreads)
     fpcg_dots_box_kernel(const float *__restrict__ r, const float *__restrict__ z, const float *__restrict__ wa,
                          BoxTopo B, PcgWork<float> W, int first) {
     if (W.scal->done) return;
+    if (first < 0) first = W.scal->iter == 0 ? 1 : 0;  // uniform
     constexpr int N1 = N + 1, NL = N1 * N1;
     float f0 = 0.f, f1 = 0.f;
     const int nx = B.nel[0], ny = B.nel[1];
@@ -1071,11 +1089,26 @@ __global__ void bt_round_end_kernel(PcgScal *s, const int *__restrict__ err, int
     cudaGraphSetConditional(h, fin ? 0u : 1u);
 }
 
+// Schwarz inner solve (flexible CG, restarted at every refinement): in
+// phase kBtReliable the inner FP32 iteration starts again from the new FP64
+// residual (the init of the single-solve path), then the solve iterates.
+__global__ void __launch_bounds__(kPThreads)
+    bt_restart_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
+                      int64_t n, PcgWork<float> W, PcgScal *so, double delta, int max_iter) {
+    if (so->phase != kBtReliable) return;  // uniform
+    const int before = W.scal->iter;  // read before the last block resets it
+    if (pcg_init_body<float, double>(r64, nullptr, dinv, minv, n, W, so, delta, 1, max_iter)) {
+        so->inner_done += before;
+        so->phase = W.scal->done && W.scal->status == SEM_ERR_NAN ? kBtFinished : kBtIterate;
+    }
+}
+
 struct BtSolve {
     const sem_mesh *m;
     const double *b;
     double *x;
     MixedWork M;
+    const sem_schwarz *sw;  // hybrid Schwarz inner preconditioner, or nullptr (Jacobi)
 };
 
 // One round of solve i on stream st: K FP32 iterations, then the guarded
@@ -1083,8 +1116,27 @@ struct BtSolve {
 static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
     const sem_mesh *m = S.m;
     const int64_t n = m->nloc;
+    const double itol = o->inner_tol > 0.0 ? o->inner_tol : 1e-2;
+    if (S.sw) {
+        // flexible CG with the hybrid Schwarz preconditioner (coarse CG as
+        // separate launches: the branches of the graph run concurrently)
+        CgFuse<float> cgs{S.M.z32, nullptr, S.M.in.p, S.M.in.scal, S.M.in.partial + 4 * kPBlocks};
+        const double ctol = o->coarse_tol > 0 ? o->coarse_tol : 1e-2;
+        for (int q = 0; q < K; ++q) {
+            int s = schwarz_apply_f32(S.sw, S.M.in.r, S.M.z32, o->coarse_iters, ctol, &S.M.in.scal->done, st, false);
+            if (s != SEM_OK) return s;
+            s = launch_fpcg_dots_box(m, S.M.in.r, S.M.z32, S.M.wa32, S.M.in, -1, st);
+            if (s != SEM_OK) return s;
+            s = ax_cg_launch_f32(m, cgs, S.M.in.w, st);
+            if (s != SEM_OK) return s;
+            s = gs_yz_launch(m, S.M.in.w, SEM_F32, st, &S.M.in.scal->done, 0);
+            if (s != SEM_OK) return s;
+            s = launch_update_box<float>(m, S.M.d32, m->dinv32, S.M.in, st, S.M.wa32);
+            if (s != SEM_OK) return s;
+        }
+    }
     CgFuse<float> cg{S.M.in.r, m->dinv32, S.M.in.p, S.M.in.scal, S.M.in.partial + 4 * kPBlocks};
-    for (int q = 0; q < K; ++q) {
+    for (int q = 0; q < (S.sw ? 0 : K); ++q) {
         int s = ax_cg_launch_f32(m, cg, S.M.in.w, st);
         if (s != SEM_OK) return s;
         // axis-by-axis gather-scatter: y and z passes (guarded by the solve's
@@ -1102,8 +1154,12 @@ static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
     if (s != SEM_OK) return s;
     bt_residual_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.b, S.M.w64, S.M.r64, m->minv, n, S.M.partial_out,
                                                        S.M.scal_out, S.M.in.scal);
-    bt_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
-                                                       o->inner_tol > 0.0 ? o->inner_tol : 1e-2);
+    if (S.sw)
+        bt_restart_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
+                                                          itol, o->max_iter);
+    else
+        bt_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
+                                                           itol);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
@@ -1263,9 +1319,14 @@ static int bt_capture_solve(BtSolve &S, const sem_pcg_opts *o, int K, int max_ro
 
 extern "C" {
 
-int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b, double *const *x,
-                          const sem_pcg_opts *o, sem_pcg_stats *stats, void *scratch, size_t scratch_bytes,
-                          void *stream) {
+}  // extern "C"
+
+namespace sem {
+
+// The batched solve; sws: per-solve hybrid Schwarz objects (nullptr: Jacobi).
+static int batched_impl(const sem_mesh *const *meshes, const sem_schwarz *const *sws, int nsolve,
+                        const double *const *b, double *const *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
+                        void *scratch, size_t scratch_bytes, void *stream) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!meshes || nsolve <= 0 || !b || !x || !o || !stats || !scratch)
         return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");
@@ -1293,6 +1354,7 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         S[i].b = b[i];
         S[i].x = x[i];
         S[i].M = carve_mixed(meshes[i], p);
+        S[i].sw = sws ? sws[i] : nullptr;
         p += align_up(pcg_scratch_mixed(meshes[i]));
     }
     const int K = o->check_every > 0 ? o->check_every : 16;
@@ -1354,7 +1416,9 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
     // per-solve statistics
     std::vector<unsigned long long> ht(nsolve + 1, 0ull);
     SEM_CUDA_CHECK(cudaMemcpy(ht.data(), d_t, sizeof(unsigned long long) * (nsolve + 1), cudaMemcpyDeviceToHost));
-    const int per_round = 3 * K + 7;  // kernels of one round body
+    // kernels of one round body (Schwarz: local solves, coarse CG launches,
+    // overlap sums, dots, operator, gather-scatter, update per iteration)
+    const int per_round = (sws ? (7 + 2 * o->coarse_iters) * K : 3 * K) + 7;
     int status = SEM_OK, derr = 0;
     for (int i = 0; i < nsolve; ++i) {
         PcgScal ho{}, hi{};
@@ -1365,7 +1429,7 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
         derr |= e;
         sem_pcg_stats &t = stats[i];
         t = sem_pcg_stats{};
-        t.iters = hi.iter;
+        t.iters = hi.iter + ho.inner_done;
         t.outer_iters = ho.iter > 0 ? ho.iter - 1 : 0;
         t.bnorm = std::sqrt(ho.bb);
         t.abs_res = std::sqrt(ho.rr);
@@ -1383,6 +1447,28 @@ int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const doubl
     if (status != SEM_OK) set_error(sem_status_string(status));
     (void)t0;
     return status;
+}
+
+}  // namespace sem
+
+extern "C" {
+
+int sem_pcg_solve_batched(const sem_mesh *const *meshes, int nsolve, const double *const *b, double *const *x,
+                          const sem_pcg_opts *o, sem_pcg_stats *stats, void *scratch, size_t scratch_bytes,
+                          void *stream) {
+    return batched_impl(meshes, nullptr, nsolve, b, x, o, stats, scratch, scratch_bytes, stream);
+}
+
+int sem_pcg_solve_batched_schwarz(const sem_mesh *const *meshes, const sem_schwarz *const *sws, int nsolve,
+                                  const double *const *b, double *const *x, const sem_pcg_opts *o,
+                                  sem_pcg_stats *stats, void *scratch, size_t scratch_bytes, void *stream) {
+    if (!meshes || !sws || nsolve <= 0) return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");
+    for (int i = 0; i < nsolve; ++i) {
+        if (!sws[i] || schwarz_mesh(sws[i]) != meshes[i])
+            return fail(SEM_ERR_INVALID_ARG, "Schwarz object i must be built on meshes[i]");
+    }
+    if (o && o->coarse_iters < 0) return fail(SEM_ERR_INVALID_ARG, "coarse_iters < 0");
+    return batched_impl(meshes, sws, nsolve, b, x, o, stats, scratch, scratch_bytes, stream);
 }
 
 }  // extern "C"

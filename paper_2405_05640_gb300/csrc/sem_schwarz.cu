@@ -899,6 +899,57 @@ __device__ __forceinline__ double cg_total(const double *partial) {
     return v;
 }
 
+// Per-vertex steps of the coarse CG, shared by the cooperative kernel and
+// the multi-kernel form.
+// Right-hand side of vertex v: the sum over the elements holding v (fixed
+// order) of their restrictions, 0 on Dirichlet vertices; also r = b,
+// x = p_old = 0.  Returns b (D^-1 b b of the first rz).
+__device__ __forceinline__ float coarse_rhs_vertex(const CoarseArgs &P, int v) {
+    const CoarseTopo &C = P.C;
+    const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
+    float b = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int ex = elem_coord(vx, s & 1, C.nel[0], C.per[0]);
+        const int ey = elem_coord(vy, (s >> 1) & 1, C.nel[1], C.per[1]);
+        const int ez = elem_coord(vz, s >> 2, C.nel[2], C.per[2]);
+        if (ex < 0 || ey < 0 || ez < 0) continue;
+        b += __ldg(P.rce + (ex + (int64_t)C.nel[0] * (ey + (int64_t)C.nel[1] * ez)) * 8 + s);
+    }
+    if (__ldg(P.cdinv + v) == 0.f) b = 0.f;
+    __stcg(P.r + v, b);
+    __stcg(P.x + v, 0.f);
+    __stcg(P.p0 + v, 0.f);
+    return b;
+}
+
+// p_new(v) = cdinv r + beta p_old at v and w(v) = (A_c p_new)(v), the
+// neighbours' p_new rebuilt from their r and p_old.  Returns p_new(v).
+__device__ __forceinline__ float coarse_apply_vertex(const CoarseArgs &P, int v, float beta, const float *pold,
+                                                     float &w) {
+    const CoarseTopo &C = P.C;
+    const int nvt = C.nvt;
+    const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
+    int nx[3], ny[3], nz[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        nx[o] = nb_coord(vx, o - 1, C.nv[0], C.per[0]);
+        ny[o] = nb_coord(vy, o - 1, C.nv[1], C.per[1]);
+        nz[o] = nb_coord(vz, o - 1, C.nv[2], C.per[2]);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+        const int a = nx[o % 3], b = ny[(o / 3) % 3], c = nz[o / 9];
+        if (a < 0 || b < 0 || c < 0) continue;
+        const int q = a + C.nv[0] * (b + C.nv[1] * c);
+        const float pq = fmaf(beta, __ldcg(pold + q), __ldg(P.cdinv + q) * __ldcg(P.r + q));
+        acc = fmaf(__ldg(P.sten + (int64_t)o * nvt + v), pq, acc);
+    }
+    w = acc;
+    return fmaf(beta, __ldcg(pold + v), __ldg(P.cdinv + v) * __ldcg(P.r + v));
+}
+
 // The coarse solve A_c x = b, b assembled from the element restrictions,
 // x0 = 0, up to `iters` Jacobi-CG iterations or rz <= tol2 rz0.  Per
 // iteration: (1) p_new = cdinv r + beta p_old for the owned vertices and
@@ -914,22 +965,8 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
     // b = sum over the elements holding v (fixed order) of their restriction
     double part = 0.0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvt; v += stride) {
-        const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
-        float b = 0.f;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int ex = elem_coord(vx, s & 1, C.nel[0], C.per[0]);
-            const int ey = elem_coord(vy, (s >> 1) & 1, C.nel[1], C.per[1]);
-            const int ez = elem_coord(vz, s >> 2, C.nel[2], C.per[2]);
-            if (ex < 0 || ey < 0 || ez < 0) continue;
-            b += __ldg(P.rce + (ex + (int64_t)C.nel[0] * (ey + (int64_t)C.nel[1] * ez)) * 8 + s);
-        }
-        const float di = __ldg(P.cdinv + v);
-        if (di == 0.f) b = 0.f;
-        __stcg(P.r + v, b);
-        __stcg(P.x + v, 0.f);
-        __stcg(P.p0 + v, 0.f);
-        part += (double)b * (double)(di * b);
+        const float b = coarse_rhs_vertex(P, v);
+        part += (double)b * (double)(__ldg(P.cdinv + v) * b);
     }
     cg_block_partial(part, P.partial);
     if (!grid_barrier_bounded(P.bar, ++nbar * gridDim.x, P.err)) return;
@@ -941,24 +978,8 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
         if (!(rz > P.tol2 * rz0)) break;
         part = 0.0;
         for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvt; v += stride) {
-            const int vx = v % C.nv[0], vy = (v / C.nv[0]) % C.nv[1], vz = v / (C.nv[0] * C.nv[1]);
-            int nx[3], ny[3], nz[3];
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                nx[o] = nb_coord(vx, o - 1, C.nv[0], C.per[0]);
-                ny[o] = nb_coord(vy, o - 1, C.nv[1], C.per[1]);
-                nz[o] = nb_coord(vz, o - 1, C.nv[2], C.per[2]);
-            }
-            float w = 0.f;
-#pragma unroll
-            for (int o = 0; o < 27; ++o) {
-                const int a = nx[o % 3], b = ny[(o / 3) % 3], c = nz[o / 9];
-                if (a < 0 || b < 0 || c < 0) continue;
-                const int q = a + C.nv[0] * (b + C.nv[1] * c);
-                const float pq = fmaf(beta, __ldcg(pold + q), __ldg(P.cdinv + q) * __ldcg(P.r + q));
-                w = fmaf(__ldg(P.sten + (int64_t)o * nvt + v), pq, w);
-            }
-            const float pv = fmaf(beta, __ldcg(pold + v), __ldg(P.cdinv + v) * __ldcg(P.r + v));
+            float w;
+            const float pv = coarse_apply_vertex(P, v, beta, pold, w);
             __stcg(pnew + v, pv);
             __stcg(P.w + v, w);
             part += (double)pv * (double)w;
@@ -983,6 +1004,96 @@ __global__ void __launch_bounds__(kCgThreads) coarse_cg_kernel(CoarseArgs P) {
         float *t = pold;
         pold = pnew;
         pnew = t;
+    }
+}
+
+// ---- the coarse CG as separate launches (no grid barrier)
+//
+// The same iteration in three kernels -- right-hand side and rz0, then per
+// iteration p_new and A_c p_new with <p, A_c p>, then the x and r updates
+// with <r, D^-1 r> -- each closed by a deterministic last-block reduction
+// (block partials, summed in block order by the last block to arrive).  For
+// graphs whose branches run concurrently: a cooperative grid must not wait
+// on CTAs that other branches' kernels keep from being scheduled.  An early
+// stop (rz <= tol2 rz0) turns the remaining launches into no-ops.
+struct CoarseScal {
+    unsigned bar;   // grid barrier counter of the cooperative form
+    unsigned cnt;   // arrival counter of the last-block reductions
+    int stop;       // 1: the iteration is over
+    int pad;
+    double rz, rz0, pw;
+    float alpha, beta;
+};
+
+// Block partial of v; in the last block to arrive, tot = the sum of all
+// partials in block order (every thread) and the counter is reset.
+__device__ __forceinline__ bool coarse_last_block(double v, double *partial, unsigned *cnt, double &tot) {
+    __shared__ int last;
+    cg_block_partial(v, partial);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    tot = cg_total(partial);
+    if (threadIdx.x == 0) *cnt = 0u;
+    return true;
+}
+
+__global__ void __launch_bounds__(kCgThreads) coarse_mk_init_kernel(CoarseArgs P, CoarseScal *S) {
+    if (P.done && *P.done) return;
+    double part = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.C.nvt; v += gridDim.x * blockDim.x) {
+        const float b = coarse_rhs_vertex(P, v);
+        part += (double)b * (double)(__ldg(P.cdinv + v) * b);
+    }
+    double tot;
+    if (coarse_last_block(part, P.partial, &S->cnt, tot) && threadIdx.x == 0) {
+        S->rz = tot;
+        S->rz0 = tot;
+        S->beta = 0.f;
+        S->stop = (P.iters > 0 && tot > P.tol2 * tot) ? 0 : 1;
+    }
+}
+
+__global__ void __launch_bounds__(kCgThreads)
+    coarse_mk_pw_kernel(CoarseArgs P, CoarseScal *S, const float *pold, float *pnew) {
+    if ((P.done && *P.done) || S->stop) return;
+    const float beta = S->beta;
+    double part = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.C.nvt; v += gridDim.x * blockDim.x) {
+        float w;
+        const float pv = coarse_apply_vertex(P, v, beta, pold, w);
+        __stcg(pnew + v, pv);
+        __stcg(P.w + v, w);
+        part += (double)pv * (double)w;
+    }
+    double tot;
+    if (coarse_last_block(part, P.partial, &S->cnt, tot) && threadIdx.x == 0) {
+        S->pw = tot;
+        S->alpha = tot != 0.0 ? (float)(S->rz / tot) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kCgThreads) coarse_mk_xr_kernel(CoarseArgs P, CoarseScal *S, const float *pnew) {
+    if ((P.done && *P.done) || S->stop) return;
+    const float alpha = S->alpha;
+    double part = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.C.nvt; v += gridDim.x * blockDim.x) {
+        const float pv = __ldcg(pnew + v), wv = __ldcg(P.w + v);
+        __stcg(P.x + v, fmaf(alpha, pv, __ldcg(P.x + v)));
+        const float rv = fmaf(-alpha, wv, __ldcg(P.r + v));
+        __stcg(P.r + v, rv);
+        part += (double)rv * (double)(__ldg(P.cdinv + v) * rv);
+    }
+    double tot;
+    if (coarse_last_block(part, P.partial + kCgMaxGrid, &S->cnt, tot) && threadIdx.x == 0) {
+        const double rz = S->rz;
+        S->beta = rz != 0.0 ? (float)(tot / rz) : 0.f;
+        S->rz = tot;
+        S->stop = tot > P.tol2 * S->rz0 ? 0 : 1;
     }
 }
 
@@ -1067,7 +1178,7 @@ static size_t sw_layout(const sem_mesh *m, size_t *off) {
     off[5] = take(sizeof(float) * 27 * nv);
     for (int q = 6; q < 12; ++q) off[q] = take(sizeof(float) * nv);
     off[12] = take(sizeof(double) * 2 * kCgMaxGrid);
-    off[13] = take(sizeof(unsigned) * 4);
+    off[13] = take(sizeof(CoarseScal));
     off[14] = take(sizeof(float) * 2 * kMaxN1);
     off[15] = take(sizeof(short) * 3 * 32 * 5);  // LPT <= 5 (N <= 9)
     return o;
@@ -1086,7 +1197,7 @@ static SwArgs sw_args(const sem_mesh *m) {
 
 template <int N>
 static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      const int *done, cudaStream_t st) {
+                      const int *done, cudaStream_t st, bool coop) {
     using S = SwShape<N>;
     const sem_mesh *m = sw->m;
     const SwArgs A = sw_args(m);
@@ -1111,7 +1222,7 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
     SEM_CUDA_CHECK(cudaGetLastError());
     const CoarseTopo C = coarse_topo(m);
     if (coarse) {
-        SEM_CUDA_CHECK(cudaMemsetAsync(sw->bar, 0, sizeof(unsigned), st));
+        SEM_CUDA_CHECK(cudaMemsetAsync(sw->bar, 0, sizeof(CoarseScal), st));
         CoarseArgs P;
         P.sten = sw->sten;
         P.cdinv = sw->cdinv;
@@ -1137,9 +1248,23 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
         int gc = (C.nvt + kCgThreads - 1) / kCgThreads;
         gc = std::min(gc, std::min(m->num_sms * std::max(cg_per_sm, 1), kCgMaxGrid));
         gc = std::min(gc, m->num_sms);
-        void *args[] = {&P};
-        SEM_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(coarse_cg_kernel), dim3(gc),
-                                                   dim3(kCgThreads), args, 0, st));
+        if (coop) {
+            void *args[] = {&P};
+            SEM_CUDA_CHECK(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(coarse_cg_kernel), dim3(gc),
+                                                       dim3(kCgThreads), args, 0, st));
+        } else {
+            CoarseScal *S = reinterpret_cast<CoarseScal *>(sw->bar);
+            int gm = (C.nvt + kCgThreads - 1) / kCgThreads;
+            gm = std::min(gm, kCgMaxGrid);
+            coarse_mk_init_kernel<<<gm, kCgThreads, 0, st>>>(P, S);
+            float *pold = sw->pc0, *pnew = sw->pc1;
+            for (int it = 0; it < coarse_iters; ++it) {
+                coarse_mk_pw_kernel<<<gm, kCgThreads, 0, st>>>(P, S, pold, pnew);
+                coarse_mk_xr_kernel<<<gm, kCgThreads, 0, st>>>(P, S, pnew);
+                std::swap(pold, pnew);
+            }
+            SEM_CUDA_CHECK(cudaGetLastError());
+        }
     }
     int64_t gp = (m->E + sum_epb<N>() - 1) / sum_epb<N>();
     if (gp > (int64_t)m->num_sms * 16) gp = (int64_t)m->num_sms * 16;
@@ -1149,10 +1274,10 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
 }
 
 int schwarz_apply_f32(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
-                      const int *done, cudaStream_t st) {
+                      const int *done, cudaStream_t st, bool coop) {
     switch (sw->N) {
 #define SEM_SW_CASE(n) \
-    case n: return sw_apply_n<n>(sw, r, z, coarse_iters, coarse_tol, done, st);
+    case n: return sw_apply_n<n>(sw, r, z, coarse_iters, coarse_tol, done, st, coop);
         SEM_SW_CASE(2) SEM_SW_CASE(3) SEM_SW_CASE(4) SEM_SW_CASE(5) SEM_SW_CASE(6) SEM_SW_CASE(7)
         SEM_SW_CASE(8) SEM_SW_CASE(9)
 #undef SEM_SW_CASE
