@@ -754,19 +754,21 @@ def run_op_gemm(args):
         A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16)
         B = torch.randn((N, K), generator=g, device="cuda").to(torch.bfloat16)
         bias = torch.zeros(N, dtype=torch.float32, device="cuda")
+        # the weight gradients (small outputs, K = the rows) with split-K, as the network runs them
+        work = binding.gemm_splitk_work(M, N, K) if name.startswith("bwd dW") else None
         for _ in range(args.warmup):
-            binding.gemm_bf16(A, B, bias, act, err=err)
+            binding.gemm_bf16(A, B, bias, act, err=err, work=work)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(s)
         for _ in range(args.steps):
-            binding.gemm_bf16(A, B, bias, act, err=err)
+            binding.gemm_bf16(A, B, bias, act, err=err, work=work)
         e1.record(s)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
         rows.append({"gemm": name, "M": M, "N": N, "K": K, "ms": round(ms, 4), "tflops": round(tf, 1),
-                     "frac": round(tf / peak, 4)})
+                     "frac": round(tf / peak, 4), "split_k": work is not None})
     assert int(err.item()) == 0, "a bounded wait of the GEMM gave up"
     fwd = [r for r in rows if r["gemm"].startswith("fwd")]
     bwd = [r for r in rows if r["gemm"].startswith("bwd")]

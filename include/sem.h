@@ -391,6 +391,19 @@ int sem_ns_kinetic_energy(const sem_ns *ns, double *energy, void *d_scratch, siz
  * guess of the pressure solve uses it. */
 int sem_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *C32,
                   void *C16, int ldc, int *d_err, void *stream);
+/* The same product with split-K for small outputs: when the 128 x BN output
+ * tiles alone fill fewer CTAs than the GPU has SMs, K is cut into up to 16
+ * slices (at least 8 K-blocks of 64 each), each slice's FP32 tile is written
+ * to d_work, and a second kernel sums the slices in slice order
+ * (deterministic), adds the bias and applies the activation.  d_work:
+ * device, 16-byte aligned, work_bytes >= sem_gemm_bf16_splitk_work_bytes
+ * for the full 16 slices (fewer fit a smaller work space); NULL: no split.
+ * Used for the network's weight gradients (M x N <= 256 x 2048, K = the
+ * rows). */
+size_t sem_gemm_bf16_splitk_work_bytes(int M, int N, int K);
+int sem_gemm_bf16_splitk(const void *A, const void *B, int M, int N, int K, const float *bias, int act,
+                         float *C32, void *C16, int ldc, void *d_work, size_t work_bytes, int *d_err,
+                         void *stream);
 
 /* ---- Element-local network for the learned initial guess ----------------
  * Not from the paper.  Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 per row

@@ -103,6 +103,9 @@ _SIGS = {
                             ctypes.c_size_t, _VP], ctypes.c_int),
     "sem_mesh_check_device_error": ([_VP, ctypes.POINTER(ctypes.c_int), _VP], ctypes.c_int),
     "sem_wait_selftest": ([_VP, ctypes.c_int, ctypes.c_double, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "sem_gemm_bf16_splitk_work_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "sem_gemm_bf16_splitk": ([_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                              ctypes.c_int, _VP, ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "sem_gemm_bf16": ([_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                        ctypes.c_int, _VP, _VP], ctypes.c_int),
     "sem_mlp_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
@@ -531,9 +534,10 @@ class NSState:
         return e.value
 
 
-def gemm_bf16(A, B, bias=None, act=0, out32=True, out16=False, err=None):
+def gemm_bf16(A, B, bias=None, act=0, out32=True, out16=False, err=None, work=None):
     """sem_gemm_bf16: act(A @ B^T + bias) with A [M, K], B [N, K] bfloat16
-    CUDA tensors; returns (C32 or None, C16 or None)."""
+    CUDA tensors; work (a uint8 CUDA tensor): split-K work space
+    (sem_gemm_bf16_splitk); returns (C32 or None, C16 or None)."""
     import torch
     M, K = A.shape
     N = B.shape[0]
@@ -541,10 +545,21 @@ def gemm_bf16(A, B, bias=None, act=0, out32=True, out16=False, err=None):
     c16 = torch.empty((M, N), dtype=torch.bfloat16, device="cuda") if out16 else None
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    check(lib().sem_gemm_bf16(_ptr(A), _ptr(B), M, N, K, _ptr(bias) if bias is not None else None, int(act),
-                              _ptr(c32) if c32 is not None else None, _ptr(c16) if c16 is not None else None,
-                              N, _ptr(err), _stream()), "sem_gemm_bf16")
+    args = (_ptr(A), _ptr(B), M, N, K, _ptr(bias) if bias is not None else None, int(act),
+            _ptr(c32) if c32 is not None else None, _ptr(c16) if c16 is not None else None, N)
+    if work is not None:
+        base = (work.data_ptr() + 255) // 256 * 256
+        nb = work.numel() - (base - work.data_ptr())
+        check(lib().sem_gemm_bf16_splitk(*args, _VP(base), nb, _ptr(err), _stream()), "sem_gemm_bf16_splitk")
+    else:
+        check(lib().sem_gemm_bf16(*args, _ptr(err), _stream()), "sem_gemm_bf16")
     return c32, c16
+
+
+def gemm_splitk_work(M, N, K):
+    """A work space for sem_gemm_bf16_splitk (16 slices)."""
+    import torch
+    return torch.empty(lib().sem_gemm_bf16_splitk_work_bytes(M, N, K) + 256, dtype=torch.uint8, device="cuda")
 
 
 class MLP:

@@ -120,6 +120,8 @@ struct GemmEpi {
     float *c32;         // [M][ldc] or null
     __nv_bfloat16 *c16; // [M][ldc] or null
     int ldc;
+    float *ws;          // split-K: [splits][M][N] FP32 partial tiles (no bias, no activation), or null
+    int M, N;
 };
 
 template <int BN>
@@ -140,7 +142,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * BN;
-    const int KT = K / kGemmBK;
+    // split-K: CTA z takes the K-blocks [kb0, kb0 + KT) of its slice
+    const int KTall = K / kGemmBK, per = (KTall + gridDim.z - 1) / gridDim.z;
+    const int kb0 = blockIdx.z * per;
+    const int KT = KTall - kb0 < per ? KTall - kb0 : per;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGemmStages; ++s) {
@@ -171,8 +176,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             mbar_arrive_expect_tx(&full[s], kTileABytes + kTileBBytes);
-            tma_load_2d(sA + s * kTileABytes, &tmA, kt * kGemmBK, m0, &full[s]);
-            tma_load_2d(sB + s * kTileBBytes, &tmB, kt * kGemmBK, n0, &full[s]);
+            tma_load_2d(sA + s * kTileABytes, &tmA, (kb0 + kt) * kGemmBK, m0, &full[s]);
+            tma_load_2d(sB + s * kTileBBytes, &tmB, (kb0 + kt) * kGemmBK, n0, &full[s]);
         }
         if (!ok) {
             // drain the stages still being filled (bounded)
@@ -213,6 +218,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             float v[32];
             tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
             const int col = n0 + c;
+            if (epi.ws) {  // split-K partial: raw FP32 tile
+                float4 *dst = reinterpret_cast<float4 *>(epi.ws + ((size_t)blockIdx.z * epi.M + row) * epi.N + col);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 float x = v[q];
@@ -235,6 +246,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, (uint32_t)BN);
+}
+
+// Split-K reduction: C = act(sum over the slices, in slice order, + bias).
+__global__ void gemm_splitk_reduce_kernel(const float *__restrict__ ws, int splits, GemmEpi epi) {
+    const int64_t MN = (int64_t)epi.M * epi.N;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < MN; q += (int64_t)gridDim.x * blockDim.x) {
+        float x = 0.f;
+        for (int s = 0; s < splits; ++s) x += ws[s * MN + q];
+        const int row = (int)(q / epi.N), col = (int)(q - (int64_t)row * epi.N);
+        if (epi.bias) x += epi.bias[col];
+        if (epi.act == 1) x = fmaxf(x, 0.0f);
+        if (epi.c32) epi.c32[(size_t)row * epi.ldc + col] = x;
+        if (epi.c16) epi.c16[(size_t)row * epi.ldc + col] = __float2bfloat16_rn(x);
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -273,8 +298,26 @@ static int make_tmap(CUtensorMap *tm, const void *ptr, int rows, int cols, int b
     return SEM_OK;
 }
 
+// Split count for a workspace of ws_floats: slices of K when the output
+// tiles alone fill less than the SMs (at least 8 K-blocks per slice, at most
+// 16 slices), else 1.
+int gemm_splits(int M, int N, int K, size_t ws_floats, int num_sms) {
+    const int BN = (N % 256 == 0) ? 256 : 128;
+    const int tiles = (M / kGemmBM) * (N / BN);
+    const int KT = K / kGemmBK;
+    int s = (num_sms + tiles - 1) / tiles;
+    s = s < 16 ? s : 16;
+    s = s < KT / 8 ? s : KT / 8;
+    while (s > 1 && (size_t)s * M * N > ws_floats) --s;
+    if (s <= 1) return 1;
+    // every slice non-empty: the kernel gives slice z the K-blocks from
+    // z * ceil(KT / s), so s is the number of slices of that length
+    const int per = (KT + s - 1) / s;
+    return (KT + per - 1) / per;
+}
+
 int gemm_tn_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *c32,
-                 void *c16, int ldc, int *d_err, cudaStream_t st) {
+                 void *c16, int ldc, int *d_err, cudaStream_t st, float *ws, size_t ws_floats) {
     if (!A || !B || (!c32 && !c16) || !d_err) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (M <= 0 || N <= 0 || K <= 0 || M % kGemmBM || K % kGemmBK || N % 128)
         return fail(SEM_ERR_INVALID_ARG, "GEMM needs M % 128 == 0, N % 128 == 0, K % 64 == 0");
@@ -287,8 +330,12 @@ int gemm_tn_bf16(const void *A, const void *B, int M, int N, int K, const float 
     if (s != SEM_OK) return s;
     s = make_tmap(&tb, B, N, K, BN);
     if (s != SEM_OK) return s;
-    GemmEpi epi{bias, act, c32, static_cast<__nv_bfloat16 *>(c16), ldc};
-    dim3 grid(N / BN, M / kGemmBM);
+    int dev = 0, sms = 148;
+    SEM_CUDA_CHECK(cudaGetDevice(&dev));
+    SEM_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int splits = ws ? gemm_splits(M, N, K, ws_floats, sms) : 1;
+    GemmEpi epi{bias, act, c32, static_cast<__nv_bfloat16 *>(c16), ldc, splits > 1 ? ws : nullptr, M, N};
+    dim3 grid(N / BN, M / kGemmBM, splits);
     if (BN == 256) {
         constexpr int smem = gemm_smem_bytes<256>();
         SEM_CUDA_CHECK(cudaFuncSetAttribute(gemm_tn_bf16_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -299,6 +346,12 @@ int gemm_tn_bf16(const void *A, const void *B, int M, int N, int K, const float 
         gemm_tn_bf16_kernel<128><<<grid, kGemmThreads, smem, st>>>(ta, tb, K, epi, d_err);
     }
     SEM_CUDA_CHECK(cudaGetLastError());
+    if (splits > 1) {
+        const int64_t MN = (int64_t)M * N;
+        const int g = (int)((MN + 255) / 256 < (int64_t)sms * 8 ? (MN + 255) / 256 : (int64_t)sms * 8);
+        gemm_splitk_reduce_kernel<<<g, 256, 0, st>>>(ws, splits, epi);
+        SEM_CUDA_CHECK(cudaGetLastError());
+    }
     return SEM_OK;
 }
 
@@ -310,7 +363,20 @@ extern "C" {
 
 int sem_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *C32,
                   void *C16, int ldc, int *d_err, void *stream) {
-    return gemm_tn_bf16(A, B, M, N, K, bias, act, C32, C16, ldc, d_err, as_stream(stream));
+    return gemm_tn_bf16(A, B, M, N, K, bias, act, C32, C16, ldc, d_err, as_stream(stream), nullptr, 0);
+}
+
+size_t sem_gemm_bf16_splitk_work_bytes(int M, int N, int K) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    return sizeof(float) * 16 * (size_t)M * N;
+}
+
+int sem_gemm_bf16_splitk(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *C32,
+                         void *C16, int ldc, void *d_work, size_t work_bytes, int *d_err, void *stream) {
+    if (d_work && reinterpret_cast<uintptr_t>(d_work) % 16)
+        return fail(SEM_ERR_WORKSPACE, "split-K work space must be 16-byte aligned");
+    return gemm_tn_bf16(A, B, M, N, K, bias, act, C32, C16, ldc, d_err, as_stream(stream),
+                        static_cast<float *>(d_work), d_work ? work_bytes / sizeof(float) : 0);
 }
 
 }  // extern "C"

@@ -25,7 +25,7 @@
 
 namespace sem {
 int gemm_tn_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int act, float *c32,
-                 void *c16, int ldc, int *d_err, cudaStream_t st);
+                 void *c16, int ldc, int *d_err, cudaStream_t st, float *ws, size_t ws_floats);
 }
 
 struct sem_mlp {
@@ -36,6 +36,8 @@ struct sem_mlp {
     __nv_bfloat16 *XT, *H1, *H1T, *H2, *H2T, *dY, *dYT, *dA2, *dA2T, *dA1, *dA1T;
     float *Y, *dH2, *dH1;
     float *part;
+    float *wsk;          // split-K partials of the weight-gradient GEMMs
+    size_t wsk_floats;
     int *err;
     int t;
 };
@@ -166,6 +168,15 @@ static int refresh_bf16(sem_mlp *n, cudaStream_t st) {
     return SEM_OK;
 }
 
+// Split-K work space of the weight-gradient GEMMs (M x N = O x H, H x H,
+// H x I; K = the rows): up to 16 slices of the largest.
+static size_t splitk_floats(int I, int H, int O) {
+    size_t mn = (size_t)O * H;
+    if ((size_t)H * H > mn) mn = (size_t)H * H;
+    if ((size_t)H * I > mn) mn = (size_t)H * I;
+    return 16 * mn;
+}
+
 static size_t mlp_bytes(int I, int H, int O, int R, size_t *P_out) {
     const size_t P = (size_t)H * I + H + (size_t)H * H + H + (size_t)O * H + O;
     if (P_out) *P_out = P;
@@ -176,6 +187,7 @@ static size_t mlp_bytes(int I, int H, int O, int R, size_t *P_out) {
     b += 2 * align_up(2 * (size_t)R * O);                                 // dY dYT
     b += align_up(4 * (size_t)R * O) + 2 * align_up(4 * (size_t)R * H);  // Y dH2 dH1
     b += align_up(4 * ((size_t)kColChunks * (I > O ? (I > H ? I : H) : (O > H ? O : H)) + 4096));
+    b += align_up(4 * splitk_floats(I, H, O));
     b += align_up(64);
     return b;
 }
@@ -238,6 +250,8 @@ int sem_mlp_create(int n_in, int n_hidden, int n_out, int max_rows, void *ws, si
     n->dH1 = reinterpret_cast<float *>(take(4 * (size_t)n->R * n->H));
     const int wide = n->I > n->O ? (n->I > n->H ? n->I : n->H) : (n->O > n->H ? n->O : n->H);
     n->part = reinterpret_cast<float *>(take(4 * ((size_t)kColChunks * wide + 4096)));
+    n->wsk_floats = splitk_floats(n_in, n_hidden, n_out);
+    n->wsk = reinterpret_cast<float *>(take(4 * n->wsk_floats));
     n->err = reinterpret_cast<int *>(take(64));
     n->t = 0;
     cudaError_t e = cudaMemset(ws, 0, need);
@@ -286,9 +300,9 @@ int sem_mlp_get_grads(const sem_mlp *n, float *host, void *stream) {
 }
 
 static int fwd(sem_mlp *n, const void *X, int rows, cudaStream_t st) {
-    int s = gemm_tn_bf16(X, n->W1h, rows, n->H, n->I, n->p + n->ob1, 1, nullptr, n->H1, n->H, n->err, st);
-    if (s == SEM_OK) s = gemm_tn_bf16(n->H1, n->W2h, rows, n->H, n->H, n->p + n->ob2, 1, nullptr, n->H2, n->H, n->err, st);
-    if (s == SEM_OK) s = gemm_tn_bf16(n->H2, n->W3h, rows, n->O, n->H, n->p + n->ob3, 0, n->Y, nullptr, n->O, n->err, st);
+    int s = gemm_tn_bf16(X, n->W1h, rows, n->H, n->I, n->p + n->ob1, 1, nullptr, n->H1, n->H, n->err, st, nullptr, 0);
+    if (s == SEM_OK) s = gemm_tn_bf16(n->H1, n->W2h, rows, n->H, n->H, n->p + n->ob2, 1, nullptr, n->H2, n->H, n->err, st, nullptr, 0);
+    if (s == SEM_OK) s = gemm_tn_bf16(n->H2, n->W3h, rows, n->O, n->H, n->p + n->ob3, 0, n->Y, nullptr, n->O, n->err, st, nullptr, 0);
     return s;
 }
 
@@ -319,25 +333,25 @@ int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_r
     // layer 3
     transpose<bf16, bf16>(n->dY, n->dYT, R, O, st);
     transpose<bf16, bf16>(n->H2, n->H2T, R, H, st);
-    s = gemm_tn_bf16(n->dYT, n->H2T, O, H, R, nullptr, 0, n->g + n->oW3, nullptr, H, n->err, st);
+    s = gemm_tn_bf16(n->dYT, n->H2T, O, H, R, nullptr, 0, n->g + n->oW3, nullptr, H, n->err, st, n->wsk, n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dY, R, O, n->part, n->g + n->ob3, st);
-    s = gemm_tn_bf16(n->dY, n->W3t, R, H, O, nullptr, 0, n->dH2, nullptr, H, n->err, st);
+    s = gemm_tn_bf16(n->dY, n->W3t, R, H, O, nullptr, 0, n->dH2, nullptr, H, n->err, st, nullptr, 0);
     if (s != SEM_OK) return s;
     relu_mask_kernel<<<gridn((int64_t)R * H), 256, 0, st>>>(n->dH2, n->H2, n->dA2, (int64_t)R * H);
     // layer 2
     transpose<bf16, bf16>(n->dA2, n->dA2T, R, H, st);
     transpose<bf16, bf16>(n->H1, n->H1T, R, H, st);
-    s = gemm_tn_bf16(n->dA2T, n->H1T, H, H, R, nullptr, 0, n->g + n->oW2, nullptr, H, n->err, st);
+    s = gemm_tn_bf16(n->dA2T, n->H1T, H, H, R, nullptr, 0, n->g + n->oW2, nullptr, H, n->err, st, n->wsk, n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dA2, R, H, n->part, n->g + n->ob2, st);
-    s = gemm_tn_bf16(n->dA2, n->W2t, R, H, H, nullptr, 0, n->dH1, nullptr, H, n->err, st);
+    s = gemm_tn_bf16(n->dA2, n->W2t, R, H, H, nullptr, 0, n->dH1, nullptr, H, n->err, st, nullptr, 0);
     if (s != SEM_OK) return s;
     relu_mask_kernel<<<gridn((int64_t)R * H), 256, 0, st>>>(n->dH1, n->H1, n->dA1, (int64_t)R * H);
     // layer 1
     transpose<bf16, bf16>(n->dA1, n->dA1T, R, H, st);
     transpose<bf16, bf16>(static_cast<const bf16 *>(X), n->XT, R, I, st);
-    s = gemm_tn_bf16(n->dA1T, n->XT, H, I, R, nullptr, 0, n->g + n->oW1, nullptr, I, n->err, st);
+    s = gemm_tn_bf16(n->dA1T, n->XT, H, I, R, nullptr, 0, n->g + n->oW1, nullptr, I, n->err, st, n->wsk, n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dA1, R, H, n->part, n->g + n->ob1, st);
     SEM_CUDA_CHECK(cudaGetLastError());

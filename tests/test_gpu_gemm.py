@@ -9,14 +9,15 @@ from paper_2405_05640_gb300 import binding
 pytestmark = pytest.mark.gpu
 
 
-def _case(M, N, K, seed, bias, act):
+def _case(M, N, K, seed, bias, act, splitk=False):
     import torch
     g = torch.Generator().manual_seed(seed)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, generator=g).to(torch.bfloat16)
     bb = torch.randn(N, generator=g).float() if bias else None
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    c32, c16 = binding.gemm_bf16(A.cuda(), B.cuda(), bb.cuda() if bias else None, act, True, True, err)
+    work = binding.gemm_splitk_work(M, N, K) if splitk else None
+    c32, c16 = binding.gemm_bf16(A.cuda(), B.cuda(), bb.cuda() if bias else None, act, True, True, err, work=work)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     a = A.double().numpy()
@@ -31,6 +32,7 @@ def _case(M, N, K, seed, bias, act):
     assert np.all(np.abs(got - ref) <= bound + 1e-6 * np.abs(ref)), np.max(np.abs(got - ref) / bound)
     # the BF16 output is the FP32 result rounded to BF16
     np.testing.assert_array_equal(c16.cpu().float().numpy(), c32.cpu().to(torch.bfloat16).float().numpy())
+    return c32
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 256, 128), (256, 256, 2048), (384, 512, 256),
@@ -50,3 +52,14 @@ def test_gemm_rejects_ragged_shapes():
     with pytest.raises(binding.SemError) as ei:
         binding.gemm_bf16(A, B)
     assert ei.value.status == binding.SEM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 2048, 8192), (512, 256, 16384), (256, 256, 8192), (128, 128, 1088)])
+def test_gemm_splitk_matches_fp64_and_is_deterministic(M, N, K):
+    """Split-K for small outputs with a long K (the network's weight
+    gradients; K = 1088 = 17 K-blocks: the slice count is reduced so that no
+    slice is empty): the same bound against FP64, the bias and activation
+    after the slices are summed, and the same bits on a second call."""
+    c1 = _case(M, N, K, seed=M + N + K, bias=True, act=1, splitk=True)
+    c2 = _case(M, N, K, seed=M + N + K, bias=True, act=1, splitk=True)
+    np.testing.assert_array_equal(c1.cpu().numpy(), c2.cpu().numpy())
