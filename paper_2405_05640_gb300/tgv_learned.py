@@ -22,7 +22,9 @@ only sequences calls and keeps device buffers):
      around flexible FP32 CG with the hybrid Schwarz preconditioner (the
      paper's pressure preconditioner, "schwarz_*"), each from p^{n-1}, from
      p_ext and from the learned guess p_ext + se * MLP(features).
-     Pressure-solve wall time includes building the guess.
+     The three-level Schwarz multigrid ("schwarz3_*": an intermediate order-3
+     level) from p_ext and from the learned guess.  Pressure-solve wall time
+     includes building the guess.
   Phase 1 solves with the Schwarz solver when it is among the methods (the
   pressures, hence the samples, are the same to the tolerance).
 """
@@ -103,7 +105,7 @@ class GuessNet:
 
 
 METHODS = ("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned", "schwarz_prev", "schwarz_extrap",
-           "schwarz_learned")
+           "schwarz_learned", "schwarz3_extrap", "schwarz3_learned")
 
 
 def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs=8, lr=1e-3, hidden=256,
@@ -129,6 +131,11 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
         sw = binding.Schwarz(gm, gc)
         schwarz = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
                               use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2)
+        gmid = binding.Mesh(3, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
+        swmid = binding.Schwarz(gmid, gc)
+        schwarz3 = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
+                               use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
+                               schwarz_mid=swmid, mid_weight=0.15)
     phase1_opts = schwarz if use_sw else chosen
     g = GuessNet(gm, hidden, seed, variant)
 
@@ -209,7 +216,8 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
             guess_ms = (time.perf_counter() - tg) * 1e3
             x0 = guess if guess is not None else p1
             x0c = x0.clone()
-            popts = plain if meth.startswith("plain") else schwarz if meth.startswith("schwarz") else chosen
+            popts = (plain if meth.startswith("plain") else schwarz3 if meth.startswith("schwarz3")
+                     else schwarz if meth.startswith("schwarz") else chosen)
             ps, vs = ns.step_finish(popts, vopts, p_guess=guess)
             p_new = ns.get(3)
             if meth.endswith("_learned") and variant == "d3":
