@@ -262,6 +262,15 @@ typedef struct {
                               order-M mesh of the same elements, M < N, see
                               sem_schwarz_apply3); NULL: two levels */
     double mid_weight;     /* its weight w_M (0 = 0.15) */
+    double inner_adapt;    /* SEM_PCG_MIXED: theta > 0 lets a refinement round stop
+                              once the outer target is within reach: its inner
+                              relative tolerance is max(inner_tol, min(0.5,
+                              theta * target / ||r||)), with target the outer
+                              stopping norm and r the FP64 residual the round
+                              starts from (a guess already near the target needs
+                              a short round, not a reduction by inner_tol);
+                              0 (default): inner_tol every round.  The FP64 true
+                              residual still decides convergence. */
 } sem_pcg_opts;
 
 typedef struct {

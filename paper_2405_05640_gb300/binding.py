@@ -53,7 +53,8 @@ class PcgOpts(ctypes.Structure):
                 ("h2", ctypes.c_double), ("check_every", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int),
                 ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double),
-                ("outer_pair", ctypes.c_int), ("schwarz_mid", ctypes.c_void_p), ("mid_weight", ctypes.c_double)]
+                ("outer_pair", ctypes.c_int), ("schwarz_mid", ctypes.c_void_p), ("mid_weight", ctypes.c_double),
+                ("inner_adapt", ctypes.c_double)]
 
 
 class PcgStats(ctypes.Structure):
@@ -320,12 +321,14 @@ class Mesh:
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
                  mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2,
-                 outer_pair=False, schwarz_mid=None, mid_weight=0.15) -> PcgOpts:
+                 outer_pair=False, schwarz_mid=None, mid_weight=0.15, inner_adapt=0.0) -> PcgOpts:
         """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
         preconditioner of the mixed solver), its coarse level solved by
         coarse_iters Jacobi-CG iterations (3: on the 32^3 channel, N = 7, more
-        do not lower the outer iteration count) to coarse_tol."""
+        do not lower the outer iteration count) to coarse_tol; inner_adapt:
+        theta of the adaptive inner tolerance (0: inner_tol every round)."""
         o = PcgOpts()
+        o.inner_adapt = float(inner_adapt)
         o.schwarz = schwarz.handle.value if schwarz is not None else None
         o.schwarz_mid = schwarz_mid.handle.value if schwarz_mid is not None else None
         o.mid_weight = float(mid_weight)

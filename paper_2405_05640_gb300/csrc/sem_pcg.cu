@@ -106,6 +106,18 @@ __device__ __forceinline__ void set_start_flags(PcgScal *s, double bb, double rr
     }
 }
 
+// Inner relative tolerance of a refinement round: delta, or with theta > 0
+// the larger theta * target / ||r|| (target^2 = the outer tol2, ||r||^2 =
+// the outer rr of `so`), capped at 0.5 so that every round iterates: a round
+// that starts near the outer target stops once the target is within reach.
+__device__ __forceinline__ double inner_delta(const PcgScal *__restrict__ so, double delta, double theta) {
+    if (theta > 0.0 && so->rr > 0.0) {
+        const double a = fmin(0.5, theta * sqrt(so->tol2 / so->rr));
+        if (a > delta) return a;
+    }
+    return delta;
+}
+
 // Start of a CG solve in precision T: r = scale * (b - Ax0) (ax0 may be
 // null), z = dinv r, p = z; bb = <b,b>, rr = <r,r>, rho = <r,z>.
 // In the mixed solver b is the FP64 outer residual and `scale` = 1/||b||
@@ -114,14 +126,14 @@ template <typename T, typename TB>
 __device__ __forceinline__ bool pcg_init_body(const TB *__restrict__ b, const T *__restrict__ ax0,
                                               const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
                                               PcgWork<T> W, const PcgScal *__restrict__ scale_src, double tol,
-                                              int rel, int max_iter);
+                                              int rel, int max_iter, double theta = 0.0);
 
 template <typename T, typename TB>
 __global__ void __launch_bounds__(kPThreads)
     pcg_init_kernel(const TB *__restrict__ b, const T *__restrict__ ax0, const T *__restrict__ dinv,
                     const T *__restrict__ minv, int64_t n, PcgWork<T> W, const PcgScal *__restrict__ scale_src,
-                    double tol, int rel, int max_iter) {
-    pcg_init_body<T, TB>(b, ax0, dinv, minv, n, W, scale_src, tol, rel, max_iter);
+                    double tol, int rel, int max_iter, double theta = 0.0) {
+    pcg_init_body<T, TB>(b, ax0, dinv, minv, n, W, scale_src, tol, rel, max_iter, theta);
 }
 
 // Returns true on the thread that wrote the scalars.
@@ -129,8 +141,9 @@ template <typename T, typename TB>
 __device__ __forceinline__ bool pcg_init_body(const TB *__restrict__ b, const T *__restrict__ ax0,
                                               const T *__restrict__ dinv, const T *__restrict__ minv, int64_t n,
                                               PcgWork<T> W, const PcgScal *__restrict__ scale_src, double tol,
-                                              int rel, int max_iter) {
+                                              int rel, int max_iter, double theta) {
     const double sc = scale_src ? scale_src->scale : 1.0;
+    if (scale_src) tol = inner_delta(scale_src, tol, theta);
     double v[3] = {0.0, 0.0, 0.0};
     T f[3] = {T(0), T(0), T(0)};  // per-thread partials in T (FP32: no FP64 pipe per element)
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
@@ -439,7 +452,8 @@ __global__ void __launch_bounds__(kPThreads)
 // loop resumes until its residual has fallen by `delta` again.
 __global__ void __launch_bounds__(kPThreads)
     ir_reliable_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
-                       int64_t n, PcgWork<float> W, const PcgScal *__restrict__ so, double delta) {
+                       int64_t n, PcgWork<float> W, const PcgScal *__restrict__ so, double delta, double theta) {
+    delta = inner_delta(so, delta, theta);
     const double inv = so->scale;
     const float c = (float)(so->scale / so->scale_prev);
     float f0 = 0.f, f1 = 0.f;
@@ -855,11 +869,12 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
             // inner FP32 solve of A d = r / ||r||, from d = 0
             SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
             pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
-                M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total);
+                M.r64, nullptr, m->dinv32, m->minv32, n, M.in, M.scal_out, inner_tol, 1, o->max_iter - inner_total,
+                o->inner_adapt);
         } else {
             // keep the search direction: swap in the FP64 residual and go on
             ir_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(M.r64, m->dinv32, m->minv32, n, M.in, M.scal_out,
-                                                               inner_tol);
+                                                               inner_tol, o->inner_adapt);
         }
         SEM_CUDA_CHECK(cudaGetLastError());
         cin.launches += 1;
@@ -926,6 +941,8 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_INVALID_ARG, "SEM_PCG_MIXED needs a mesh built with SEM_GEOM_F32");
     if (o->precision == SEM_PCG_MIXED && (o->h2 != 0.0 || o->h1 != 1.0 || o->dinv))
         return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_MIXED solves the Poisson operator (h1 = 1, h2 = 0, mesh diagonal)");
+    if (!(o->inner_adapt >= 0.0 && o->inner_adapt < 1.0))
+        return fail(SEM_ERR_INVALID_ARG, "inner_adapt must be in [0, 1)");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     return SEM_OK;
 }
@@ -1024,8 +1041,9 @@ __global__ void __launch_bounds__(kPThreads)
 // the last block resumes the iteration.
 __global__ void __launch_bounds__(kPThreads)
     bt_reliable_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
-                       int64_t n, PcgWork<float> W, PcgScal *so, double delta) {
+                       int64_t n, PcgWork<float> W, PcgScal *so, double delta, double theta) {
     if (so->phase != kBtReliable) return;
+    delta = inner_delta(so, delta, theta);
     const double inv = so->scale;
     const float c = (float)(so->scale / so->scale_prev);
     float f0 = 0.f, f1 = 0.f;
@@ -1094,10 +1112,10 @@ __global__ void bt_round_end_kernel(PcgScal *s, const int *__restrict__ err, int
 // residual (the init of the single-solve path), then the solve iterates.
 __global__ void __launch_bounds__(kPThreads)
     bt_restart_kernel(const double *__restrict__ r64, const float *__restrict__ dinv, const float *__restrict__ minv,
-                      int64_t n, PcgWork<float> W, PcgScal *so, double delta, int max_iter) {
+                      int64_t n, PcgWork<float> W, PcgScal *so, double delta, int max_iter, double theta) {
     if (so->phase != kBtReliable) return;  // uniform
     const int before = W.scal->iter;  // read before the last block resets it
-    if (pcg_init_body<float, double>(r64, nullptr, dinv, minv, n, W, so, delta, 1, max_iter)) {
+    if (pcg_init_body<float, double>(r64, nullptr, dinv, minv, n, W, so, delta, 1, max_iter, theta)) {
         so->inner_done += before;
         so->phase = W.scal->done && W.scal->status == SEM_ERR_NAN ? kBtFinished : kBtIterate;
     }
@@ -1156,10 +1174,10 @@ static int bt_round(BtSolve &S, const sem_pcg_opts *o, int K, cudaStream_t st) {
                                                        S.M.scal_out, S.M.in.scal);
     if (S.sw)
         bt_restart_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
-                                                          itol, o->max_iter);
+                                                          itol, o->max_iter, o->inner_adapt);
     else
         bt_reliable_kernel<<<kPBlocks, kPThreads, 0, st>>>(S.M.r64, m->dinv32, m->minv32, n, S.M.in, S.M.scal_out,
-                                                           itol);
+                                                           itol, o->inner_adapt);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
@@ -1279,7 +1297,8 @@ static int bt_capture_solve(BtSolve &S, const sem_pcg_opts *o, int K, int max_ro
     ir_residual_kernel<<<kPBlocks, kPThreads, 0, q>>>(S.b, nullptr, S.M.r64, m->minv, n, S.M.partial_out,
                                                       S.M.scal_out, o->tol, o->tol_is_relative);
     pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, q>>>(S.M.r64, nullptr, m->dinv32, m->minv32, n, S.M.in,
-                                                                  S.M.scal_out, itol, 1, o->max_iter);
+                                                                  S.M.scal_out, itol, 1, o->max_iter,
+                                                                  o->inner_adapt);
     SEM_CUDA_CHECK(cudaGetLastError());
     cudaStreamCaptureStatus cst;
     cudaGraph_t g = nullptr;
@@ -1334,6 +1353,8 @@ static int batched_impl(const sem_mesh *const *meshes, const sem_schwarz *const 
     if (o->use_initial_guess) return fail(SEM_ERR_UNSUPPORTED, "batched solves start from x = 0");
     if (o->schwarz || o->schwarz_mid || o->outer_pair)
         return fail(SEM_ERR_UNSUPPORTED, "batched solves use the Jacobi inner solver");
+    if (!(o->inner_adapt >= 0.0 && o->inner_adapt < 1.0))
+        return fail(SEM_ERR_INVALID_ARG, "inner_adapt must be in [0, 1)");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     for (int i = 0; i < nsolve; ++i) {
         if (!meshes[i] || !b[i] || !x[i]) return fail(SEM_ERR_INVALID_ARG, "NULL mesh, b or x");

@@ -23,8 +23,10 @@ only sequences calls and keeps device buffers):
      paper's pressure preconditioner, "schwarz_*"), each from p^{n-1}, from
      p_ext and from the learned guess p_ext + se * MLP(features).
      The three-level Schwarz multigrid ("schwarz3_*": an intermediate order-3
-     level) from p_ext and from the learned guess.  Pressure-solve wall time
-     includes building the guess.
+     level) from p_ext and from the learned guess.  Every mixed solve uses
+     the adaptive inner tolerance inner_adapt (a round stops once the outer
+     target is within reach); the "*_fixed" methods keep inner_tol = 1e-2
+     every round.  Pressure-solve wall time includes building the guess.
   Phase 1 solves with the Schwarz solver when it is among the methods (the
   pressures, hence the samples, are the same to the tolerance).
 """
@@ -104,12 +106,20 @@ class GuessNet:
         return self.guess
 
 
-METHODS = ("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned", "schwarz_prev", "schwarz_extrap",
-           "schwarz_learned", "schwarz3_extrap", "schwarz3_learned")
+METHODS = ("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned", "chosen_extrap_fixed",
+           "schwarz_prev", "schwarz_extrap", "schwarz_learned", "schwarz_extrap_fixed", "schwarz_learned_fixed",
+           "schwarz3_extrap", "schwarz3_learned")
+
+
+def _method(meth):
+    """(solver, guess, fixed inner tolerance) of a method name."""
+    solver = meth.split("_")[0]
+    guess = "extrap" if "_extrap" in meth else "learned" if "_learned" in meth else "prev"
+    return solver, guess, meth.endswith("_fixed")
 
 
 def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs=8, lr=1e-3, hidden=256,
-        tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, log=None):
+        tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, inner_adapt=0.5, log=None):
     import torch
     log = log or (lambda *a: None)
     t_all = time.perf_counter()
@@ -120,7 +130,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     ns = binding.NSState(gm, Re)
     ns.set_velocity(u0)
     chosen = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
-                         use_initial_guess=True, check_every=32)
+                         use_initial_guess=True, check_every=32, inner_adapt=inner_adapt)
     plain = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_F64, use_initial_guess=True,
                         check_every=32)
     vopts = gm.pcg_opts(tol=tol, max_iter=50000, check_every=8)
@@ -130,12 +140,13 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
         gc = binding.Mesh(1, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
         sw = binding.Schwarz(gm, gc)
         schwarz = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
-                              use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2)
+                              use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
+                              inner_adapt=inner_adapt)
         gmid = binding.Mesh(3, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
         swmid = binding.Schwarz(gmid, gc)
         schwarz3 = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
                                use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
-                               schwarz_mid=swmid, mid_weight=0.15)
+                               schwarz_mid=swmid, mid_weight=0.15, inner_adapt=inner_adapt)
     phase1_opts = schwarz if use_sw else chosen
     g = GuessNet(gm, hidden, seed, variant)
 
@@ -193,7 +204,15 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     p4_ck = p4.clone()
     rho_ck = g.rho_prev
     results = {}
+    by_solver = {"plain": plain, "chosen": chosen}
+    if use_sw:
+        by_solver.update(schwarz=schwarz, schwarz3=schwarz3)
     for meth in methods:
+        solver, gkind, fixed = _method(meth)
+        popts = by_solver[solver]
+        if fixed:
+            popts = binding.PcgOpts.from_buffer_copy(popts)
+            popts.inner_adapt = 0.0
         ns.restore(ck)
         p4 = p4_ck.clone()
         g.rho_prev = rho_ck
@@ -204,10 +223,10 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
             torch.cuda.synchronize()
             tg = time.perf_counter()
             guess = None
-            if meth.endswith("_extrap"):
+            if gkind == "extrap":
                 guess = g.extrap(p1, p2, p3)
                 torch.cuda.synchronize()
-            elif meth.endswith("_learned"):
+            elif gkind == "learned":
                 g.residual(b, p1, p2, p3)
                 g.set_scales(p1, p2, p3, p4)
                 g.features(p1, p2, p3, p4)
@@ -216,11 +235,9 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
             guess_ms = (time.perf_counter() - tg) * 1e3
             x0 = guess if guess is not None else p1
             x0c = x0.clone()
-            popts = (plain if meth.startswith("plain") else schwarz3 if meth.startswith("schwarz3")
-                     else schwarz if meth.startswith("schwarz") else chosen)
             ps, vs = ns.step_finish(popts, vopts, p_guess=guess)
             p_new = ns.get(3)
-            if meth.endswith("_learned") and variant == "d3":
+            if gkind == "learned" and variant == "d3":
                 g.update_rho(p_new)
             err = math.sqrt(gm.glsc3(x0c - p_new, x0c - p_new) / max(gm.glsc3(p_new, p_new), 1e-300))
             iters.append(ps["iters"])

@@ -90,7 +90,38 @@ def test_schwarz_and_solver_option_host_checks(lib):
     # double-float outer-residual switch and the intermediate multigrid level
     # at the end of the struct
     names = [f[0] for f in binding.PcgOpts._fields_]
-    assert names[-6:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair", "schwarz_mid", "mid_weight"]
+    assert names[-7:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair", "schwarz_mid", "mid_weight",
+                          "inner_adapt"]
     assert lib.sem_schwarz_mid_work_bytes(None) == 0
     assert lib.sem_schwarz_apply3(None, None, 0.15, None, None, 3, 1e-2, None, 0, None) == \
         binding.SEM_ERR_INVALID_ARG
+
+
+def _header_struct(name):
+    """(field, C type class) of `typedef struct { ... } name;` in sem.h, in
+    declaration order."""
+    text = open(os.path.join(ROOT, "include", "sem.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        kind = "ptr" if "*" in decl else decl.split()[0]
+        pieces = decl.replace("*", " ").split(",")
+        out.append((pieces[0].split()[-1], kind))
+        out += [(p.strip(), kind) for p in pieces[1:]]
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("sem_pcg_opts", "PcgOpts"), ("sem_pcg_stats", "PcgStats")])
+def test_option_and_stats_structs_match_the_header(cname, pyname):
+    """The binding's ctypes layouts follow the header field by field (name,
+    order and type), so a field added to the C struct cannot shift the
+    ones after it."""
+    kinds = {"double": ctypes.c_double, "int": ctypes.c_int, "ptr": ctypes.c_void_p}
+    want = [(n, kinds[k]) for n, k in _header_struct(cname)]
+    got = list(getattr(binding, pyname)._fields_)
+    assert got == want
