@@ -99,6 +99,12 @@ def parse_args(argv=None):
     p.add_argument("--epochs", type=int, default=30)
     p.add_argument("--variant", choices=["p1", "d3"], default="p1")
     p.add_argument("--tol", type=float, default=1e-8, help="tgv-learned: relative tolerance of the pressure solves")
+    p.add_argument("--loss", choices=["mse", "energy", "energy_avg"], default="energy_avg",
+                   help="tgv-learned: training loss")
+    p.add_argument("--lam", type=float, default=1.0, help="tgv-learned: mass weight of the energy-norm loss")
+    p.add_argument("--methods", default="", help="tgv-learned: comma-separated subset of the methods")
+    p.add_argument("--fp64-residual", action="store_true",
+                   help="tgv-learned: residual feature with the FP64 operator (default: FP32-pair)")
     p.add_argument("--bf16", action="store_true",
                    help="channel variant: the FP32 inner operator reads BF16 geometric factors (32 B/point)")
     p.add_argument("--affine", action="store_true",
@@ -908,9 +914,12 @@ def run_tgv_learned(args):
     from paper_2405_05640_gb300 import tgv_learned
     _build.build()
     out = tgv_learned.run(nel=args.nel, N=args.order, train_steps=args.train_steps, eval_steps=args.eval_steps,
-                          epochs=args.epochs, variant=args.variant, inner_adapt=INNER_ADAPT, tol=args.tol)
+                          epochs=args.epochs, variant=args.variant, inner_adapt=INNER_ADAPT, tol=args.tol,
+                          loss=args.loss, lam=args.lam,
+                          pair=not args.fp64_residual,
+                          **({"methods": tuple(args.methods.split(","))} if args.methods else {}))
     m = out["methods"]
-    best = max((k for k in m if k != "plain_f64_prev"), key=lambda k: m[k]["speedup_vs_plain_f64_prev"])
+    best = min((k for k in m if k != "plain_f64_prev"), key=lambda k: m[k]["pressure_ms_total"])
     gain = {}
     for solver in ("chosen", "schwarz", "schwarz3", "schwarz_fixed"):
         base, fx = solver.split("_")[0], "_fixed" if solver.endswith("_fixed") else ""
@@ -921,7 +930,7 @@ def run_tgv_learned(args):
                             "time_gain": round(1.0 - a["pressure_ms_total"] / b["pressure_ms_total"], 4)}
     rec = {"metric": f"pressure-solve wall time to {args.tol:g} over the evaluated TGV steps, fastest method vs plain "
                      "FP64 (x0 = previous pressure)",
-           "value": m[best]["speedup_vs_plain_f64_prev"], "unit": "x (speedup)", "best_method": best,
+           "value": m[best].get("speedup_vs_plain_f64_prev"), "unit": "x (speedup)", "best_method": best,
            "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 network / f32 inner / f64 refinement",
            "data": "synthetic", "config": {"workload": out["workload"]}, "inner_adapt": INNER_ADAPT,
            "learned_gain": gain, **out}

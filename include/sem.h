@@ -440,6 +440,25 @@ int sem_mlp_forward(sem_mlp *mlp, const void *X, int rows, float *Y, void *strea
  * Waits for `stream`. */
 int sem_mlp_grad(sem_mlp *mlp, const void *X, const float *T, int rows, int rows_real, int outs_real,
                  double *loss, void *stream);
+/* Forward and backward with the energy-norm loss of a guess network on
+ * `mesh` (one row per element, output q = the element's point q):
+ *   L = (1 / (2 E npt)) sum_e d_e^T (A_e + lambda B_e) d_e
+ * over the E elements and npt points, with d = Y - T (assembled = 0) or,
+ * assembled = 1, d = M^-1 Q Q^T (Y - T): the error of the averaged,
+ * continuous correction the guess uses (sem_guess_apply), so that the
+ * disagreement of neighbouring elements is part of the loss (gradient
+ * Q Q^T M^-1 (A_L + lambda B) d).  A_e: element stiffness matrix, the local
+ * operator of sem_ax, here in FP32 on the mesh's FP32 geometric factors;
+ * B_e: diagonal mass; the sums of copies in FP32.  Errors of high spatial
+ * frequency, which the solver sees amplified in its residual, weigh more
+ * than in the plain mean square; lambda B keeps the element-wise constants
+ * (the null space of A_e) in the loss.  X [rows x I] BF16, T [rows x O] FP32
+ * (row e = element e, rows >= E, O >= npt); work: device, >= 2 nloc floats
+ * (caller-owned).  Requires SEM_GEOM_F32 in the mesh; lambda >= 0.  Waits
+ * for `stream`. */
+int sem_mlp_grad_energy(sem_mlp *mlp, const sem_mesh *mesh, const void *X, const float *T, int rows,
+                        double lambda, int assembled, float *work, size_t work_floats, double *loss,
+                        void *stream);
 /* One Adam step with the stored gradients. */
 int sem_mlp_adam(sem_mlp *mlp, double lr, double beta1, double beta2, double eps, void *stream);
 
@@ -449,6 +468,11 @@ int sem_mlp_adam(sem_mlp *mlp, double lr, double beta1, double beta2, double eps
  * remove, e = p - p_ext, satisfies A e = r. */
 int sem_guess_residual(const sem_mesh *mesh, const double *b, const double *p1, const double *p2,
                        const double *p3, double *r, double *work, void *stream);
+/* The same residual with the operator in FP32-pair arithmetic (as sem_ax
+ * SEM_F64_PAIR: error ~2^-42 of the line-wise magnitudes, plenty for a
+ * feature that is rounded to BF16); requires SEM_GEOM_PAIR in the mesh. */
+int sem_guess_residual_pair(const sem_mesh *mesh, const double *b, const double *p1, const double *p2,
+                            const double *p3, double *r, double *work, void *stream);
 /* Features for every element e (row e of X, BF16, ldx >= 4 npt):
  * (p1 - p2)/sd, (p2 - p3)/sd, r/sr and, with p4 (the pressure four steps
  * back) given, the previous step's extrapolation error (third difference)

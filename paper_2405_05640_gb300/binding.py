@@ -120,8 +120,11 @@ _SIGS = {
     "sem_mlp_forward": ([_VP, _VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "sem_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                       _VP], ctypes.c_int),
+    "sem_mlp_grad_energy": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, ctypes.c_size_t,
+                             ctypes.POINTER(ctypes.c_double), _VP], ctypes.c_int),
     "sem_mlp_adam": ([_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
     "sem_guess_residual": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "sem_guess_residual_pair": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "sem_guess_features": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             _VP, ctypes.c_int, _VP], ctypes.c_int),
     "sem_ns_step_begin": ([_VP, ctypes.c_double, _VP], ctypes.c_int),
@@ -637,14 +640,29 @@ class MLP:
                                  int(outs_real or self.O), ctypes.byref(loss), _stream()), "sem_mlp_grad")
         return loss.value
 
+    def grad_energy(self, X, T, mesh, lam, assembled=False, work=None):
+        """sem_mlp_grad_energy: the energy-norm loss on `mesh` (assembled:
+        of the averaged correction; work: >= 2 nloc FP32 device floats,
+        allocated when not given)."""
+        import torch
+        if work is None:
+            work = torch.empty(2 * mesh.nloc, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        check(lib().sem_mlp_grad_energy(self.handle, mesh.handle, _ptr(X), _ptr(T), X.shape[0], float(lam),
+                                        int(bool(assembled)), _ptr(work), work.numel(), ctypes.byref(loss),
+                                        _stream()),
+              "sem_mlp_grad_energy")
+        return loss.value
+
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         check(lib().sem_mlp_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps), _stream()),
               "sem_mlp_adam")
 
 
-def guess_residual(mesh, b, p1, p2, p3, r, work):
-    check(lib().sem_guess_residual(mesh.handle, _ptr(b), _ptr(p1), _ptr(p2), _ptr(p3), _ptr(r), _ptr(work),
-                                   _stream()), "sem_guess_residual")
+def guess_residual(mesh, b, p1, p2, p3, r, work, pair=False):
+    """r = b - A p_ext (pair: the operator in FP32-pair arithmetic)."""
+    fn = "sem_guess_residual_pair" if pair else "sem_guess_residual"
+    check(getattr(lib(), fn)(mesh.handle, _ptr(b), _ptr(p1), _ptr(p2), _ptr(p3), _ptr(r), _ptr(work), _stream()), fn)
 
 
 def guess_features(mesh, p1, p2, p3, p4, r, sd, sr, s3, X):

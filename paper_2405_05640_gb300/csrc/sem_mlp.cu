@@ -101,6 +101,78 @@ __global__ void sum_partials_kernel(const float *__restrict__ part, int n, doubl
     }
 }
 
+// Energy-norm loss: delta = Y - T for the E elements (rows) and npt points
+// (outputs) of a mesh, in the element-local layout [E][npt] of its fields.
+__global__ void energy_delta_kernel(const float *__restrict__ Y, const float *__restrict__ T, int ld, int64_t E,
+                                    int npt, float *__restrict__ D) {
+    const int64_t n = E * npt;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = l / npt;
+        const int q = (int)(l - e * npt);
+        D[l] = Y[e * ld + q] - T[e * ld + q];
+    }
+}
+
+// x *= w (FP32 by an FP32 weight)
+__global__ void scale_f32_kernel(float *__restrict__ x, const float *__restrict__ w, int64_t n) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+        x[l] *= w[l];
+}
+
+// K-norm pieces: g = A_L delta + lambda B delta (W = A_L delta, element by
+// element); sum delta g into the block partials; g stays in W when
+// `keep`, else dY = g / (E npt) (BF16) on real entries, 0 elsewhere.
+__global__ void energy_grad_kernel(const float *__restrict__ D, float *__restrict__ W,
+                                   const double *__restrict__ Bm, float lambda, int rows, int outs, int64_t E,
+                                   int npt, bool keep, bf16 *__restrict__ dY, float *__restrict__ part) {
+    __shared__ float sh[8];
+    const float sc = 1.0f / ((float)E * (float)npt);
+    float acc = 0.f;
+    if (keep) {
+        const int64_t n = E * npt;
+        for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+             l += (int64_t)gridDim.x * blockDim.x) {
+            const float d = D[l];
+            const float g = fmaf(lambda * (float)Bm[l], d, W[l]);
+            W[l] = g;
+            acc = fmaf(d, g, acc);
+        }
+    } else {
+        const int64_t n = (int64_t)rows * outs;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int r = (int)(i / outs), o = (int)(i - (int64_t)r * outs);
+            float g = 0.f;
+            if (r < E && o < npt) {
+                const int64_t l = (int64_t)r * npt + o;
+                const float d = D[l];
+                g = fmaf(lambda * (float)Bm[l], d, W[l]);
+                acc = fmaf(d, g, acc);
+            }
+            dY[i] = __float2bfloat16_rn(g * sc);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        part[blockIdx.x] = t;
+    }
+}
+
+// dY = G / (E npt) (BF16) on real entries (G in the element layout), 0 elsewhere.
+__global__ void energy_dy_kernel(const float *__restrict__ G, int rows, int outs, int64_t E, int npt,
+                                 bf16 *__restrict__ dY) {
+    const float sc = 1.0f / ((float)E * (float)npt);
+    const int64_t n = (int64_t)rows * outs;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / outs), o = (int)(i - (int64_t)r * outs);
+        dY[i] = __float2bfloat16_rn(r < E && o < npt ? G[(int64_t)r * npt + o] * sc : 0.f);
+    }
+}
+
 // dA = dH * (H > 0) (ReLU derivative from the post-activation), BF16
 __global__ void relu_mask_kernel(const float *__restrict__ dH, const bf16 *__restrict__ H, bf16 *__restrict__ dA,
                                  int64_t n) {
@@ -316,24 +388,15 @@ int sem_mlp_forward(sem_mlp *n, const void *X, int rows, float *Y, void *stream)
     return SEM_OK;
 }
 
-int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_real, int outs_real, double *loss,
-                 void *stream) {
-    if (!n || !X || !T || !loss) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
-    if (rows <= 0 || rows % 128 || rows > n->R || rows_real <= 0 || rows_real > rows || outs_real <= 0 ||
-        outs_real > n->O)
-        return fail(SEM_ERR_INVALID_ARG, "bad row / output counts");
-    cudaStream_t st = as_stream(stream);
-    const int I = n->I, H = n->H, O = n->O, R = rows;
-    int s = fwd(n, X, R, st);
-    if (s != SEM_OK) return s;
-    const int lblocks = 1024;
-    loss_grad_kernel<<<lblocks, 256, 0, st>>>(n->Y, T, R, O, rows_real, outs_real, n->dY, n->part);
-    double *dloss = reinterpret_cast<double *>(n->err + 8);
-    sum_partials_kernel<<<1, 32, 0, st>>>(n->part, lblocks, dloss);
+// Backward pass from the BF16 output gradient in n->dY: the weight and bias
+// gradients into n->g.
+static int mlp_backward(sem_mlp *n, const void *X, int R, cudaStream_t st) {
+    const int I = n->I, H = n->H, O = n->O;
     // layer 3
     transpose<bf16, bf16>(n->dY, n->dYT, R, O, st);
     transpose<bf16, bf16>(n->H2, n->H2T, R, H, st);
-    s = gemm_tn_bf16(n->dYT, n->H2T, O, H, R, nullptr, 0, n->g + n->oW3, nullptr, H, n->err, st, n->wsk, n->wsk_floats);
+    int s = gemm_tn_bf16(n->dYT, n->H2T, O, H, R, nullptr, 0, n->g + n->oW3, nullptr, H, n->err, st, n->wsk,
+                         n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dY, R, O, n->part, n->g + n->ob3, st);
     s = gemm_tn_bf16(n->dY, n->W3t, R, H, O, nullptr, 0, n->dH2, nullptr, H, n->err, st, nullptr, 0);
@@ -342,7 +405,8 @@ int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_r
     // layer 2
     transpose<bf16, bf16>(n->dA2, n->dA2T, R, H, st);
     transpose<bf16, bf16>(n->H1, n->H1T, R, H, st);
-    s = gemm_tn_bf16(n->dA2T, n->H1T, H, H, R, nullptr, 0, n->g + n->oW2, nullptr, H, n->err, st, n->wsk, n->wsk_floats);
+    s = gemm_tn_bf16(n->dA2T, n->H1T, H, H, R, nullptr, 0, n->g + n->oW2, nullptr, H, n->err, st, n->wsk,
+                     n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dA2, R, H, n->part, n->g + n->ob2, st);
     s = gemm_tn_bf16(n->dA2, n->W2t, R, H, H, nullptr, 0, n->dH1, nullptr, H, n->err, st, nullptr, 0);
@@ -351,18 +415,84 @@ int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_r
     // layer 1
     transpose<bf16, bf16>(n->dA1, n->dA1T, R, H, st);
     transpose<bf16, bf16>(static_cast<const bf16 *>(X), n->XT, R, I, st);
-    s = gemm_tn_bf16(n->dA1T, n->XT, H, I, R, nullptr, 0, n->g + n->oW1, nullptr, I, n->err, st, n->wsk, n->wsk_floats);
+    s = gemm_tn_bf16(n->dA1T, n->XT, H, I, R, nullptr, 0, n->g + n->oW1, nullptr, I, n->err, st, n->wsk,
+                     n->wsk_floats);
     if (s != SEM_OK) return s;
     colsum(n->dA1, R, H, n->part, n->g + n->ob1, st);
     SEM_CUDA_CHECK(cudaGetLastError());
+    return SEM_OK;
+}
+
+// The loss sum (dloss, reduced from the partials before the backward pass
+// reuses n->part) and the GEMMs' timeout flag, read after the pass:
+// *loss = 0.5 sum / norm.
+static int mlp_finish(sem_mlp *n, const double *dloss, double norm, double *loss, cudaStream_t st) {
     double h = 0.0;
     int herr = 0;
     SEM_CUDA_CHECK(cudaMemcpyAsync(&h, dloss, sizeof(double), cudaMemcpyDeviceToHost, st));
     SEM_CUDA_CHECK(cudaMemcpyAsync(&herr, n->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SEM_CUDA_CHECK(cudaStreamSynchronize(st));
     if (herr) return fail(SEM_ERR_TIMEOUT, "a GEMM wait timed out");
-    *loss = 0.5 * h / ((double)rows_real * outs_real);
+    *loss = 0.5 * h / norm;
     return SEM_OK;
+}
+
+int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_real, int outs_real, double *loss,
+                 void *stream) {
+    if (!n || !X || !T || !loss) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (rows <= 0 || rows % 128 || rows > n->R || rows_real <= 0 || rows_real > rows || outs_real <= 0 ||
+        outs_real > n->O)
+        return fail(SEM_ERR_INVALID_ARG, "bad row / output counts");
+    cudaStream_t st = as_stream(stream);
+    int s = fwd(n, X, rows, st);
+    if (s != SEM_OK) return s;
+    const int lblocks = 1024;
+    loss_grad_kernel<<<lblocks, 256, 0, st>>>(n->Y, T, rows, n->O, rows_real, outs_real, n->dY, n->part);
+    double *dloss = reinterpret_cast<double *>(n->err + 8);
+    sum_partials_kernel<<<1, 32, 0, st>>>(n->part, lblocks, dloss);
+    s = mlp_backward(n, X, rows, st);
+    if (s != SEM_OK) return s;
+    return mlp_finish(n, dloss, (double)rows_real * outs_real, loss, st);
+}
+
+int sem_mlp_grad_energy(sem_mlp *n, const sem_mesh *m, const void *X, const float *T, int rows, double lambda,
+                        int assembled, float *work, size_t work_floats, double *loss, void *stream) {
+    if (!n || !m || !X || !T || !work || !loss) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (rows <= 0 || rows % 128 || rows > n->R || m->E > rows || m->npt > n->O)
+        return fail(SEM_ERR_INVALID_ARG, "rows must be a multiple of 128 with E <= rows <= max_rows, npt <= n_out");
+    if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "the energy norm needs a mesh built with SEM_GEOM_F32");
+    if (!(lambda >= 0.0)) return fail(SEM_ERR_INVALID_ARG, "lambda must be >= 0");
+    if (work_floats < 2 * (size_t)m->nloc) return fail(SEM_ERR_WORKSPACE, "work holds fewer than 2 nloc floats");
+    cudaStream_t st = as_stream(stream);
+    int s = fwd(n, X, rows, st);
+    if (s != SEM_OK) return s;
+    float *D = work, *W = work + m->nloc;
+    energy_delta_kernel<<<gridn(m->nloc), 256, 0, st>>>(n->Y, T, n->O, m->E, m->npt, D);
+    SEM_CUDA_CHECK(cudaGetLastError());
+    if (assembled) {
+        // the averaged correction's error: D <- M^-1 S D (S: sum of the copies)
+        s = gs_launch(m, D, SEM_F32, kGsSum, st);
+        if (s != SEM_OK) return s;
+        scale_f32_kernel<<<gridn(m->nloc), 256, 0, st>>>(D, m->minv32, m->nloc);
+    }
+    s = ax_launch_f32(m, D, W, st);
+    if (s != SEM_OK) return s;
+    const int lblocks = 1024;
+    energy_grad_kernel<<<lblocks, 256, 0, st>>>(D, W, m->B, (float)lambda, rows, n->O, m->E, m->npt, assembled != 0,
+                                                n->dY, n->part);
+    double *dloss = reinterpret_cast<double *>(n->err + 8);
+    sum_partials_kernel<<<1, 32, 0, st>>>(n->part, lblocks, dloss);
+    if (assembled) {
+        // gradient S M^-1 (A_L + lambda B) M^-1 S delta
+        scale_f32_kernel<<<gridn(m->nloc), 256, 0, st>>>(W, m->minv32, m->nloc);
+        s = gs_launch(m, W, SEM_F32, kGsSum, st);
+        if (s != SEM_OK) return s;
+        energy_dy_kernel<<<gridn((int64_t)rows * n->O), 256, 0, st>>>(W, rows, n->O, m->E, m->npt, n->dY);
+    }
+    SEM_CUDA_CHECK(cudaGetLastError());
+    s = mlp_backward(n, X, rows, st);
+    if (s != SEM_OK) return s;
+    return mlp_finish(n, dloss, (double)m->E * m->npt, loss, st);
 }
 
 int sem_mlp_adam(sem_mlp *n, double lr, double beta1, double beta2, double eps, void *stream) {
@@ -447,19 +577,30 @@ __global__ void scale_by_kernel(double *__restrict__ g, const double *__restrict
 
 extern "C" {
 
-int sem_guess_residual(const sem_mesh *m, const double *b, const double *p1, const double *p2, const double *p3,
-                       double *r, double *work, void *stream) {
+static int guess_residual(const sem_mesh *m, const double *b, const double *p1, const double *p2, const double *p3,
+                          double *r, double *work, bool pair, void *stream) {
     if (!m || !b || !p1 || !p2 || !p3 || !r || !work || r == work) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
+    if (pair && !m->G2) return fail(SEM_ERR_INVALID_ARG, "the FP32-pair operator needs a mesh built with SEM_GEOM_PAIR");
     cudaStream_t st = as_stream(stream);
     extrap_kernel<<<gridn(m->nloc), 256, 0, st>>>(p1, p2, p3, m->nloc, work);
     SEM_CUDA_CHECK(cudaGetLastError());
-    int s = ax_launch_f64(m, work, r, 1.0, 0.0, st);
+    int s = pair ? ax_launch_pair(m, work, r, st) : ax_launch_f64(m, work, r, 1.0, 0.0, st);
     if (s != SEM_OK) return s;
     s = gs_launch(m, r, SEM_F64, kGsSumMask, st);
     if (s != SEM_OK) return s;
     sub_kernel<<<gridn(m->nloc), 256, 0, st>>>(b, r, m->nloc, r);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
+}
+
+int sem_guess_residual(const sem_mesh *m, const double *b, const double *p1, const double *p2, const double *p3,
+                       double *r, double *work, void *stream) {
+    return guess_residual(m, b, p1, p2, p3, r, work, false, stream);
+}
+
+int sem_guess_residual_pair(const sem_mesh *m, const double *b, const double *p1, const double *p2,
+                            const double *p3, double *r, double *work, void *stream) {
+    return guess_residual(m, b, p1, p2, p3, r, work, true, stream);
 }
 
 int sem_guess_features(const sem_mesh *m, const double *p1, const double *p2, const double *p3, const double *p4,

@@ -15,7 +15,12 @@ only sequences calls and keeps device buffers):
          se; rho taken from the previous step (tracks its drift).
      Every scale is known before the solve, so inference uses the same ones.
   2. The element-local network (sem_mlp_*) is trained with Adam on all
-     samples (tcgen05 GEMMs forward and backward).
+     samples (tcgen05 GEMMs forward and backward), with the mean-square loss
+     ("mse") or the energy norm of its error (sem_mlp_grad_energy: stiffness
+     plus lam times the mass, so that errors the solver sees amplified in its
+     residual weigh more), element by element ("energy") or of the averaged
+     correction the guess uses ("energy_avg": the disagreement of
+     neighbouring elements counts too).
   3. From the checkpoint at step train_steps, eval_steps more steps are run
      once per method: plain FP64 PCG from x0 = p^{n-1} (the stronger plain
      baseline); FP64 refinement around FP32 Jacobi-PCG ("chosen_*") and
@@ -47,10 +52,11 @@ def _rup(x, m=128):
 class GuessNet:
     """Features, targets and guesses for one mesh, plus the network."""
 
-    def __init__(self, gm, hidden=256, seed=0, variant="p1"):
+    def __init__(self, gm, hidden=256, seed=0, variant="p1", pair=False):
         import torch
         self.gm = gm
         self.variant = variant
+        self.pair = pair  # residual feature with the FP32-pair operator
         self.E, self.npt = gm.E, gm.npt
         self.I, self.O, self.R = _rup(4 * self.npt), _rup(self.npt), _rup(self.E)
         self.H = hidden
@@ -69,7 +75,7 @@ class GuessNet:
         return math.sqrt(max(self.gm.glsc3(a, a), 0.0) / self.gm.nglob)
 
     def residual(self, b, p1, p2, p3):
-        binding.guess_residual(self.gm, b, p1, p2, p3, self.r, self.pext)
+        binding.guess_residual(self.gm, b, p1, p2, p3, self.r, self.pext, pair=self.pair)
 
     def extrap(self, p1, p2, p3):
         """The cubic extrapolation alone (no residual: only the network's
@@ -119,12 +125,14 @@ def _method(meth):
 
 
 def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs=8, lr=1e-3, hidden=256,
-        tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, inner_adapt=0.5, log=None):
+        tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, inner_adapt=0.5, loss="energy_avg", lam=1.0,
+        pair=True, log=None):
     import torch
     log = log or (lambda *a: None)
     t_all = time.perf_counter()
     case = inputs.tgv_box(nel, N)
-    gm = binding.Mesh(N, case.nel, case.periodic, case.faces, case.vertices(), geom_rx=True, geom_f32=True)
+    gm = binding.Mesh(N, case.nel, case.periodic, case.faces, case.vertices(), geom_rx=True, geom_f32=True,
+                      geom_pair=pair)
     xyz = gm.coords().cpu().numpy()
     u0 = torch.from_numpy(np.stack([c.reshape(-1) for c in inputs.tgv_velocity(*xyz)])).cuda()
     ns = binding.NSState(gm, Re)
@@ -148,7 +156,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
                                use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
                                schwarz_mid=swmid, mid_weight=0.15, inner_adapt=inner_adapt)
     phase1_opts = schwarz if use_sw else chosen
-    g = GuessNet(gm, hidden, seed, variant)
+    g = GuessNet(gm, hidden, seed, variant, pair)
 
     # ---- phase 1: simulate and collect samples
     Xs, Ts = [], []
@@ -185,13 +193,17 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     rng = np.random.default_rng(seed)
     total = epochs * len(Xs)
     losses = []
+    ework = torch.empty(2 * gm.nloc, dtype=torch.float32, device="cuda") if loss != "mse" else None
     k = 0
     for ep in range(epochs):
         for i in rng.permutation(len(Xs)):
             lr_k = lr * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * k / max(total - 1, 1))))
-            loss = g.net.grad(Xs[i], Ts[i], rows_real=g.E, outs_real=g.npt)
+            if loss in ("energy", "energy_avg"):
+                li = g.net.grad_energy(Xs[i], Ts[i], gm, lam, assembled=loss == "energy_avg", work=ework)
+            else:
+                li = g.net.grad(Xs[i], Ts[i], rows_real=g.E, outs_real=g.npt)
             g.net.adam(lr_k)
-            losses.append(loss)
+            losses.append(li)
             k += 1
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
@@ -258,7 +270,8 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
            "train": {"samples": len(losses) // max(epochs, 1), "adam_steps": k, "seconds": round(train_s, 3),
                      "loss_first": losses[0], "loss_last": losses[-1],
                      "network": f"{g.I}-{g.H}-{g.H}-{g.O} BF16 (tcgen05), {g.net.P} parameters",
-                     "variant": variant},
+                     "variant": variant, "loss": loss, "lam": lam if loss != "mse" else None,
+                     "pair_residual": bool(pair)},
            "phase1_iters_mean": float(np.mean([a for a, _ in phase1])),
            "phase1_solver": "schwarz" if use_sw else "chosen",
            "methods": results, "wall_s": round(time.perf_counter() - t_all, 1)}
