@@ -271,7 +271,21 @@ typedef struct {
                               a short round, not a reduction by inner_tol);
                               0 (default): inner_tol every round.  The FP64 true
                               residual still decides convergence. */
+    int krylov;            /* SEM_PCG_MIXED: inner Krylov method, SEM_KRYLOV_CG (default:
+                              Jacobi-PCG, or flexible CG with a Schwarz preconditioner)
+                              or SEM_KRYLOV_FGMRES: flexible restarted GMRES (the
+                              paper's pressure solver, Sec. 3.1), one cycle of at most
+                              gmres_restart iterations per refinement round (the
+                              restart is the refinement: the next cycle starts from the
+                              FP64 true residual), preconditioned by the Schwarz
+                              object(s) or the Jacobi diagonal; Arnoldi in FP32 with
+                              classical Gram-Schmidt and a second pass where the first
+                              cancelled all but 1 % of the vector */
+    int gmres_restart;     /* SEM_KRYLOV_FGMRES: cycle length, 1..128 (0 = 30); the
+                              scratch grows by 2 gmres_restart + 2 FP32 vectors */
 } sem_pcg_opts;
+#define SEM_KRYLOV_CG 0
+#define SEM_KRYLOV_FGMRES 1
 
 typedef struct {
     int iters;             /* total (inner) CG iterations */

@@ -30,6 +30,7 @@ SEM_GEOM_PAIR = 4
 SEM_GEOM_AFFINE = 8
 SEM_GEOM_BF16 = 16
 SEM_PCG_F64, SEM_PCG_MIXED, SEM_PCG_F64_PAIR = 0, 1, 2
+SEM_KRYLOV_CG, SEM_KRYLOV_FGMRES = 0, 1
 
 FIELD_MASS, FIELD_MULT, FIELD_DINV = 0, 1, 2
 
@@ -54,7 +55,7 @@ class PcgOpts(ctypes.Structure):
                 ("profile", ctypes.c_int), ("dinv", ctypes.c_void_p), ("mixed_restart", ctypes.c_int),
                 ("schwarz", ctypes.c_void_p), ("coarse_iters", ctypes.c_int), ("coarse_tol", ctypes.c_double),
                 ("outer_pair", ctypes.c_int), ("schwarz_mid", ctypes.c_void_p), ("mid_weight", ctypes.c_double),
-                ("inner_adapt", ctypes.c_double)]
+                ("inner_adapt", ctypes.c_double), ("krylov", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
 
 
 class PcgStats(ctypes.Structure):
@@ -324,14 +325,18 @@ class Mesh:
     def pcg_opts(self, tol=1e-10, max_iter=10000, precision=SEM_PCG_F64, inner_tol=1e-4, h1=1.0, h2=0.0,
                  check_every=16, use_initial_guess=False, relative=True, profile=False,
                  mixed_restart=False, schwarz=None, coarse_iters=3, coarse_tol=1e-2,
-                 outer_pair=False, schwarz_mid=None, mid_weight=0.15, inner_adapt=0.0) -> PcgOpts:
+                 outer_pair=False, schwarz_mid=None, mid_weight=0.15, inner_adapt=0.0, krylov=0,
+                 gmres_restart=0) -> PcgOpts:
         """Solver options; schwarz: a Schwarz object (hybrid Schwarz inner
         preconditioner of the mixed solver), its coarse level solved by
         coarse_iters Jacobi-CG iterations (3: on the 32^3 channel, N = 7, more
         do not lower the outer iteration count) to coarse_tol; inner_adapt:
-        theta of the adaptive inner tolerance (0: inner_tol every round)."""
+        theta of the adaptive inner tolerance (0: inner_tol every round);
+        krylov: SEM_KRYLOV_CG or SEM_KRYLOV_FGMRES (gmres_restart: cycle
+        length, 0 = 30)."""
         o = PcgOpts()
         o.inner_adapt = float(inner_adapt)
+        o.krylov, o.gmres_restart = int(krylov), int(gmres_restart)
         o.schwarz = schwarz.handle.value if schwarz is not None else None
         o.schwarz_mid = schwarz_mid.handle.value if schwarz_mid is not None else None
         o.mid_weight = float(mid_weight)

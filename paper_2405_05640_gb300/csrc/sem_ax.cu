@@ -468,14 +468,16 @@ static int dispatch_ax(const sem_mesh *m, const T *u, T *w, const void *G, doubl
     }
 }
 
-int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st) {
+int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st, const int *guard, int gval) {
     if (!m->G32) return fail(SEM_ERR_INVALID_ARG, "mesh built without SEM_GEOM_F32");
     const CgFuse<float> none{};
     if (m->aff32)
-        return dispatch_ax<float, false, false, DMatF, true>(m, u, w, m->aff32, 1.0, 0.0, m->Df, none, st);
+        return dispatch_ax<float, false, false, DMatF, true>(m, u, w, m->aff32, 1.0, 0.0, m->Df, none, st, guard,
+                                                             gval);
     if (m->G16)
-        return dispatch_ax<float, false, false, DMatF, false, true>(m, u, w, m->G16, 1.0, 0.0, m->Df, none, st);
-    return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st);
+        return dispatch_ax<float, false, false, DMatF, false, true>(m, u, w, m->G16, 1.0, 0.0, m->Df, none, st,
+                                                                    guard, gval);
+    return dispatch_ax<float, false, false>(m, u, w, m->G32, 1.0, 0.0, m->Df, none, st, guard, gval);
 }
 
 int ax_cg_launch_f32(const sem_mesh *m, const CgFuse<float> &cg, float *w, cudaStream_t st) {

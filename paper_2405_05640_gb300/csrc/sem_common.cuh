@@ -37,6 +37,18 @@ struct PcgScal {
     unsigned cnt[4];  // arrival counters of the grid reductions (cnt[3]: fused operator)
 };
 
+// Inner relative tolerance of a refinement round: delta, or with theta > 0
+// the larger theta * target / ||r|| (target^2 = the outer tol2, ||r||^2 =
+// the outer rr of `so`), capped at 0.5 so that every round iterates: a round
+// that starts near the outer target stops once the target is within reach.
+__device__ __forceinline__ double inner_delta(const PcgScal *__restrict__ so, double delta, double theta) {
+    if (theta > 0.0 && so->rr > 0.0) {
+        const double a = fmin(0.5, theta * sqrt(so->tol2 / so->rr));
+        if (a > delta) return a;
+    }
+    return delta;
+}
+
 // Arguments of the fused CG operator: p <- dinv r + beta p, w = A_L p,
 // alpha = rho / sum_l p_l w_l (grid reduction over per-CTA partials).
 template <typename T>
@@ -214,7 +226,8 @@ __device__ __forceinline__ bool grid_barrier_bounded(unsigned *bar, unsigned tar
 // ---------------------------------------------------------------- host helpers
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,
                   cudaStream_t st, const int *guard = nullptr, int gval = 0);
-int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st);
+int ax_launch_f32(const sem_mesh *m, const float *u, float *w, cudaStream_t st, const int *guard = nullptr,
+                  int gval = 0);
 // FP64 operator in FP32-pair arithmetic (sem_ax_pair.cu); needs m->G2.
 int ax_launch_pair(const sem_mesh *m, const double *u, double *w, cudaStream_t st);
 // Fused CG operator (see CgFuse); w receives the local (unassembled) A_L p.
@@ -291,6 +304,30 @@ size_t schwarz_mid_work_bytes(const sem_schwarz *mid);
 int schwarz_mid_check(const sem_schwarz *sw, const sem_schwarz *mid);
 int schwarz_mid_apply_add(const sem_schwarz *sw, const sem_schwarz *mid, double w, const float *r, float *z,
                           void *work, const int *done, cudaStream_t st);
+
+// Flexible GMRES inner solve (sem_gmres.cu): one cycle of at most `restart`
+// iterations on A d = r64 * so->scale from d = 0, preconditioned by the
+// hybrid Schwarz object sw (plus the intermediate level mid), or by the FP32
+// Jacobi diagonal when sw is null; stops when the Arnoldi residual estimate
+// has fallen by inner_delta(so, delta, theta); writes d.  work:
+// gmres_work_bytes(m, restart).
+constexpr int kGmMaxRestart = 128;
+struct GmresArgs {
+    int restart, max_iter, check;
+    double delta, theta;
+    const sem_schwarz *sw;
+    int coarse_iters;
+    double coarse_tol;
+    const sem_schwarz *mid;
+    double mid_w;
+    void *mid_work;
+};
+struct GmresResult {
+    int iters, converged, status, launches, ax_launches;
+};
+size_t gmres_work_bytes(const sem_mesh *m, int restart);
+int gmres_cycle(const sem_mesh *m, const double *r64, const PcgScal *so, float *d, const GmresArgs &a, void *work,
+                cudaStream_t st, GmresResult *out);
 
 // gather-scatter modes
 constexpr int kGsSum = 0;       // sum copies

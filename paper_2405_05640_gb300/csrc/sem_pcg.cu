@@ -106,18 +106,6 @@ __device__ __forceinline__ void set_start_flags(PcgScal *s, double bb, double rr
     }
 }
 
-// Inner relative tolerance of a refinement round: delta, or with theta > 0
-// the larger theta * target / ||r|| (target^2 = the outer tol2, ||r||^2 =
-// the outer rr of `so`), capped at 0.5 so that every round iterates: a round
-// that starts near the outer target stops once the target is within reach.
-__device__ __forceinline__ double inner_delta(const PcgScal *__restrict__ so, double delta, double theta) {
-    if (theta > 0.0 && so->rr > 0.0) {
-        const double a = fmin(0.5, theta * sqrt(so->tol2 / so->rr));
-        if (a > delta) return a;
-    }
-    return delta;
-}
-
 // Start of a CG solve in precision T: r = scale * (b - Ax0) (ax0 may be
 // null), z = dinv r, p = z; bb = <b,b>, rr = <r,r>, rho = <r,z>.
 // In the mixed solver b is the FP64 outer residual and `scale` = 1/||b||
@@ -496,9 +484,16 @@ static size_t pcg_scratch_mixed(const sem_mesh *m) {
            2 * align_up(kPartialBytes) + 2 * align_up(sizeof(PcgScal));
 }
 
+static int gmres_restart(const sem_pcg_opts *o) { return o->gmres_restart > 0 ? o->gmres_restart : 30; }
+
+static size_t mid_bytes(const sem_pcg_opts *o) {
+    return o->schwarz && o->schwarz_mid ? align_up(schwarz_mid_work_bytes(o->schwarz_mid)) : 0;
+}
+
 static size_t pcg_scratch(const sem_mesh *m, const sem_pcg_opts *o) {
     if (o && o->precision == SEM_PCG_MIXED)
-        return pcg_scratch_mixed(m) + (o->schwarz && o->schwarz_mid ? schwarz_mid_work_bytes(o->schwarz_mid) : 0);
+        return pcg_scratch_mixed(m) + mid_bytes(o) +
+               (o->krylov == SEM_KRYLOV_FGMRES ? gmres_work_bytes(m, gmres_restart(o)) : 0);
     return pcg_scratch_f64(m);
 }
 
@@ -849,7 +844,7 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
     c.launches += 1;
     PcgScal ho{}, hi{};
     int inner_total = 0, outer = 0, status = SEM_ERR_NOT_CONVERGED;
-    double prev_rr = -1.0;
+    double prev_rr = -1.0, guard = 0.25;
     while (true) {
         SEM_CUDA_CHECK(cudaMemcpyAsync(&ho, M.scal_out, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
         SEM_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -862,10 +857,30 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         }
         if (inner_total >= o->max_iter) break;
         // stagnation guard: the FP64 residual must keep falling
-        if (prev_rr >= 0.0 && !(ho.rr < 0.25 * prev_rr)) break;
+        if (prev_rr >= 0.0 && !(ho.rr < guard * prev_rr)) break;
         prev_rr = ho.rr;
         const sem_schwarz *sw = static_cast<const sem_schwarz *>(o->schwarz);
-        if (outer == 0 || o->mixed_restart || sw) {
+        if (o->krylov == SEM_KRYLOV_FGMRES) {
+            // one flexible GMRES cycle on A d = r / ||r||, from d = 0
+            char *mid_work = static_cast<char *>(scratch) + pcg_scratch_mixed(m);
+            GmresArgs ga{gmres_restart(o), o->max_iter - inner_total, check, inner_tol, o->inner_adapt, sw,
+                         o->coarse_iters, o->coarse_tol > 0 ? o->coarse_tol : 1e-2,
+                         static_cast<const sem_schwarz *>(o->schwarz_mid),
+                         o->mid_weight > 0.0 ? o->mid_weight : 0.15, mid_work};
+            GmresResult gr{};
+            int s = gmres_cycle(m, M.r64, M.scal_out, M.d32, ga, mid_work + mid_bytes(o), st, &gr);
+            if (s != SEM_OK) return s;
+            cin.launches += gr.launches;
+            cin.ax_launches += gr.ax_launches;
+            inner_total += gr.iters;
+            if (gr.status == SEM_ERR_NAN) {
+                status = SEM_ERR_NAN;
+                break;
+            }
+            // a cycle that stopped at its restart length must still lower the
+            // FP64 residual, one that met its tolerance by the usual factor
+            guard = gr.converged ? 0.25 : 1.0;
+        } else if (outer == 0 || o->mixed_restart || sw) {
             // inner FP32 solve of A d = r / ||r||, from d = 0
             SEM_CUDA_CHECK(cudaMemsetAsync(M.d32, 0, sizeof(float) * n, st));
             pcg_init_kernel<float, double><<<kPBlocks, kPThreads, 0, st>>>(
@@ -878,8 +893,10 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
         }
         SEM_CUDA_CHECK(cudaGetLastError());
         cin.launches += 1;
-        int s;
-        if (sw)
+        int s = SEM_OK;
+        if (o->krylov == SEM_KRYLOV_FGMRES)
+            ;  // the cycle above
+        else if (sw)
             s = cg_loop_schwarz(m, M.in, M.z32, M.wa32, M.d32, sw, o->coarse_iters, o->coarse_tol > 0 ? o->coarse_tol : 1e-2,
                                 o->max_iter - inner_total, check, st, cin, &hi, o->schwarz_mid,
                                 o->mid_weight > 0.0 ? o->mid_weight : 0.15,
@@ -888,7 +905,8 @@ static int pcg_mixed(const sem_mesh *m, const double *b, double *x, const sem_pc
             s = cg_loop<float>(m, M.in, M.d32, m->dinv32, o->max_iter - inner_total, check, o->h1, o->h2, st, cin,
                                &hi);
         if (s != SEM_OK) return s;
-        inner_total = (o->mixed_restart || sw) ? inner_total + hi.iter : hi.iter;
+        if (o->krylov != SEM_KRYLOV_FGMRES)
+            inner_total = (o->mixed_restart || sw) ? inner_total + hi.iter : hi.iter;
         // x += ||r|| d; r = b - A x in FP64
         ir_correct_kernel<<<kPBlocks, kPThreads, 0, st>>>(x, M.d32, n, M.scal_out);
         s = apply_assembled_timed<double>(m, x, M.w64, o->h1, o->h2, st, c, o->outer_pair != 0);
@@ -943,6 +961,12 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
         return fail(SEM_ERR_UNSUPPORTED, "SEM_PCG_MIXED solves the Poisson operator (h1 = 1, h2 = 0, mesh diagonal)");
     if (!(o->inner_adapt >= 0.0 && o->inner_adapt < 1.0))
         return fail(SEM_ERR_INVALID_ARG, "inner_adapt must be in [0, 1)");
+    if (o->krylov != SEM_KRYLOV_CG && o->krylov != SEM_KRYLOV_FGMRES)
+        return fail(SEM_ERR_INVALID_ARG, "unknown krylov method");
+    if (o->krylov == SEM_KRYLOV_FGMRES && o->precision != SEM_PCG_MIXED)
+        return fail(SEM_ERR_UNSUPPORTED, "flexible GMRES is the inner solver of SEM_PCG_MIXED");
+    if (o->gmres_restart < 0 || o->gmres_restart > kGmMaxRestart)
+        return fail(SEM_ERR_INVALID_ARG, "gmres_restart outside [0, 128]");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");
     return SEM_OK;
 }
@@ -1353,6 +1377,7 @@ static int batched_impl(const sem_mesh *const *meshes, const sem_schwarz *const 
     if (o->use_initial_guess) return fail(SEM_ERR_UNSUPPORTED, "batched solves start from x = 0");
     if (o->schwarz || o->schwarz_mid || o->outer_pair)
         return fail(SEM_ERR_UNSUPPORTED, "batched solves use the Jacobi inner solver");
+    if (o->krylov != SEM_KRYLOV_CG) return fail(SEM_ERR_UNSUPPORTED, "batched solves use CG inner solves");
     if (!(o->inner_adapt >= 0.0 && o->inner_adapt < 1.0))
         return fail(SEM_ERR_INVALID_ARG, "inner_adapt must be in [0, 1)");
     if (!(o->tol > 0.0) || o->max_iter < 1) return fail(SEM_ERR_INVALID_ARG, "tol must be > 0, max_iter >= 1");

@@ -28,7 +28,8 @@ only sequences calls and keeps device buffers):
      paper's pressure preconditioner, "schwarz_*"), each from p^{n-1}, from
      p_ext and from the learned guess p_ext + se * MLP(features).
      The three-level Schwarz multigrid ("schwarz3_*": an intermediate order-3
-     level) from p_ext and from the learned guess.  Every mixed solve uses
+     level) from p_ext and from the learned guess; flexible GMRES(30) with
+     the two-level Schwarz preconditioner ("schwarzgm_*") from p_ext.  Every mixed solve uses
      the adaptive inner tolerance inner_adapt (a round stops once the outer
      target is within reach); the "*_fixed" methods keep inner_tol = 1e-2
      every round.  Pressure-solve wall time includes building the guess.
@@ -114,7 +115,7 @@ class GuessNet:
 
 METHODS = ("plain_f64_prev", "chosen_prev", "chosen_extrap", "chosen_learned", "chosen_extrap_fixed",
            "schwarz_prev", "schwarz_extrap", "schwarz_learned", "schwarz_extrap_fixed", "schwarz_learned_fixed",
-           "schwarz3_extrap", "schwarz3_learned")
+           "schwarz3_extrap", "schwarz3_learned", "schwarzgm_extrap")
 
 
 def _method(meth):
@@ -218,7 +219,9 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     results = {}
     by_solver = {"plain": plain, "chosen": chosen}
     if use_sw:
-        by_solver.update(schwarz=schwarz, schwarz3=schwarz3)
+        gmo = binding.PcgOpts.from_buffer_copy(schwarz)
+        gmo.krylov, gmo.gmres_restart = binding.SEM_KRYLOV_FGMRES, 30
+        by_solver.update(schwarz=schwarz, schwarz3=schwarz3, schwarzgm=gmo)
     for meth in methods:
         solver, gkind, fixed = _method(meth)
         popts = by_solver[solver]

@@ -90,8 +90,8 @@ def test_schwarz_and_solver_option_host_checks(lib):
     # double-float outer-residual switch and the intermediate multigrid level
     # at the end of the struct
     names = [f[0] for f in binding.PcgOpts._fields_]
-    assert names[-7:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair", "schwarz_mid", "mid_weight",
-                          "inner_adapt"]
+    assert names[-9:] == ["schwarz", "coarse_iters", "coarse_tol", "outer_pair", "schwarz_mid", "mid_weight",
+                          "inner_adapt", "krylov", "gmres_restart"]
     assert lib.sem_schwarz_mid_work_bytes(None) == 0
     assert lib.sem_schwarz_apply3(None, None, 0.15, None, None, 3, 1e-2, None, 0, None) == \
         binding.SEM_ERR_INVALID_ARG
