@@ -88,6 +88,7 @@ def parse_args(argv=None):
     p.add_argument("--krylov", choices=["cg", "fgmres"], default="cg",
                    help="schwarz: inner Krylov method (flexible CG or flexible restarted GMRES)")
     p.add_argument("--gmres-restart", type=int, default=30, help="schwarz: GMRES cycle length")
+    p.add_argument("--inner-tol", type=float, default=1e-5, help="schwarz: inner relative tolerance of a round")
     p.add_argument("--outer-pair", action="store_true",
                    help="Schwarz workload: outer residual with the double-float (FP32-pair) operator")
     p.add_argument("--nsolve", type=int, default=64)
@@ -330,7 +331,10 @@ MID_WEIGHT = 0.15  # weight of the intermediate Schwarz level (oracle and GPU me
 # theta of the adaptive inner tolerance: a refinement round stops once half
 # the outer target is within reach (the FP64 residual still decides)
 INNER_ADAPT = 0.5
-CHOSEN_SCHWARZ = dict(precision=1, inner_tol=1e-2, coarse_iters=3, coarse_tol=1e-2, check_every=8,
+# inner tolerance of the Schwarz solves: 1e-5 (two refinement rounds; Jacobi-PCG keeps 1e-2, its long FP32
+# runs lose orthogonality)
+SCHWARZ_INNER_TOL = 1e-5
+CHOSEN_SCHWARZ = dict(precision=1, inner_tol=SCHWARZ_INNER_TOL, coarse_iters=3, coarse_tol=1e-2, check_every=8,
                       inner_adapt=INNER_ADAPT)
 JACOBI_MIXED = dict(precision=1, inner_tol=1e-2, inner_adapt=INNER_ADAPT)  # FP64 refinement around FP32 Jacobi-PCG
 GMRES_RESTART = 30  # cycle length of flexible GMRES (one cycle per refinement round)
@@ -881,7 +885,7 @@ def run_schwarz(args):
     case = inputs.channel(args.nel, args.order)
     gm, sw = _schwarz_setup(case, pair=args.outer_pair)
     b = gm.scatter(torch.from_numpy(case.rhs_global()).cuda())
-    opts = dict(tol=TOL, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, check_every=8,
+    opts = dict(tol=TOL, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=args.inner_tol, check_every=8,
                 schwarz=sw, coarse_iters=args.coarse_iters, coarse_tol=1e-2, outer_pair=args.outer_pair,
                 inner_adapt=INNER_ADAPT)
     if args.krylov == "fgmres":
@@ -911,6 +915,7 @@ def run_schwarz(args):
                       "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
                       "dtype": "f32 inner / f64 refinement",
                       "config": {"workload": WORKLOAD, "coarse_iters": args.coarse_iters, "krylov": args.krylov,
+                                 "inner_tol": args.inner_tol,
                                  "gmres_restart": args.gmres_restart if args.krylov == "fgmres" else None,
                                  "levels": 3 if args.mid else 2, "mid_order": args.mid or None,
                                  "mid_weight": args.mid_weight if args.mid else None,
@@ -933,6 +938,7 @@ def run_tgv_learned(args):
     from paper_2405_05640_gb300 import tgv_learned
     _build.build()
     out = tgv_learned.run(nel=args.nel, N=args.order, train_steps=args.train_steps, eval_steps=args.eval_steps,
+                          schwarz_inner_tol=SCHWARZ_INNER_TOL,
                           epochs=args.epochs, variant=args.variant, inner_adapt=INNER_ADAPT, tol=args.tol,
                           loss=args.loss, lam=args.lam,
                           pair=not args.fp64_residual,
@@ -986,7 +992,8 @@ def run_batched(args):
     for N in sorted({c.N for c in used}):
         i = next(k for k, c in enumerate(used) if c.N == N)
         tune[N] = meshes[i].autotune(binding.SEM_F32, True)
-    kw = dict(tol=TOL, max_iter=50000, inner_tol=1e-2, check_every=args.round_iters, inner_adapt=INNER_ADAPT)
+    kw = dict(tol=TOL, max_iter=50000, inner_tol=SCHWARZ_INNER_TOL if args.batched_schwarz else 1e-2,
+              check_every=args.round_iters, inner_adapt=INNER_ADAPT)
     keep = []
     if args.batched_schwarz:
         sws = []
@@ -1180,7 +1187,8 @@ def run_tgv_long(args):
     ns = binding.NSState(gm, Re)
     ns.set_scheme(3, dealias=True)
     ns.set_velocity(u0)
-    po = gm.pcg_opts(tol=1e-8, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2, check_every=8,
+    po = gm.pcg_opts(tol=1e-8, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=SCHWARZ_INNER_TOL,
+                     check_every=8,
                      schwarz=sw, coarse_iters=3, coarse_tol=1e-2, use_initial_guess=True, inner_adapt=INNER_ADAPT)
     vo = gm.pcg_opts(tol=1e-8, max_iter=50000, check_every=8)
     Bm = gm.field(0)

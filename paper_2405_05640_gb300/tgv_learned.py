@@ -31,8 +31,9 @@ only sequences calls and keeps device buffers):
      level) from p_ext and from the learned guess; flexible GMRES(30) with
      the two-level Schwarz preconditioner ("schwarzgm_*") from p_ext.  Every mixed solve uses
      the adaptive inner tolerance inner_adapt (a round stops once the outer
-     target is within reach); the "*_fixed" methods keep inner_tol = 1e-2
-     every round.  Pressure-solve wall time includes building the guess.
+     target is within reach), the Schwarz ones an inner tolerance of
+     schwarz_inner_tol (Jacobi: 1e-2); the "*_fixed" methods keep
+     inner_tol = 1e-2 every round.  Pressure-solve wall time includes building the guess.
   Phase 1 solves with the Schwarz solver when it is among the methods (the
   pressures, hence the samples, are the same to the tolerance).
 """
@@ -127,7 +128,7 @@ def _method(meth):
 
 def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs=8, lr=1e-3, hidden=256,
         tol=1e-8, seed=0, skip=10, variant="p1", methods=METHODS, inner_adapt=0.5, loss="energy_avg", lam=1.0,
-        pair=True, log=None):
+        pair=True, schwarz_inner_tol=1e-5, log=None):
     import torch
     log = log or (lambda *a: None)
     t_all = time.perf_counter()
@@ -148,12 +149,14 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     if use_sw:
         gc = binding.Mesh(1, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
         sw = binding.Schwarz(gm, gc)
-        schwarz = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
+        schwarz = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED,
+                              inner_tol=schwarz_inner_tol,
                               use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
                               inner_adapt=inner_adapt)
         gmid = binding.Mesh(3, case.nel, case.periodic, case.faces, case.vertices(), geom_f32=True)
         swmid = binding.Schwarz(gmid, gc)
-        schwarz3 = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED, inner_tol=1e-2,
+        schwarz3 = gm.pcg_opts(tol=tol, max_iter=50000, precision=binding.SEM_PCG_MIXED,
+                               inner_tol=schwarz_inner_tol,
                                use_initial_guess=True, check_every=8, schwarz=sw, coarse_iters=3, coarse_tol=1e-2,
                                schwarz_mid=swmid, mid_weight=0.15, inner_adapt=inner_adapt)
     phase1_opts = schwarz if use_sw else chosen
@@ -227,7 +230,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
         popts = by_solver[solver]
         if fixed:
             popts = binding.PcgOpts.from_buffer_copy(popts)
-            popts.inner_adapt = 0.0
+            popts.inner_adapt, popts.inner_tol = 0.0, 1e-2
         ns.restore(ck)
         p4 = p4_ck.clone()
         g.rho_prev = rho_ck
