@@ -223,7 +223,7 @@ def run(nel=32, N=7, Re=1600.0, dt=1e-3, train_steps=100, eval_steps=100, epochs
     by_solver = {"plain": plain, "chosen": chosen}
     if use_sw:
         gmo = binding.PcgOpts.from_buffer_copy(schwarz)
-        gmo.krylov, gmo.gmres_restart = binding.SEM_KRYLOV_FGMRES, 30
+        gmo.krylov, gmo.gmres_restart, gmo.inner_tol = binding.SEM_KRYLOV_FGMRES, 30, 1e-2
         by_solver.update(schwarz=schwarz, schwarz3=schwarz3, schwarzgm=gmo)
     for meth in methods:
         solver, gkind, fixed = _method(meth)
