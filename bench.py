@@ -48,6 +48,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Ax GDOF/s (% HBM roofline); PCG time-to-1e-8 residual, plain FP64 vs chosen"
 UNIT = "GDOF/s"
 WORKLOAD = "channel 32x32x32 hex, N=7, tanh beta=2 in y, periodic x/z, Dirichlet y, random mean-zero RHS"
+
+
+def channel_workload(nel, order):
+    """The channel workload's name at the sizes a run uses (WORKLOAD at 32^3, N = 7)."""
+    return WORKLOAD.replace("32x32x32", f"{nel}x{nel}x{nel}").replace("N=7", f"N={order}")
 TOL = 1e-8
 AX_BYTES_PER_POINT = {"f64": 64}
 
@@ -624,7 +629,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "E": case.E, "N": case.N, "n_paper": case.n_paper,
+        "config": {"workload": channel_workload(args.nel, args.order), "E": case.E, "N": case.N,
+                   "n_paper": case.n_paper,
                    "nloc": case.nloc, "nglob": gm.nglob, "tol": TOL,
                    "precision": "FP64 Jacobi-PCG (FP64 operator, gather-scatter, vectors and dot products)",
                    "geometry": "general: 6 geometric factors per point (FP64)",
@@ -700,7 +706,8 @@ def run_reference(args):
     rec = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "E": case.E, "N": case.N,
+           "data": "synthetic", "config": {"workload": channel_workload(args.nel, args.order), "E": case.E,
+                                           "N": case.N,
                                            "n_paper": case.n_paper, "tol": TOL, "precision": "FP64 oracle"},
            "ms_per_step_stats": median_ci([t * 1e3 for t in times]),
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
@@ -916,7 +923,8 @@ def run_schwarz(args):
                       "value": round(ms, 3), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
                       "dtype": "f32 inner / f64 refinement",
-                      "config": {"workload": WORKLOAD, "coarse_iters": args.coarse_iters, "krylov": args.krylov,
+                      "config": {"workload": channel_workload(args.nel, args.order),
+                                 "coarse_iters": args.coarse_iters, "krylov": args.krylov,
                                  "inner_tol": args.inner_tol,
                                  "gmres_restart": args.gmres_restart if args.krylov == "fgmres" else None,
                                  "levels": 3 if args.mid else 2, "mid_order": args.mid or None,

@@ -76,7 +76,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags: list[str] | N
         objs = list(ex.map(one, sources()))
     tmp = SO + f".{os.getpid()}.tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-L", _cuda_lib(),
-                                                         "-Xlinker", "-rpath," + _cuda_lib()]
+                                                         "-Xlinker", "-rpath," + _cuda_lib(), "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "../../include/sem.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sem {
 
@@ -222,6 +223,16 @@ __device__ __forceinline__ bool grid_barrier_bounded(unsigned *bar, unsigned tar
     __syncthreads();
     return ok != 0;
 }
+
+// A named range on a profiler's CPU timeline (NVTX; a no-op when no tool is
+// attached): solves, refinement rounds, Krylov cycles, NS phases, network
+// passes.  ncu can select the kernels of a range (--nvtx --nvtx-include).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------- host helpers
 int ax_launch_f64(const sem_mesh *m, const double *u, double *w, double h1, double h2,

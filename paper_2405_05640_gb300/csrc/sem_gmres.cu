@@ -393,6 +393,7 @@ static int gm_iteration(const sem_mesh *m, const GmWork &W, int jj, const GmresA
 
 int gmres_cycle(const sem_mesh *m, const double *r64, const PcgScal *so, float *d, const GmresArgs &a, void *work,
                 cudaStream_t st, GmresResult *out) {
+    NvtxRange nvtx_range("GMRES cycle");
     if (a.restart < 1 || a.restart > kGmMaxRestart) return fail(SEM_ERR_INVALID_ARG, "restart outside [1, 128]");
     const int64_t n = m->nloc;
     GmWork W = carve(m, a.restart, work);

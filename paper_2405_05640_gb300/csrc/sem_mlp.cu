@@ -379,6 +379,7 @@ static int fwd(sem_mlp *n, const void *X, int rows, cudaStream_t st) {
 }
 
 int sem_mlp_forward(sem_mlp *n, const void *X, int rows, float *Y, void *stream) {
+    NvtxRange nvtx_range("network forward");
     if (!n || !X || !Y) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (rows <= 0 || rows % 128 || rows > n->R) return fail(SEM_ERR_INVALID_ARG, "rows must be a multiple of 128, <= max_rows");
     cudaStream_t st = as_stream(stream);
@@ -439,6 +440,7 @@ static int mlp_finish(sem_mlp *n, const double *dloss, double norm, double *loss
 
 int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_real, int outs_real, double *loss,
                  void *stream) {
+    NvtxRange nvtx_range("network forward + backward");
     if (!n || !X || !T || !loss) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (rows <= 0 || rows % 128 || rows > n->R || rows_real <= 0 || rows_real > rows || outs_real <= 0 ||
         outs_real > n->O)
@@ -457,6 +459,7 @@ int sem_mlp_grad(sem_mlp *n, const void *X, const float *T, int rows, int rows_r
 
 int sem_mlp_grad_energy(sem_mlp *n, const sem_mesh *m, const void *X, const float *T, int rows, double lambda,
                         int assembled, float *work, size_t work_floats, double *loss, void *stream) {
+    NvtxRange nvtx_range("network forward + backward (energy norm)");
     if (!n || !m || !X || !T || !work || !loss) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (rows <= 0 || rows % 128 || rows > n->R || m->E > rows || m->npt > n->O)
         return fail(SEM_ERR_INVALID_ARG, "rows must be a multiple of 128 with E <= rows <= max_rows, npt <= n_out");

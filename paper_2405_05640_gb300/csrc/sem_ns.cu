@@ -577,6 +577,7 @@ size_t sem_ns_scratch_bytes(const sem_ns *ns, const sem_pcg_opts *popts, const s
 }
 
 int sem_ns_step_begin(sem_ns *ns, double dt, void *stream) {
+    NvtxRange nvtx_range("NS step: advection, pressure right-hand side");
     if (!ns || !(dt > 0.0)) return fail(SEM_ERR_INVALID_ARG, "NULL state or dt <= 0");
     const sem_mesh *m = ns->m;
     cudaStream_t st = as_stream(stream);
@@ -616,6 +617,7 @@ int sem_ns_step_begin(sem_ns *ns, double dt, void *stream) {
 int sem_ns_step_finish(sem_ns *ns, const sem_pcg_opts *popts, const sem_pcg_opts *vopts, const double *p_guess,
                        sem_pcg_stats *pstats, sem_pcg_stats *vstats, void *scratch, size_t scratch_bytes,
                        void *stream) {
+    NvtxRange nvtx_range("NS step: pressure and velocity solves");
     if (!ns || !popts || !vopts || !pstats || !vstats || !scratch) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (!ns->begun) return fail(SEM_ERR_INVALID_ARG, "sem_ns_step_finish without sem_ns_step_begin");
     const sem_mesh *m = ns->m;

@@ -608,6 +608,7 @@ static int apply_assembled_timed(const sem_mesh *m, const T *x, T *y, double h1,
 template <typename T>
 static int cg_loop(const sem_mesh *m, PcgWork<T> W, T *x, const T *dinv, int max_iter, int check, double h1,
                    double h2, cudaStream_t st, SolveCtx &c, PcgScal *h, bool pair = false) {
+    NvtxRange nvtx_range("PCG iterations");
     CgFuse<T> cg{W.r, dinv, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
     while (true) {
@@ -730,6 +731,7 @@ static int launch_fpcg_dots_box(const sem_mesh *m, const float *r, const float *
 static int cg_loop_schwarz(const sem_mesh *m, PcgWork<float> W, float *z, float *wa, float *x, const sem_schwarz *sw,
                            int coarse_iters, double coarse_tol, int max_iter, int check, cudaStream_t st, SolveCtx &c,
                            PcgScal *h, const sem_schwarz *mid = nullptr, double mid_w = 0.0, void *mid_work = nullptr) {
+    NvtxRange nvtx_range("flexible CG iterations (Schwarz)");
     CgFuse<float> cg{z, nullptr, W.p, W.scal, W.partial + 4 * kPBlocks};
     int launched = 0;
     while (true) {
@@ -973,6 +975,7 @@ static int check_opts(const sem_mesh *m, const sem_pcg_opts *o) {
 
 static int solve_dispatch(const sem_mesh *m, const double *b, double *x, const sem_pcg_opts *o,
                           sem_pcg_stats *stats, void *scratch, cudaStream_t st) {
+    NvtxRange nvtx_range("sem_pcg_solve");
     // every solve reports the timeouts of its own kernels: an earlier call's
     // give-up (already reported by that call, or read with
     // sem_mesh_check_device_error) is cleared here
@@ -1370,6 +1373,7 @@ namespace sem {
 static int batched_impl(const sem_mesh *const *meshes, const sem_schwarz *const *sws, int nsolve,
                         const double *const *b, double *const *x, const sem_pcg_opts *o, sem_pcg_stats *stats,
                         void *scratch, size_t scratch_bytes, void *stream) {
+    NvtxRange nvtx_range("batched solves (one graph)");
     const auto t0 = std::chrono::steady_clock::now();
     if (!meshes || nsolve <= 0 || !b || !x || !o || !stats || !scratch)
         return fail(SEM_ERR_INVALID_ARG, "NULL argument or nsolve <= 0");

@@ -1691,6 +1691,7 @@ int sem_schwarz_line_table(int N, short *out, int cap, int *slots, int *pj, int 
 
 int sem_schwarz_apply(const sem_schwarz *sw, const float *r, float *z, int coarse_iters, double coarse_tol,
                       void *stream) {
+    NvtxRange nvtx_range("Schwarz application");
     if (!sw || !r || !z) return fail(SEM_ERR_INVALID_ARG, "NULL argument");
     if (r == z) return fail(SEM_ERR_INVALID_ARG, "r and z must not overlap");
     if (coarse_iters < 0) return fail(SEM_ERR_INVALID_ARG, "coarse_iters < 0");
