@@ -137,3 +137,23 @@ def test_full_size_fgmres_schwarz_true_residual():
     om = oracle.Mesh(case.N, case.nel, case.periodic, case.faces, V)
     r = bh - om.apply(xh)
     assert np.sqrt(om.glsc3(r, r) / om.glsc3(bh, bh)) <= 1.05e-8
+
+
+def test_nan_rhs_and_converged_guess():
+    """A NaN in the right-hand side is reported as SEM_ERR_NAN; a guess that
+    already meets the tolerance returns at once with no inner iteration."""
+    import torch
+    case = inputs.deformed_cube(3, 5)
+    H, gm, kw, keep = _setup(case)
+    om = H.m
+    b = om.scatter(case.rhs_global())
+    bn = b.copy()
+    bn[len(bn) // 2] = np.nan
+    _, st = gm.pcg(_dev(bn), precision=binding.SEM_PCG_MIXED, krylov=binding.SEM_KRYLOV_FGMRES,
+                   raise_on_error=False, **kw)
+    assert st["status"] == binding.SEM_ERR_NAN, st
+    xo, _, _, so = om.pcg(b, tol=1e-13, max_iter=20000)
+    assert so == 0
+    x, st = gm.pcg(_dev(b), torch.from_numpy(xo.copy()).cuda(), tol=1e-8, precision=binding.SEM_PCG_MIXED,
+                   krylov=binding.SEM_KRYLOV_FGMRES, **kw)
+    assert st["status"] == 0 and st["iters"] == 0 and st["outer_iters"] == 0, st
