@@ -680,8 +680,10 @@ constexpr int sum_epb() {  // elements per 256-thread CTA
     return 256 / ((N + 1) * (N + 1));
 }
 
-template <int N>
-__global__ void __launch_bounds__(256, 3)
+// Off: the type of the x/y neighbour offsets (int where nel_x nel_y (N+3)^3
+// < 2^31, which halves their registers; int64_t otherwise).
+template <int N, typename Off>
+__global__ void __launch_bounds__(256, 4)
     schwarz_sum_kernel(const float *__restrict__ uext, const float *__restrict__ xc, const float *__restrict__ J1,
                        SwArgs A, CoarseTopo C, const int *__restrict__ done, float *__restrict__ z) {
     constexpr int N1 = N + 1, NE = N + 3, NE3 = NE * NE * NE, NPT = N1 * N1 * N1, COLS = N1 * N1;
@@ -708,13 +710,13 @@ __global__ void __launch_bounds__(256, 3)
         const Cover cy = cover(j, N, ey, A.nel[1], A.per[1]);
         // x/y slot pairs (b outer, a inner): validity and offset
         bool okxy[9];
-        int64_t oxy[9];
+        Off oxy[9];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 okxy[3 * b + a] = cov_ok(cy, b) && cov_ok(cx, a);
-                oxy[3 * b + a] = (int64_t)(cov_d(cx, a) + sy * cov_d(cy, b)) * NE3 + cov_I(cx, a) + NE * cov_I(cy, b);
+                oxy[3 * b + a] = (Off)(cov_d(cx, a) + sy * cov_d(cy, b)) * NE3 + cov_I(cx, a) + NE * cov_I(cy, b);
             }
         float u0 = 0.f, u1 = 0.f;
         if (xc) {
@@ -1268,7 +1270,12 @@ static int sw_apply_n(const sem_schwarz *sw, const float *r, float *z, int coars
     }
     int64_t gp = (m->E + sum_epb<N>() - 1) / sum_epb<N>();
     if (gp > (int64_t)m->num_sms * 16) gp = (int64_t)m->num_sms * 16;
-    schwarz_sum_kernel<N><<<(int)gp, 256, 0, st>>>(sw->uext, coarse ? sw->xc : nullptr, sw->J1, A, C, done, z);
+    if ((int64_t)A.nel[0] * A.nel[1] * S::NE3 < ((int64_t)1 << 31))
+        schwarz_sum_kernel<N, int><<<(int)gp, 256, 0, st>>>(sw->uext, coarse ? sw->xc : nullptr, sw->J1, A, C, done,
+                                                             z);
+    else
+        schwarz_sum_kernel<N, int64_t><<<(int)gp, 256, 0, st>>>(sw->uext, coarse ? sw->xc : nullptr, sw->J1, A, C,
+                                                                 done, z);
     SEM_CUDA_CHECK(cudaGetLastError());
     return SEM_OK;
 }
