@@ -71,7 +71,7 @@ static GmWork carve(const sem_mesh *m, int restart, void *work) {
     return W;
 }
 
-// Block sum of K doubles per thread into out[k * stride] (thread 0 writes).
+// Block sums of K doubles per thread: thread k < K writes sum k to out[k * stride].
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double *out, int stride) {
     __shared__ double sh[kGmThreads / 32][K];
